@@ -1,0 +1,225 @@
+"""FP64 CPU oracle for the cut-CZ partition scheme of arXiv 1802.06952.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  It shares no code with the CUDA library (``paper_1802_06952_gb300``),
+and the library never imports it.
+
+Contents
+  circuit.py  random grid circuit generator, canonical gate-list text, cut plan
+              (Supplementary A, Eqs. 3-8; Section 2.1, Eq. 1)
+  oracle.c    plain FP64 state-vector evolution (Supplementary A, Eq. 4) and the
+              cut-and-sum reconstruction (Supplementary A, Eq. 8)
+  this file   ctypes binding, the amplitude selection draw, and the FP64
+              statistics of Section 3 (Eq. 7)
+
+Parity status: every function here is pinned by tests under ``tests/`` that do
+not call the oracle to make their expected values (brute-force Kronecker
+products, closed forms, counts printed in the paper, invariants).  The
+``rule_t_in_pool`` gate-rule variant is not implemented.
+"""
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+from . import circuit  # noqa: F401
+from .circuit import SplitMix64, CutPlan, generate, grid_cut, to_text, parse_text  # noqa: F401
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_SRC = os.path.join(_HERE, "oracle.c")
+
+CODES = {"H": 0, "X2": 1, "Y2": 2, "T": 3, "CZ": 4, "P0": 5, "P1": 6, "Z": 7}
+
+
+def build(force=False):
+    """Compile oracle.c into liboracle.so with gcc (OpenMP, -O2, portable flags)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-shared", "-fPIC", _SRC, "-o", _SO + ".tmp", "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(_SO + ".tmp", _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        dp = ctypes.POINTER(ctypes.c_double)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        L.or_evolve.argtypes = [ctypes.c_int, i32p, ctypes.c_int, dp, ctypes.c_int]
+        L.or_evolve.restype = None
+        L.or_cut_sum.argtypes = [ctypes.c_int, i32p, ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int,
+                                 ctypes.c_uint64, ctypes.c_uint64, u64p, ctypes.c_int64, u64p,
+                                 ctypes.c_int64, ctypes.c_int, dp]
+        L.or_cut_sum.restype = ctypes.c_int
+        L.or_half_state.argtypes = [ctypes.c_int, i32p, ctypes.c_int, ctypes.c_uint64, dp]
+        L.or_half_state.restype = ctypes.c_int
+        L.or_num_threads.argtypes = []
+        L.or_num_threads.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def num_threads():
+    return lib().or_num_threads()
+
+
+def _encode(gates):
+    """Gate tuples -> int32 [ngates, 3] {code, q1, q2}; cut slots -> codes -1 / -2."""
+    rows = []
+    for g in gates:
+        name = g[1]
+        if name == "CZ":
+            rows.append((CODES["CZ"], g[2], g[3]))
+        elif name == "CUTP":
+            rows.append((-1, g[3], g[2]))
+        elif name == "CUTZ":
+            rows.append((-2, g[3], g[2]))
+        else:
+            rows.append((CODES[name], g[2], 0))
+    a = np.asarray(rows if rows else np.zeros((0, 3)), dtype=np.int32).reshape(-1, 3)
+    return np.ascontiguousarray(a)
+
+
+def _ptr(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def statevector(n, gates):
+    """Uncut state U_{d-1}...U_0 |0...0> (Supplementary A, Eq. 4), gate by gate, FP64."""
+    ops = _encode(gates)
+    psi = np.zeros(1 << n, dtype=np.complex128)
+    lib().or_evolve(n, _ptr(ops, ctypes.c_int32), ops.shape[0], _ptr(psi, ctypes.c_double), 1)
+    return psi
+
+
+def apply_gates(psi, n, gates):
+    """Apply a gate list to an existing complex128 state in place (no re-init)."""
+    ops = _encode(gates)
+    assert psi.dtype == np.complex128 and psi.flags.c_contiguous and psi.size == (1 << n)
+    lib().or_evolve(n, _ptr(ops, ctypes.c_int32), ops.shape[0], _ptr(psi, ctypes.c_double), 0)
+    return psi
+
+
+def half_state(plan, half, k):
+    """Half-state of copy k: half 0 = upper (P_l slots), half 1 = lower (Z^l slots)."""
+    n_h = plan.n_u if half == 0 else plan.n_l
+    tmpl = _encode(plan.upper if half == 0 else plan.lower)
+    psi = np.zeros(1 << n_h, dtype=np.complex128)
+    rc = lib().or_half_state(n_h, _ptr(tmpl, ctypes.c_int32), tmpl.shape[0], k,
+                             _ptr(psi, ctypes.c_double))
+    assert rc == 0
+    return psi
+
+
+def cut_amplitudes(plan, sel_u=None, sel_l=None, k_begin=0, k_end=None, out=None):
+    """Section 2.1 / Supplementary A, Eq. 8: A(x_u, x_l) = sum_k U_k[x_u] L_k[x_l].
+
+    Returns a complex128 array [len(sel_l), len(sel_u)] (row = lower index); with no
+    selection it is the full vector in index order x = x_u + 2^{n_u} x_l.  A copy
+    range gives the partial sum over those copies; ``out`` accumulates into an
+    existing array.
+    """
+    if sel_u is None:
+        sel_u = np.arange(1 << plan.n_u, dtype=np.uint64)
+    if sel_l is None:
+        sel_l = np.arange(1 << plan.n_l, dtype=np.uint64)
+    sel_u = np.ascontiguousarray(sel_u, dtype=np.uint64)
+    sel_l = np.ascontiguousarray(sel_l, dtype=np.uint64)
+    if k_end is None:
+        k_end = plan.copies
+    acc = 1
+    if out is None:
+        out = np.zeros((sel_l.size, sel_u.size), dtype=np.complex128)
+        acc = 0
+    up = _encode(plan.upper)
+    lo = _encode(plan.lower)
+    rc = lib().or_cut_sum(plan.n_u, _ptr(up, ctypes.c_int32), up.shape[0],
+                          plan.n_l, _ptr(lo, ctypes.c_int32), lo.shape[0],
+                          k_begin, k_end, _ptr(sel_u, ctypes.c_uint64), sel_u.size,
+                          _ptr(sel_l, ctypes.c_uint64), sel_l.size, acc,
+                          _ptr(out, ctypes.c_double))
+    assert rc == 0
+    return out
+
+
+def floyd_select(rng, universe, count):
+    """Floyd's algorithm: `count` distinct values of [0, universe), sorted ascending.
+
+    For j = universe-count .. universe-1: t = draw mod (j+1); insert t unless it is
+    already chosen, else insert j.  One splitmix64 draw per j.
+    """
+    if count >= universe:
+        return np.arange(universe, dtype=np.uint64)
+    chosen = set()
+    for j in range(universe - count, universe):
+        t = rng.next() % (j + 1)
+        chosen.add(j if t in chosen else t)
+    return np.array(sorted(chosen), dtype=np.uint64)
+
+
+def select(n_u_qubits, n_sel_u, n_l_qubits, n_sel_l, seed):
+    """The amplitude selection of Section 3 ("sampling" of components): distinct
+    upper bitstrings first, then distinct lower ones, from one splitmix64(seed)."""
+    rng = SplitMix64(seed)
+    su = floyd_select(rng, 1 << n_u_qubits, n_sel_u)
+    sl = floyd_select(rng, 1 << n_l_qubits, n_sel_l)
+    return su, sl
+
+
+KS_BINS = 4096
+KS_ZMIN = -24.0
+KS_ZMAX = 8.0
+
+
+def gumbel_cdf(z):
+    """CDF of Eq. 7 with alpha = 1: integral of exp(z - e^z) = 1 - exp(-e^z)."""
+    return 1.0 - np.exp(-np.exp(z))
+
+
+def stats(amps, n_qubits):
+    """Section 3 statistics over a block of amplitudes, FP64:
+    [sum |A|^2, mean 2^n|A|^2, mean ln(2^n|A|^2), binned KS distance to Eq. 7].
+
+    The KS distance is taken over KS_BINS equal bins of z = ln(2^n |A|^2) on
+    [KS_ZMIN, KS_ZMAX] (values outside are clamped to the end bins): the largest
+    gap between the empirical and the Eq. 7 CDF at the bin edges.
+    """
+    a = np.asarray(amps).astype(np.complex128).ravel()
+    p = (a.real * a.real + a.imag * a.imag)
+    scale = math.ldexp(1.0, n_qubits)
+    norm = float(p.sum())
+    w = p * scale
+    mean_w = float(w.mean())
+    with np.errstate(divide="ignore"):
+        z = np.log(w)
+    finite = np.isfinite(z)
+    mean_ln = float(z[finite].mean()) if finite.any() else float("-inf")
+    zc = np.where(finite, z, KS_ZMIN)
+    idx = np.floor((zc - KS_ZMIN) * (KS_BINS / (KS_ZMAX - KS_ZMIN))).astype(np.int64)
+    idx = np.clip(idx, 0, KS_BINS - 1)
+    hist = np.bincount(idx, minlength=KS_BINS)
+    ks = ks_from_hist(hist)
+    return np.array([norm, mean_w, mean_ln, ks]), hist
+
+
+def ks_from_hist(hist):
+    hist = np.asarray(hist, dtype=np.float64)
+    tot = hist.sum()
+    if tot == 0:
+        return 0.0
+    edges = KS_ZMIN + (KS_ZMAX - KS_ZMIN) * np.arange(1, KS_BINS + 1) / KS_BINS
+    emp = np.cumsum(hist) / tot
+    theo = gumbel_cdf(edges)
+    theo[-1] = 1.0  # the last bin absorbs everything above KS_ZMAX
+    return float(np.max(np.abs(emp - theo)))
