@@ -1,0 +1,232 @@
+/*
+ * libsim: GB300 (sm_103a) implementation of the cut-CZ partition scheme of
+ * "64-qubit quantum circuit simulation" (Chen, Zhou, Xue, Yang, Guo, Guo;
+ * arXiv 1802.06952).
+ *
+ * Every CZ that crosses the cut between the upper and lower half of a grid is
+ * rewritten as P0 (x) I + P1 (x) Z (Section 2.1, Eq. 1), which turns the circuit
+ * into 2^c copies of two unentangled half-circuits (Supplementary A, Eqs. 6-8).
+ * The library evolves the half-circuit state vectors on the GPU and rebuilds
+ * amplitudes as the complex contraction over the copy index
+ *     A(x_u, x_l) = sum_k U_k[x_u] * L_k[x_l]          (Supplementary A, Eq. 8).
+ *
+ * Conventions
+ *   - Qubit q of an R x C grid is row q / C, column q % C.  The cut lies between
+ *     rows b-1 and b: the upper half holds qubits 0 .. b*C-1, the lower half the
+ *     rest.  A full index is x = x_u + 2^{n_u} * x_l and qubit q is bit q.
+ *   - Copy k = sum_m l_m 2^m, the cut CZs m numbered by (layer, upper qubit).
+ *     Copy k applies P_{l_m} to the upper endpoint and Z^{l_m} to the lower one.
+ *   - Amplitude blocks are row-major [n_sel_l][n_sel_u]:
+ *       out[i_l * n_sel_u + i_u] = A(sel_u[i_u], sel_l[i_l]).
+ *     Without a selection this is the full state vector in index order.
+ *
+ * Errors: every function returns SIM_OK or an error code and never throws or
+ * aborts.  sim_last_error() gives a description of the last error raised on the
+ * calling thread.  Functions taking a stream only enqueue work on it; device-side
+ * failures (a wait that gave up) are reported by sim_status().
+ *
+ * Ownership: handles and the device buffers they hold belong to the library and
+ * are released by the matching sim_destroy_* call.  Selection and output buffers
+ * belong to the caller.  Streams are cudaStream_t values passed as void*; NULL is
+ * the legacy default stream.
+ */
+#ifndef LIBSIM_SIM_H
+#define LIBSIM_SIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+  SIM_OK = 0,
+  SIM_EINVAL = 1,        /* invalid argument */
+  SIM_ENOMEM = 2,        /* host or device allocation failed */
+  SIM_ECUDA = 3,         /* a CUDA runtime or driver call failed */
+  SIM_ETIMEOUT = 4,      /* a device-side wait gave up (see sim_status) */
+  SIM_EUNSUPPORTED = 5   /* request outside what this build handles */
+};
+
+/* Half-state precision for sim_evolve_halves. */
+enum {
+  SIM_C64 = 0,        /* complex64 states, fused multi-gate sweeps, shared prefixes */
+  SIM_C128_PLAIN = 1  /* complex128 states, one pass per non-diagonal gate plus one
+                         combined diagonal pass per layer (Section 2.4), every copy
+                         evolved on its own (Section 2.3.1) */
+};
+
+/* Contraction for sim_amplitudes. */
+enum {
+  SIM_SPLIT_BF16 = 0,  /* 3-term split bf16 products on tcgen05, fp32 accumulation */
+  SIM_SPLIT_FP16 = 1,  /* 3-term split fp16 (power-of-two pre-scaled) on tcgen05 */
+  SIM_FP64_PLAIN = 2   /* complex128 products and sums on CUDA cores */
+};
+
+typedef struct sim_circuit_s* sim_circuit;
+typedef struct sim_cut_s* sim_cut_plan;
+typedef struct sim_halves_s* sim_halves;
+
+/* Circuit description for sim_build_circuit.
+ *   rows, cols   grid shape R x C (R*C <= 64)
+ *   depth        number of layers; layer 0 is H on every qubit, layer t >= 1 uses
+ *                CZ pattern ((t-1) mod 8) + 1 (Supplementary A, Eq. 3 circuit model)
+ *   seed         splitmix64 seed of the X^1/2 / Y^1/2 draws
+ *   cut_row      b, the row the CZ patterns 7 and 8 straddle (0 => rows / 2)
+ *   gate_list    optional canonical gate-list text ("circuit R C depth seed" then
+ *                one "t NAME q [q2]" line per gate, NAME in H X2 Y2 T CZ); when not
+ *                NULL it replaces the generator. */
+typedef struct {
+  int rows, cols, depth;
+  uint64_t seed;
+  int cut_row;
+  const char* gate_list;
+} sim_circuit_desc;
+
+/* Tuning knobs; pass NULL for defaults.  Zero fields mean "choose automatically".
+ *   fuse_qubits    local qubits staged per thread block in a fused sweep (4..13)
+ *   sweep_threads  threads per sweep block (64..1024, multiple of 32)
+ *   gemm_group_m   m-blocks per raster group of the persistent contraction */
+typedef struct {
+  int fuse_qubits;
+  int sweep_threads;
+  int gemm_group_m;
+  int reserved[5];
+} sim_opts;
+
+/* Build a circuit (Supplementary A, Eq. 3 circuit model; gate rules of the random
+ * grid circuits the paper simulates, Section 3).  Host only.
+ * Returns SIM_EINVAL for bad shapes or a malformed gate list. */
+int sim_build_circuit(const sim_circuit_desc* desc, sim_circuit* out);
+
+/* Number of qubits, layers and gates of a circuit.  Host only. */
+int sim_circuit_info(sim_circuit circ, int* n_qubits, int* depth, int* n_gates);
+
+/* Canonical gate-list text of the circuit (same format as desc->gate_list).
+ * Writes at most cap bytes including the terminating NUL; *len_out receives the
+ * full length without the NUL (call with cap = 0 to size the buffer).  Host only. */
+int sim_circuit_text(sim_circuit circ, char* buf, size_t cap, size_t* len_out);
+
+/* Cut the circuit between rows cut_row-1 and cut_row (Section 2.1; Supplementary A,
+ * Eqs. 6-8): find E_int, number the cut CZs, split the gates into two half-circuits,
+ * build the copy tree (one level per layer holding cuts) and the fused pass
+ * schedule.  Outputs (any may be NULL): c, 2^c, qubits per half.  Host only.
+ * SIM_EUNSUPPORTED if a non-CZ gate crosses the cut or a half exceeds 32 qubits. */
+int sim_cut(sim_circuit circ, int cut_row, sim_cut_plan* out, int* c_out,
+            uint64_t* copies_out, int* n_upper_out, int* n_lower_out);
+
+/* The cut list as int32 triples {layer, upper qubit, lower qubit}, ordered by copy
+ * bit m (3*c values).  *n_equiv_out (may be NULL) receives N_e of Section 3:
+ * qubits per half + log2(number of half-circuits).  Host only. */
+int sim_cut_list(sim_cut_plan plan, int32_t* cuts_out, int* n_equiv_out);
+
+/* Fused-pass schedule summary of one half (0 upper, 1 lower) for complex64 sweeps:
+ * number of copy-tree levels, number of fused passes summed over levels, and the
+ * number of plain passes the Section 2.4 scheme would need for one copy (one per
+ * non-diagonal gate plus one per layer holding diagonal gates).  Host only. */
+int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passes,
+                      int* plain_passes);
+
+/* Evolve both half-circuits of copies [copy_begin, copy_end) on the GPU
+ * (Supplementary A, Eqs. 4-5 per half; diagonal gates combined per Section 2.4).
+ *   precision    SIM_C64 or SIM_C128_PLAIN
+ *   sel_u, n_u   host array of n_u distinct upper indices < 2^{n_upper}, or NULL
+ *                for all of them in order (n_u is then ignored)
+ *   sel_l, n_l   the same for the lower half
+ *   stream       cudaStream_t on which the work is enqueued
+ * The returned handle keeps, for every copy in the range, the selected entries of
+ * both leaf half-states (complex64 or complex128) for sim_amplitudes.
+ * SIM_ENOMEM if the device cannot hold them. */
+int sim_evolve_halves(sim_cut_plan plan, int precision, uint64_t copy_begin,
+                      uint64_t copy_end, const uint64_t* sel_u, uint64_t n_u,
+                      const uint64_t* sel_l, uint64_t n_l, const sim_opts* opts,
+                      void* stream, sim_halves* out);
+
+/* Copy the selected entries of one leaf half-state (half 0 upper, 1 lower) of copy
+ * `copy` (absolute copy index inside the evolved range) into out_dev, a device
+ * buffer of n_sel elements of the halves' precision (complex64 or complex128). */
+int sim_halves_leaf(sim_halves h, int half, uint64_t copy, void* out_dev, void* stream);
+
+/* Contract the halves over the copy index (Supplementary A, Eq. 8):
+ *   out[i_l * n_u + i_u] (+)= sum_k U_k[sel_u[i_u]] * L_k[sel_l[i_l]]
+ *   contraction  SIM_SPLIT_BF16 / SIM_SPLIT_FP16 (complex64 halves, complex64 out)
+ *                or SIM_FP64_PLAIN (complex64 or complex128 halves, complex128 out)
+ *   accumulate   0: overwrite out; 1: add into out (sums over copy batches)
+ *   out          caller-owned buffer of n_l * n_u complex values, device memory or
+ *                host memory (a host buffer is filled through a device staging
+ *                buffer; the call then returns after the copy has finished). */
+int sim_amplitudes(sim_halves h, int contraction, int accumulate, void* out, void* stream);
+
+/* FP64 statistics of an amplitude block (Section 3, Eq. 7 with alpha = 1):
+ * stats_out = {sum |A|^2, mean 2^n|A|^2, mean ln(2^n|A|^2) over non-zero entries,
+ * binned KS distance between z = ln(2^n|A|^2) and Eq. 7}.  amps is device memory,
+ * complex64 (is_c128 = 0) or complex128 (is_c128 = 1).  hist_out (may be NULL)
+ * receives SIM_KS_BINS counts of z over [SIM_KS_ZMIN, SIM_KS_ZMAX), end bins
+ * clamped.  Synchronises the stream. */
+#define SIM_KS_BINS 4096
+#define SIM_KS_ZMIN (-24.0)
+#define SIM_KS_ZMAX (8.0)
+int sim_stats(const void* amps, int is_c128, uint64_t count, int n_qubits,
+              double stats_out[4], uint64_t* hist_out, void* stream);
+
+/* Draw the amplitude selection used by sim_sample (Section 3: "sampling" of state
+ * components): n_u distinct upper indices of [0, 2^{nq_u}), then n_l distinct lower
+ * indices of [0, 2^{nq_l}), each set by Floyd's algorithm from one splitmix64(seed)
+ * stream (draw t = next() mod (j+1)) and sorted ascending.  n >= 2^nq gives all
+ * indices.  Host only; outputs are caller-owned host arrays. */
+int sim_select(int nq_u, uint64_t n_u, int nq_l, uint64_t n_l, uint64_t seed,
+               uint64_t* sel_u_out, uint64_t* sel_l_out);
+
+/* Selection + evolution + split-bf16 contraction + statistics in one call:
+ * draws the selection (sim_select), evolves all copies in complex64, writes the
+ * [n_l][n_u] complex64 block to amps_dev_out (caller-owned device memory) and the
+ * statistics to stats_out (may be NULL).  Synchronises the stream. */
+int sim_sample(sim_cut_plan plan, uint64_t n_u, uint64_t n_l, uint64_t seed,
+               uint64_t* sel_u_out, uint64_t* sel_l_out, void* amps_dev_out,
+               double stats_out[4], const sim_opts* opts, void* stream);
+
+/* Synchronise the stream and report device-side failures recorded since the last
+ * call: SIM_ETIMEOUT if a kernel's bounded wait gave up, SIM_ECUDA on a CUDA error. */
+int sim_status(void* stream);
+
+/* Release cached device memory held by the library's pool. */
+int sim_release_cache(void);
+
+/* Phase profiler.  While enabled, every library call that launches kernels records
+ * a CUDA event pair around each phase on the stream it launches on, and counts the
+ * kernels it launches and the bytes it copies between host and device.
+ * sim_profile_read synchronises the recorded events and returns, per phase, the
+ * summed device milliseconds, the number of phase instances (event pairs) and the
+ * number of kernel launches; bytes_out (may be NULL) receives {host->device,
+ * device->host} bytes.  reset != 0 clears all counters afterwards. */
+enum {
+  SIM_PHASE_SWEEP = 0,     /* fused complex64 gate sweeps of the copy tree */
+  SIM_PHASE_GATHER = 1,    /* selection gather of leaf states */
+  SIM_PHASE_PLAIN = 2,     /* plain complex128 per-gate passes */
+  SIM_PHASE_PACK = 3,      /* split-pack of the contraction operands */
+  SIM_PHASE_CONTRACT = 4,  /* tcgen05 split contraction */
+  SIM_PHASE_FP64_GEMM = 5, /* plain FP64 contraction */
+  SIM_PHASE_STATS = 6,     /* FP64 statistics */
+  SIM_NUM_PHASES = 7
+};
+int sim_profile_enable(int on);
+int sim_profile_read(double* ms_out, uint64_t* instances_out, uint64_t* launches_out,
+                     uint64_t* bytes_out, int reset);
+
+void sim_destroy_circuit(sim_circuit circ);
+void sim_destroy_cut(sim_cut_plan plan);
+void sim_destroy_halves(sim_halves h);
+
+/* Description of the last error on the calling thread ("" if none). */
+const char* sim_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int sim_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBSIM_SIM_H */

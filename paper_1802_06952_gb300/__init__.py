@@ -1,0 +1,277 @@
+"""Python binding of libsim, the GB300 (sm_103a) implementation of the cut-CZ
+partition scheme of arXiv 1802.06952 (Section 2.1, Eq. 1; Supplementary A, Eqs. 6-8).
+
+Argument marshalling only: every step of the computation runs in libsim.so
+(CUDA kernels and the C++ host logic behind include/sim.h).  The functions keep
+the C names.  Device buffers are torch tensors (their data_ptr is passed through)
+and streams are torch.cuda.Stream objects or raw cudaStream_t integers.  If the
+shared library is missing, importing works but every call raises: there is no
+fallback implementation.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsim.so")
+
+SIM_OK, SIM_EINVAL, SIM_ENOMEM, SIM_ECUDA, SIM_ETIMEOUT, SIM_EUNSUPPORTED = range(6)
+SIM_C64, SIM_C128_PLAIN = 0, 1
+SIM_SPLIT_BF16, SIM_SPLIT_FP16, SIM_FP64_PLAIN = 0, 1, 2
+SIM_KS_BINS = 4096
+(SIM_PHASE_SWEEP, SIM_PHASE_GATHER, SIM_PHASE_PLAIN, SIM_PHASE_PACK, SIM_PHASE_CONTRACT,
+ SIM_PHASE_FP64_GEMM, SIM_PHASE_STATS) = range(7)
+SIM_NUM_PHASES = 7
+PHASE_NAMES = ("sweep", "gather", "plain", "pack", "contract", "fp64_gemm", "stats")
+
+# every symbol include/sim.h declares
+EXPORTS = (
+    "sim_build_circuit", "sim_circuit_info", "sim_circuit_text", "sim_cut", "sim_cut_list",
+    "sim_plan_schedule", "sim_evolve_halves", "sim_halves_leaf", "sim_amplitudes", "sim_stats",
+    "sim_select", "sim_sample", "sim_status", "sim_release_cache", "sim_destroy_circuit",
+    "sim_destroy_cut", "sim_destroy_halves", "sim_last_error", "sim_version",
+    "sim_profile_enable", "sim_profile_read",
+)
+
+
+class SimError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libsim error %d: %s" % (code, msg))
+        self.code = code
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int), ("cols", ctypes.c_int), ("depth", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("cut_row", ctypes.c_int), ("gate_list", ctypes.c_char_p)]
+
+
+class SimOpts(ctypes.Structure):
+    _fields_ = [("fuse_qubits", ctypes.c_int), ("sweep_threads", ctypes.c_int),
+                ("gemm_group_m", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libsim.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libsim.so is not built; run paper_1802_06952_gb300/build.py "
+                           "(or __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, u64, u64p, i32p = ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_int32)
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "sim_build_circuit": (ctypes.c_int, [ctypes.POINTER(_Desc), ctypes.POINTER(vp)]),
+        "sim_circuit_info": (ctypes.c_int, [vp, ip, ip, ip]),
+        "sim_circuit_text": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+        "sim_cut": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ip, u64p, ip, ip]),
+        "sim_cut_list": (ctypes.c_int, [vp, i32p, ip]),
+        "sim_plan_schedule": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ip]),
+        "sim_evolve_halves": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u64p, u64, u64p, u64,
+                                             ctypes.POINTER(SimOpts), vp, ctypes.POINTER(vp)]),
+        "sim_halves_leaf": (ctypes.c_int, [vp, ctypes.c_int, u64, vp, vp]),
+        "sim_amplitudes": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
+        "sim_stats": (ctypes.c_int, [vp, ctypes.c_int, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                     u64p, vp]),
+        "sim_select": (ctypes.c_int, [ctypes.c_int, u64, ctypes.c_int, u64, u64, u64p, u64p]),
+        "sim_sample": (ctypes.c_int, [vp, u64, u64, u64, u64p, u64p, vp, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(SimOpts), vp]),
+        "sim_status": (ctypes.c_int, [vp]),
+        "sim_release_cache": (ctypes.c_int, []),
+        "sim_destroy_circuit": (None, [vp]),
+        "sim_destroy_cut": (None, [vp]),
+        "sim_destroy_halves": (None, [vp]),
+        "sim_last_error": (ctypes.c_char_p, []),
+        "sim_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+        "sim_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), u64p, u64p, u64p, ctypes.c_int]),
+        "sim_version": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != SIM_OK:
+        raise SimError(rc, lib().sim_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t):
+    return t if isinstance(t, int) else t.data_ptr()
+
+
+def _u64(a):
+    if a is None:
+        return None, 0
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    return a, a.size
+
+
+def _opts(opts):
+    if opts is None:
+        return None
+    if isinstance(opts, SimOpts):
+        return ctypes.byref(opts)
+    o = SimOpts()
+    for k, v in opts.items():
+        setattr(o, k, v)
+    return ctypes.byref(o)
+
+
+# ---------------------------------------------------------------------------
+# C-ABI names
+# ---------------------------------------------------------------------------
+def sim_build_circuit(rows=0, cols=0, depth=0, seed=0, cut_row=0, gate_list=None):
+    d = _Desc(rows, cols, depth, seed, cut_row, gate_list.encode() if gate_list else None)
+    h = ctypes.c_void_p()
+    _check(lib().sim_build_circuit(ctypes.byref(d), ctypes.byref(h)))
+    return h.value
+
+
+def sim_circuit_info(circ):
+    n, d, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().sim_circuit_info(circ, ctypes.byref(n), ctypes.byref(d), ctypes.byref(g)))
+    return n.value, d.value, g.value
+
+
+def sim_circuit_text(circ):
+    ln = ctypes.c_size_t()
+    _check(lib().sim_circuit_text(circ, None, 0, ctypes.byref(ln)))
+    buf = ctypes.create_string_buffer(ln.value + 1)
+    _check(lib().sim_circuit_text(circ, buf, ln.value + 1, ctypes.byref(ln)))
+    return buf.value.decode()
+
+
+def sim_cut(circ, cut_row=0):
+    """Returns (plan, c, copies, n_upper, n_lower)."""
+    p = ctypes.c_void_p()
+    c, nu, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    copies = ctypes.c_uint64()
+    _check(lib().sim_cut(circ, cut_row, ctypes.byref(p), ctypes.byref(c), ctypes.byref(copies),
+                         ctypes.byref(nu), ctypes.byref(nl)))
+    return p.value, c.value, copies.value, nu.value, nl.value
+
+
+def sim_cut_list(plan, c):
+    """Returns (cuts [(layer, upper qubit, lower qubit)], N_e)."""
+    arr = (ctypes.c_int32 * max(3 * c, 1))()
+    ne = ctypes.c_int()
+    _check(lib().sim_cut_list(plan, arr, ctypes.byref(ne)))
+    return [tuple(arr[3 * m:3 * m + 3]) for m in range(c)], ne.value
+
+
+def sim_plan_schedule(plan, half):
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().sim_plan_schedule(plan, half, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def sim_evolve_halves(plan, precision, copy_begin, copy_end, sel_u=None, sel_l=None, opts=None, stream=None):
+    su, nu = _u64(sel_u)
+    sl, nl = _u64(sel_l)
+    P = ctypes.POINTER(ctypes.c_uint64)
+    h = ctypes.c_void_p()
+    _check(lib().sim_evolve_halves(plan, precision, copy_begin, copy_end,
+                                   su.ctypes.data_as(P) if su is not None else None, nu,
+                                   sl.ctypes.data_as(P) if sl is not None else None, nl,
+                                   _opts(opts), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sim_halves_leaf(halves, half, copy, out, stream=None):
+    _check(lib().sim_halves_leaf(halves, half, copy, _ptr(out), _stream(stream)))
+
+
+def sim_amplitudes(halves, contraction, accumulate, out, stream=None):
+    """out: torch tensor (device or host) or a raw pointer."""
+    _check(lib().sim_amplitudes(halves, contraction, int(accumulate), _ptr(out), _stream(stream)))
+
+
+def sim_stats(amps, is_c128, count, n_qubits, stream=None, want_hist=False):
+    st = (ctypes.c_double * 4)()
+    hist = np.zeros(SIM_KS_BINS, dtype=np.uint64) if want_hist else None
+    _check(lib().sim_stats(_ptr(amps), int(is_c128), count, n_qubits, st,
+                           hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if want_hist else None,
+                           _stream(stream)))
+    out = np.array(st[:], dtype=np.float64)
+    return (out, hist) if want_hist else out
+
+
+def sim_select(nq_u, n_u, nq_l, n_l, seed):
+    cu = min(n_u, 1 << nq_u)
+    cl = min(n_l, 1 << nq_l)
+    su = np.zeros(cu, dtype=np.uint64)
+    sl = np.zeros(cl, dtype=np.uint64)
+    P = ctypes.POINTER(ctypes.c_uint64)
+    _check(lib().sim_select(nq_u, n_u, nq_l, n_l, seed, su.ctypes.data_as(P), sl.ctypes.data_as(P)))
+    return su, sl
+
+
+def sim_sample(plan, n_u, n_l, seed, amps_out, nq_u, nq_l, opts=None, stream=None):
+    cu = min(n_u, 1 << nq_u)
+    cl = min(n_l, 1 << nq_l)
+    su = np.zeros(cu, dtype=np.uint64)
+    sl = np.zeros(cl, dtype=np.uint64)
+    st = (ctypes.c_double * 4)()
+    P = ctypes.POINTER(ctypes.c_uint64)
+    _check(lib().sim_sample(plan, n_u, n_l, seed, su.ctypes.data_as(P), sl.ctypes.data_as(P), _ptr(amps_out),
+                            st, _opts(opts), _stream(stream)))
+    return su, sl, np.array(st[:])
+
+
+def sim_status(stream=None):
+    _check(lib().sim_status(_stream(stream)))
+
+
+def sim_release_cache():
+    _check(lib().sim_release_cache())
+
+
+def sim_destroy_circuit(c):
+    lib().sim_destroy_circuit(c)
+
+
+def sim_destroy_cut(p):
+    lib().sim_destroy_cut(p)
+
+
+def sim_destroy_halves(h):
+    lib().sim_destroy_halves(h)
+
+
+def sim_profile_enable(on):
+    _check(lib().sim_profile_enable(int(on)))
+
+
+def sim_profile_read(reset=True):
+    """Returns {"ms": [...], "instances": [...], "launches": [...], "h2d": B, "d2h": B} per phase."""
+    ms = (ctypes.c_double * SIM_NUM_PHASES)()
+    inst = (ctypes.c_uint64 * SIM_NUM_PHASES)()
+    la = (ctypes.c_uint64 * SIM_NUM_PHASES)()
+    by = (ctypes.c_uint64 * 2)()
+    _check(lib().sim_profile_read(ms, inst, la, by, int(reset)))
+    return {"ms": list(ms), "instances": list(inst), "launches": list(la), "h2d": by[0], "d2h": by[1]}
+
+
+def sim_last_error():
+    return lib().sim_last_error().decode()
+
+
+def sim_version():
+    return lib().sim_version()

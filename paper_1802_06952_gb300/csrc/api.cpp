@@ -1,0 +1,974 @@
+// C-ABI of libsim (include/sim.h): error handling, the device memory pool, the
+// copy-tree evolution engine (complex64 fused path and complex128 plain path),
+// the contraction dispatch, statistics and selection.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/sim.h"
+#include "sim_internal.h"
+
+using namespace sim;
+
+struct sim_circuit_s {
+  Circuit c;
+};
+
+struct sim_cut_s {
+  CutPlan p;
+};
+
+struct sim_halves_s {
+  CutPlan* plan = nullptr;
+  int precision = SIM_C64;
+  uint64_t kb = 0, ke = 0;
+  int64_t nsel[2] = {0, 0};
+  bool full[2] = {true, true};
+  void* d_sel[2] = {nullptr, nullptr};
+  void* leafsel[2] = {nullptr, nullptr};  // [K][nsel] complex64 or complex128
+  cudaStream_t stream = nullptr;
+  int device = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess) {                                                           \
+      if (e_ == cudaErrorMemoryAllocation) {                                           \
+        cudaGetLastError();                                                            \
+        return fail(SIM_ENOMEM, std::string(#x) + ": " + cudaGetErrorString(e_));       \
+      }                                                                                \
+      return fail(SIM_ECUDA, std::string(#x) + ": " + cudaGetErrorString(e_));         \
+    }                                                                                  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Device memory pool: cudaMalloc'd blocks cached by (device, rounded size) and
+// reused in stream order.  Sizes are rounded up to 2 MiB above 1 MiB and to a
+// power of two below.
+// ---------------------------------------------------------------------------
+struct Pool {
+  std::mutex mu;
+  std::map<std::pair<int, size_t>, std::vector<void*>> free_blocks;
+  std::unordered_map<void*, std::pair<int, size_t>> owner;
+
+  static size_t round(size_t n) {
+    if (n <= 256) return 256;
+    if (n <= (1u << 20)) {
+      size_t r = 256;
+      while (r < n) r <<= 1;
+      return r;
+    }
+    const size_t g = (size_t)2 << 20;
+    return (n + g - 1) / g * g;
+  }
+
+  cudaError_t alloc(void** p, size_t n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const size_t r = round(n);
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = free_blocks.find({dev, r});
+      if (it != free_blocks.end() && !it->second.empty()) {
+        *p = it->second.back();
+        it->second.pop_back();
+        owner[*p] = {dev, r};
+        return cudaSuccess;
+      }
+    }
+    cudaError_t e = cudaMalloc(p, r);
+    if (e == cudaErrorMemoryAllocation) {
+      cudaGetLastError();
+      release(dev);
+      e = cudaMalloc(p, r);
+    }
+    if (e != cudaSuccess) {
+      *p = nullptr;
+      return e;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    owner[*p] = {dev, r};
+    return cudaSuccess;
+  }
+
+  void free(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = owner.find(p);
+    if (it == owner.end()) return;
+    free_blocks[it->second].push_back(p);
+    owner.erase(it);
+  }
+
+  void release(int dev) {
+    std::lock_guard<std::mutex> lk(mu);
+    for (auto& kv : free_blocks) {
+      if (dev >= 0 && kv.first.first != dev) continue;
+      for (void* p : kv.second) cudaFree(p);
+      kv.second.clear();
+    }
+  }
+};
+
+Pool& pool() {
+  static Pool* p = new Pool();  // never destroyed: the CUDA context may be gone at exit
+  return *p;
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { pool().free(p); }
+  cudaError_t alloc(size_t n) {
+    pool().free(p);
+    p = nullptr;
+    return pool().alloc(&p, n ? n : 1);
+  }
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Phase profiler: CUDA event pairs per phase instance on the launching stream,
+// kernel launch and host<->device byte counters.
+// ---------------------------------------------------------------------------
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  struct Rec {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> spare;
+  double ms[SIM_NUM_PHASES] = {};
+  uint64_t inst[SIM_NUM_PHASES] = {};
+  uint64_t launches[SIM_NUM_PHASES] = {};
+  uint64_t h2d = 0, d2h = 0;
+
+  cudaEvent_t get() {
+    if (!spare.empty()) {
+      cudaEvent_t e = spare.back();
+      spare.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+};
+
+Profiler& prof() {
+  static Profiler* p = new Profiler();
+  return *p;
+}
+
+// Records a begin event at construction and an end event at destruction when
+// the profiler is on.
+struct PhaseScope {
+  int phase;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  PhaseScope(int ph, cudaStream_t s) : phase(ph), st(s) {
+    Profiler& P = prof();
+    std::lock_guard<std::mutex> lk(P.mu);
+    if (!P.on) return;
+    a = P.get();
+    if (a) cudaEventRecord(a, st);
+  }
+  ~PhaseScope() {
+    if (!a) return;
+    Profiler& P = prof();
+    std::lock_guard<std::mutex> lk(P.mu);
+    cudaEvent_t b = P.get();
+    if (!b) return;
+    cudaEventRecord(b, st);
+    P.recs.push_back({phase, a, b});
+  }
+};
+
+// per-device status word of the contraction and other per-device constants
+struct DeviceInfo {
+  int* d_status = nullptr;
+  int num_sms = 0;
+  size_t total_mem = 0;
+};
+
+std::mutex g_dev_mu;
+std::map<int, DeviceInfo> g_dev;
+
+int device_info(DeviceInfo** out) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_dev_mu);
+  DeviceInfo& d = g_dev[dev];
+  if (!d.d_status) {
+    CK(cudaMalloc(&d.d_status, sizeof(int)));
+    CK(cudaMemset(d.d_status, 0, sizeof(int)));
+    CK(cudaDeviceGetAttribute(&d.num_sms, cudaDevAttrMultiProcessorCount, dev));
+    size_t fr = 0;
+    CK(cudaMemGetInfo(&fr, &d.total_mem));
+  }
+  *out = &d;
+  return SIM_OK;
+}
+
+// Op tables of a plan live in pool memory, uploaded on the caller's stream the
+// first time the plan is evolved on a device.
+void free_plan_ops(CutPlan& P) {
+  for (int h = 0; h < 2; ++h) {
+    pool().free(P.d_ops[h]);
+    pool().free(P.d_plain_ops[h]);
+    P.d_ops[h] = P.d_plain_ops[h] = nullptr;
+  }
+  P.device = -1;
+}
+
+int upload_plan_ops(CutPlan& P, cudaStream_t st) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (P.device == dev && P.d_ops[0]) return SIM_OK;
+  free_plan_ops(P);
+  for (int h = 0; h < 2; ++h) {
+    const auto& ops = P.sched[h].ops;
+    void* p = nullptr;
+    CK(pool().alloc(&p, sizeof(OpRec) * (ops.size() + 1)));
+    P.d_ops[h] = (OpRec*)p;
+    if (!ops.empty())
+      CK(cudaMemcpyAsync(P.d_ops[h], ops.data(), sizeof(OpRec) * ops.size(), cudaMemcpyHostToDevice, st));
+    note_bytes(sizeof(OpRec) * ops.size(), 0);
+    std::vector<OpRec>& flat = P.plain_flat[h];
+    flat.clear();
+    P.plain_op_offsets[h].clear();
+    for (const PlainLayer& L : P.plain[h]) {
+      P.plain_op_offsets[h].push_back((int)flat.size());
+      flat.insert(flat.end(), L.gates.begin(), L.gates.end());
+      flat.insert(flat.end(), L.diags.begin(), L.diags.end());
+    }
+    CK(pool().alloc(&p, sizeof(OpRec) * (flat.size() + 1)));
+    P.d_plain_ops[h] = (OpRec*)p;
+    if (!flat.empty())
+      CK(cudaMemcpyAsync(P.d_plain_ops[h], flat.data(), sizeof(OpRec) * flat.size(), cudaMemcpyHostToDevice, st));
+    note_bytes(sizeof(OpRec) * flat.size(), 0);
+  }
+  P.device = dev;
+  return SIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// complex64 copy-tree evolution of one half
+// ---------------------------------------------------------------------------
+struct LaunchRec {
+  int level, pass;      // pass < 0: gather
+  int64_t table_off, nslots;
+  int src_buf, dst_buf; // buffer ids: level index, or -1 = leafsel
+};
+
+struct TreeProgram {
+  std::vector<NodeEntry> table;
+  std::vector<LaunchRec> launches;
+  std::vector<int64_t> level_cap;  // nodes per chunk buffer of each level
+};
+
+struct TreeBuilder {
+  const HalfSchedule& S;
+  uint64_t kb, ke;
+  bool direct;            // leaves written straight into leafsel rows (no selection)
+  std::vector<std::vector<uint64_t>> needed;  // sorted node ids per level
+  TreeProgram& prog;
+
+  std::vector<uint64_t> needed_ids(int j) const {
+    const int bits = S.levels[j].bits_total;
+    std::vector<uint64_t> ids;
+    const uint64_t count = bits >= 63 ? ~0ull : (1ull << bits);
+    if (ke - kb >= count) {
+      ids.resize(count);
+      for (uint64_t i = 0; i < count; ++i) ids[i] = i;
+    } else {
+      ids.reserve(ke - kb);
+      for (uint64_t k = kb; k < ke; ++k) ids.push_back(k & (count - 1));
+      std::sort(ids.begin(), ids.end());
+      ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
+    }
+    return ids;
+  }
+
+  void build() {
+    const int J = (int)S.levels.size();
+    for (int j = 0; j < J; ++j) needed.push_back(needed_ids(j));
+    std::vector<uint64_t> root_ids = needed[0];
+    process(0, root_ids, {});
+  }
+
+  // ids: node ids of level j to run; parent_slot: slot of each id's parent in the
+  // parent level's current chunk buffer (empty at the root)
+  void process(int j, const std::vector<uint64_t>& ids, const std::unordered_map<uint64_t, int64_t>& parent_slot) {
+    const int J = (int)S.levels.size();
+    const Level& L = S.levels[j];
+    const bool leaf = (j == J - 1);
+    const int64_t cap = prog.level_cap[j];
+    for (size_t c0 = 0; c0 < ids.size(); c0 += (size_t)cap) {
+      const size_t c1 = std::min(ids.size(), c0 + (size_t)cap);
+      const int64_t off = (int64_t)prog.table.size();
+      std::unordered_map<uint64_t, int64_t> my_slot;
+      for (size_t i = c0; i < c1; ++i) {
+        NodeEntry e;
+        e.node_id = ids[i];
+        e.parent_slot = 0;
+        if (j > 0) {
+          const uint64_t pmask = L.bits_before >= 63 ? ~0ull : ((1ull << L.bits_before) - 1);
+          e.parent_slot = parent_slot.at(ids[i] & pmask);
+        }
+        e.dst_row = (leaf && direct) ? (int64_t)(ids[i] - kb) : (int64_t)(i - c0);
+        prog.table.push_back(e);
+        my_slot[ids[i]] = (int64_t)(i - c0);
+      }
+      const int64_t ns = (int64_t)(c1 - c0);
+      const int dst = (leaf && direct) ? -1 : j;
+      for (size_t p = 0; p < L.passes.size(); ++p) {
+        LaunchRec r;
+        r.level = j;
+        r.pass = (int)p;
+        r.table_off = off;
+        r.nslots = ns;
+        r.src_buf = (p == 0 && j > 0) ? j - 1 : dst;
+        r.dst_buf = dst;
+        prog.launches.push_back(r);
+      }
+      if (leaf) {
+        if (!direct) {
+          // gather table: rows of leafsel
+          const int64_t goff = (int64_t)prog.table.size();
+          for (size_t i = c0; i < c1; ++i) {
+            NodeEntry e;
+            e.node_id = ids[i];
+            e.parent_slot = 0;
+            e.dst_row = (int64_t)(ids[i] - kb);
+            prog.table.push_back(e);
+          }
+          LaunchRec r;
+          r.level = j;
+          r.pass = -1;
+          r.table_off = goff;
+          r.nslots = ns;
+          r.src_buf = j;
+          r.dst_buf = -1;
+          prog.launches.push_back(r);
+        }
+      } else {
+        const Level& N = S.levels[j + 1];
+        const int nb = N.bits_total - N.bits_before;
+        std::vector<uint64_t> kids;
+        const auto& nxt = needed[j + 1];
+        for (size_t i = c0; i < c1; ++i)
+          for (uint64_t l = 0; l < (1ull << nb); ++l) {
+            const uint64_t cid = ids[i] | (l << N.bits_before);
+            if (std::binary_search(nxt.begin(), nxt.end(), cid)) kids.push_back(cid);
+          }
+        std::sort(kids.begin(), kids.end());
+        process(j + 1, kids, my_slot);
+      }
+    }
+  }
+};
+
+int evolve_c64_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t* d_sel, int64_t nsel, bool full,
+                    void* leafsel, cudaStream_t st, const sim_opts* opts) {
+  const HalfSchedule& S = P.sched[h];
+  const int n = S.n;
+  const size_t state_bytes = sizeof(float) * 2 * ((size_t)1 << n);
+  const int J = (int)S.levels.size();
+  TreeProgram prog;
+  // chunk capacity per level from the free device memory
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  const size_t budget = (size_t)(fr * 0.6);
+  for (int j = 0; j < J; ++j) {
+    const int64_t need_nodes = (int64_t)std::min<uint64_t>(
+        ke - kb, S.levels[j].bits_total >= 63 ? ~0ull : (1ull << S.levels[j].bits_total));
+    int64_t cap = (int64_t)(budget / std::max(1, J) / state_bytes);
+    if (cap < 1) cap = 1;
+    prog.level_cap.push_back(std::min<int64_t>(cap, std::max<int64_t>(need_nodes, 1)));
+  }
+  TreeBuilder tb{S, kb, ke, full, {}, prog};
+  tb.build();
+  // buffers
+  std::vector<DevBuf> lvl(J);
+  for (int j = 0; j < J; ++j) {
+    const bool leaf = (j == J - 1);
+    if (leaf && full) continue;
+    CK(lvl[j].alloc(state_bytes * (size_t)prog.level_cap[j]));
+  }
+  DevBuf table;
+  CK(table.alloc(sizeof(NodeEntry) * (prog.table.size() + 1)));
+  CK(cudaMemcpyAsync(table.p, prog.table.data(), sizeof(NodeEntry) * prog.table.size(), cudaMemcpyHostToDevice, st));
+  note_bytes(sizeof(NodeEntry) * prog.table.size(), 0);
+  const int threads = (opts && opts->sweep_threads > 0) ? opts->sweep_threads : 256;
+  for (const LaunchRec& r : prog.launches) {
+    void* dstp = r.dst_buf < 0 ? leafsel : lvl[r.dst_buf].p;
+    PhaseScope ps(r.pass < 0 ? SIM_PHASE_GATHER : SIM_PHASE_SWEEP, st);
+    if (r.pass < 0) {
+      CK(launch_gather(lvl[r.src_buf].p, n, table.as<NodeEntry>() + r.table_off, r.nslots, d_sel, nsel, leafsel, 0, st));
+      continue;
+    }
+    const PassDesc& pd = S.levels[r.level].passes[r.pass];
+    SweepLaunch sl;
+    sl.n = n;
+    sl.k = pd.k;
+    sl.local_mask = pd.local_mask;
+    sl.ops = P.d_ops[h] + pd.op_begin;
+    sl.op_count = pd.op_count;
+    sl.src = pd.src;
+    sl.nodes = table.as<NodeEntry>() + r.table_off;
+    sl.nslots = r.nslots;
+    sl.src_base = pd.src == SRC_PARENT ? lvl[r.src_buf].p : dstp;
+    sl.dst_base = dstp;
+    sl.threads = threads;
+    CK(launch_sweep_c64(sl, st));
+  }
+  // the pool may hand these buffers to the next call on this stream only after
+  // the launches above have been enqueued, which keeps reuse stream-ordered
+  return SIM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// complex128 plain path of one half: every copy evolved on its own, one pass per
+// non-diagonal gate and one combined diagonal pass per layer (Sections 2.3.1, 2.4)
+// ---------------------------------------------------------------------------
+int evolve_plain_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t* d_sel, int64_t nsel, bool full,
+                      void* leafsel, cudaStream_t st) {
+  const int n = h ? P.n_l : P.n_u;
+  const size_t state_bytes = sizeof(double) * 2 * ((size_t)1 << n);
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  const uint64_t K = ke - kb;
+  uint64_t cap = (uint64_t)(fr * 0.5 / state_bytes);
+  if (cap < 1) cap = 1;
+  const uint64_t batch = std::min(K, cap);
+  DevBuf work, ids, table;
+  if (!full) CK(work.alloc(state_bytes * batch));
+  CK(ids.alloc(sizeof(uint64_t) * batch));
+  CK(table.alloc(sizeof(NodeEntry) * batch));
+  std::vector<uint64_t> hid(batch);
+  std::vector<NodeEntry> htab(batch);
+  PhaseScope ps(SIM_PHASE_PLAIN, st);
+  for (uint64_t k0 = kb; k0 < ke; k0 += batch) {
+    const uint64_t nb = std::min(batch, ke - k0);
+    for (uint64_t i = 0; i < nb; ++i) {
+      hid[i] = k0 + i;
+      htab[i].node_id = k0 + i;
+      htab[i].parent_slot = 0;
+      htab[i].dst_row = (int64_t)(k0 + i - kb);
+    }
+    CK(cudaMemcpyAsync(ids.p, hid.data(), sizeof(uint64_t) * nb, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(table.p, htab.data(), sizeof(NodeEntry) * nb, cudaMemcpyHostToDevice, st));
+    note_bytes((sizeof(uint64_t) + sizeof(NodeEntry)) * nb, 0);
+    void* psi = full ? (void*)((char*)leafsel + (k0 - kb) * state_bytes) : work.p;
+    CK(launch_plain_init_zero(psi, n, (int64_t)nb, st));
+    for (size_t t = 0; t < P.plain[h].size(); ++t) {
+      const PlainLayer& L = P.plain[h][t];
+      const OpRec* base = P.d_plain_ops[h] + P.plain_op_offsets[h][t];
+      for (size_t g = 0; g < L.gates.size(); ++g) {
+        PlainLaunch pl{n, L.gates[g].q, base + g, ids.as<uint64_t>(), (int64_t)nb, psi};
+        CK(launch_plain_gate(pl, st));
+      }
+      for (size_t d = 0; d < L.diags.size(); ++d) {
+        PlainLaunch pl{n, -1, base + L.gates.size() + d, ids.as<uint64_t>(), (int64_t)nb, psi};
+        CK(launch_plain_diag(pl, st));
+      }
+    }
+    if (!full) CK(launch_gather(work.p, n, table.as<NodeEntry>(), (int64_t)nb, d_sel, nsel, leafsel, 1, st));
+    if (k0 + batch < ke) CK(cudaStreamSynchronize(st));  // host arrays are reused
+  }
+  CK(cudaStreamSynchronize(st));
+  return SIM_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int check_device_status(DeviceInfo* di) {
+  int v = 0;
+  CK(cudaMemcpy(&v, di->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v != 0) {
+    CK(cudaMemset(di->d_status, 0, sizeof(int)));
+    char buf[96];
+    snprintf(buf, sizeof buf, "a bounded device wait gave up (code 0x%x)", v);
+    return fail(SIM_ETIMEOUT, buf);
+  }
+  return SIM_OK;
+}
+
+int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cudaStream_t st) {
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return rc;
+  const int64_t M = h->nsel[1], N = h->nsel[0];
+  const int64_t K = (int64_t)(h->ke - h->kb);
+  if (contraction == SIM_FP64_PLAIN) {
+    PhaseScope ps(SIM_PHASE_FP64_GEMM, st);
+    CK(launch_fp64_gemm(h->leafsel[1], h->leafsel[0], h->precision == SIM_C128_PLAIN, K, M, N, accumulate, out, st));
+    return SIM_OK;
+  }
+  if (contraction != SIM_SPLIT_BF16 && contraction != SIM_SPLIT_FP16)
+    return fail(SIM_EINVAL, "unknown contraction");
+  if (h->precision != SIM_C64) return fail(SIM_EINVAL, "split contractions need complex64 halves (SIM_C64)");
+  const int fp16 = contraction == SIM_SPLIT_FP16;
+  const int64_t kpad = ((2 * K + 63) / 64) * 64;
+  const int64_t N2 = 2 * N;
+  DevBuf ahi, alo, bhi, blo, sc;
+  CK(ahi.alloc((size_t)M * kpad * 2));
+  CK(alo.alloc((size_t)M * kpad * 2));
+  CK(bhi.alloc((size_t)N2 * kpad * 2));
+  CK(blo.alloc((size_t)N2 * kpad * 2));
+  const float* sa = nullptr;
+  const float* sb = nullptr;
+  {
+  PhaseScope ps(SIM_PHASE_PACK, st);
+  if (fp16) {
+    CK(sc.alloc(4 * sizeof(float)));
+    CK(launch_absmax_c64(h->leafsel[1], K * M, sc.as<float>(), st));
+    CK(launch_absmax_c64(h->leafsel[0], K * N, sc.as<float>() + 2, st));
+    sa = sc.as<float>() + 1;
+    sb = sc.as<float>() + 3;
+  }
+  CK(launch_pack_a(h->leafsel[1], K, M, kpad, fp16, sa, ahi.p, alo.p, st));
+  CK(launch_pack_b(h->leafsel[0], K, N, kpad, fp16, sb, bhi.p, blo.p, st));
+  }
+  TcGemmArgs g;
+  g.a_hi = ahi.p; g.a_lo = alo.p; g.b_hi = bhi.p; g.b_lo = blo.p;
+  g.M = M; g.N2 = N2; g.kpad = kpad;
+  g.fp16 = fp16;
+  g.scale_a = sa; g.scale_b = sb;
+  g.accumulate = accumulate;
+  g.C = out;
+  g.group_m = 0;
+  g.num_sms = di->num_sms;
+  g.d_status = di->d_status;
+  PhaseScope ps(SIM_PHASE_CONTRACT, st);
+  CK(launch_tc_gemm(g, st));
+  return SIM_OK;
+}
+
+}  // namespace
+
+namespace sim {
+void note_launches(int phase, int count) {
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  if (P.on && phase >= 0 && phase < SIM_NUM_PHASES) P.launches[phase] += (uint64_t)count;
+}
+void note_bytes(uint64_t h2d, uint64_t d2h) {
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  if (P.on) {
+    P.h2d += h2d;
+    P.d2h += d2h;
+  }
+}
+}  // namespace sim
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+#define API_BEGIN try {
+#define API_END                                                          \
+  }                                                                      \
+  catch (const std::bad_alloc&) {                                        \
+    return fail(SIM_ENOMEM, "host allocation failed");                   \
+  }                                                                      \
+  catch (const std::exception& ex) {                                     \
+    return fail(SIM_EINVAL, std::string("internal error: ") + ex.what()); \
+  }                                                                      \
+  catch (...) {                                                          \
+    return fail(SIM_EINVAL, "internal error");                           \
+  }
+
+extern "C" {
+
+const char* sim_last_error(void) { return g_err.c_str(); }
+
+int sim_version(void) { return 100; }
+
+int sim_build_circuit(const sim_circuit_desc* desc, sim_circuit* out) {
+  API_BEGIN
+  if (!desc || !out) return fail(SIM_EINVAL, "desc and out must not be NULL");
+  *out = nullptr;
+  auto* c = new sim_circuit_s();
+  std::string err;
+  if (desc->gate_list)
+    err = parse_circuit(desc->gate_list, c->c);
+  else
+    err = generate_circuit(desc->rows, desc->cols, desc->depth, desc->seed, desc->cut_row, c->c);
+  if (!err.empty()) {
+    delete c;
+    return fail(SIM_EINVAL, err);
+  }
+  *out = c;
+  return SIM_OK;
+  API_END
+}
+
+int sim_circuit_info(sim_circuit circ, int* n_qubits, int* depth, int* n_gates) {
+  if (!circ) return fail(SIM_EINVAL, "NULL circuit");
+  if (n_qubits) *n_qubits = circ->c.n;
+  if (depth) *depth = circ->c.depth;
+  if (n_gates) *n_gates = (int)circ->c.gates.size();
+  return SIM_OK;
+}
+
+int sim_circuit_text(sim_circuit circ, char* buf, size_t cap, size_t* len_out) {
+  API_BEGIN
+  if (!circ) return fail(SIM_EINVAL, "NULL circuit");
+  std::string s = circuit_text(circ->c);
+  if (len_out) *len_out = s.size();
+  if (buf && cap) {
+    size_t n = std::min(cap - 1, s.size());
+    memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return SIM_OK;
+  API_END
+}
+
+int sim_cut(sim_circuit circ, int cut_row, sim_cut_plan* out, int* c_out, uint64_t* copies_out, int* n_upper_out,
+            int* n_lower_out) {
+  API_BEGIN
+  if (!circ || !out) return fail(SIM_EINVAL, "circuit and out must not be NULL");
+  *out = nullptr;
+  auto* p = new sim_cut_s();
+  std::string err = build_cut_plan(circ->c, cut_row, 0, p->p);
+  if (!err.empty()) {
+    delete p;
+    return fail(err.find("at most") != std::string::npos || err.find("more than") != std::string::npos
+                    ? SIM_EUNSUPPORTED
+                    : SIM_EINVAL,
+                err);
+  }
+  if (c_out) *c_out = p->p.c;
+  if (copies_out) *copies_out = 1ull << p->p.c;
+  if (n_upper_out) *n_upper_out = p->p.n_u;
+  if (n_lower_out) *n_lower_out = p->p.n_l;
+  *out = p;
+  return SIM_OK;
+  API_END
+}
+
+int sim_cut_list(sim_cut_plan plan, int32_t* cuts_out, int* n_equiv_out) {
+  if (!plan) return fail(SIM_EINVAL, "NULL plan");
+  const CutPlan& P = plan->p;
+  if (cuts_out)
+    for (int m = 0; m < P.c; ++m) {
+      cuts_out[3 * m] = P.cuts[m].t;
+      cuts_out[3 * m + 1] = P.cuts[m].h;
+      cuts_out[3 * m + 2] = P.cuts[m].k;
+    }
+  if (n_equiv_out) *n_equiv_out = std::max(P.n_u, P.n_l) + P.c + 1;
+  return SIM_OK;
+}
+
+int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passes, int* plain_passes) {
+  if (!plan || half < 0 || half > 1) return fail(SIM_EINVAL, "bad plan or half");
+  const HalfSchedule& S = plan->p.sched[half];
+  int np = 0;
+  for (const Level& L : S.levels) np += (int)L.passes.size();
+  if (levels) *levels = (int)S.levels.size();
+  if (fused_passes) *fused_passes = np;
+  if (plain_passes) *plain_passes = S.plain_passes;
+  return SIM_OK;
+}
+
+int sim_evolve_halves(sim_cut_plan plan, int precision, uint64_t copy_begin, uint64_t copy_end, const uint64_t* sel_u,
+                      uint64_t n_u, const uint64_t* sel_l, uint64_t n_l, const sim_opts* opts, void* stream,
+                      sim_halves* out) {
+  API_BEGIN
+  if (!plan || !out) return fail(SIM_EINVAL, "plan and out must not be NULL");
+  *out = nullptr;
+  CutPlan& P = plan->p;
+  if (precision != SIM_C64 && precision != SIM_C128_PLAIN) return fail(SIM_EINVAL, "unknown precision");
+  const uint64_t copies = 1ull << P.c;
+  if (copy_begin >= copy_end || copy_end > copies) return fail(SIM_EINVAL, "copy range must satisfy begin < end <= 2^c");
+  if (opts && opts->fuse_qubits && opts->fuse_qubits != P.fuse_qubits) {
+    CutPlan np;
+    std::string err = build_cut_plan(P.circ, P.circ.cut_row ? (P.n_u / P.circ.C) : 0, opts->fuse_qubits, np);
+    if (!err.empty()) return fail(SIM_EINVAL, err);
+    free_plan_ops(P);
+    P = np;
+  }
+  if (opts && opts->sweep_threads && (opts->sweep_threads < 64 || opts->sweep_threads > 256 || opts->sweep_threads % 32))
+    return fail(SIM_EINVAL, "sweep_threads must be a multiple of 32 in 64..256");
+  const uint64_t* sels[2] = {sel_u, sel_l};
+  const uint64_t nreq[2] = {n_u, n_l};
+  const int nq[2] = {P.n_u, P.n_l};
+  for (int hh = 0; hh < 2; ++hh) {
+    if (sels[hh]) {
+      if (nreq[hh] == 0) return fail(SIM_EINVAL, "empty selection");
+      for (uint64_t i = 0; i < nreq[hh]; ++i)
+        if (sels[hh][i] >> nq[hh]) return fail(SIM_EINVAL, "selected index out of range for its half");
+    }
+  }
+  int rc = upload_plan_ops(P, (cudaStream_t)stream);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto* h = new sim_halves_s();
+  h->plan = &P;
+  h->precision = precision;
+  h->kb = copy_begin;
+  h->ke = copy_end;
+  h->stream = st;
+  CK(cudaGetDevice(&h->device));
+  const uint64_t K = copy_end - copy_begin;
+  const size_t esz = precision == SIM_C64 ? 8 : 16;
+  auto cleanup = [&]() { sim_destroy_halves(h); };
+  for (int hh = 0; hh < 2; ++hh) {
+    h->full[hh] = sels[hh] == nullptr;
+    h->nsel[hh] = h->full[hh] ? (int64_t)1 << nq[hh] : (int64_t)nreq[hh];
+    const size_t bytes = esz * (size_t)K * (size_t)h->nsel[hh];
+    cudaError_t e = pool().alloc(&h->leafsel[hh], bytes);
+    if (e != cudaSuccess) {
+      cleanup();
+      return fail(e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA,
+                  "cannot allocate the leaf buffers of the evolved halves");
+    }
+    if (!h->full[hh]) {
+      e = pool().alloc(&h->d_sel[hh], sizeof(uint64_t) * h->nsel[hh]);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->d_sel[hh], sels[hh], sizeof(uint64_t) * h->nsel[hh], cudaMemcpyHostToDevice, st);
+      note_bytes(sizeof(uint64_t) * h->nsel[hh], 0);
+      if (e != cudaSuccess) {
+        cleanup();
+        return fail(SIM_ECUDA, std::string("selection upload: ") + cudaGetErrorString(e));
+      }
+    }
+  }
+  for (int hh = 0; hh < 2; ++hh) {
+    int r = precision == SIM_C64
+                ? evolve_c64_half(P, hh, copy_begin, copy_end, (const uint64_t*)h->d_sel[hh], h->nsel[hh],
+                                  h->full[hh], h->leafsel[hh], st, opts)
+                : evolve_plain_half(P, hh, copy_begin, copy_end, (const uint64_t*)h->d_sel[hh], h->nsel[hh],
+                                    h->full[hh], h->leafsel[hh], st);
+    if (r) {
+      std::string keep = g_err;
+      cleanup();
+      return fail(r, keep);
+    }
+  }
+  *out = h;
+  return SIM_OK;
+  API_END
+}
+
+int sim_halves_leaf(sim_halves h, int half, uint64_t copy, void* out_dev, void* stream) {
+  API_BEGIN
+  if (!h || half < 0 || half > 1 || !out_dev) return fail(SIM_EINVAL, "bad arguments");
+  if (copy < h->kb || copy >= h->ke) return fail(SIM_EINVAL, "copy outside the evolved range");
+  const size_t esz = h->precision == SIM_C64 ? 8 : 16;
+  const size_t bytes = esz * (size_t)h->nsel[half];
+  CK(cudaMemcpyAsync(out_dev, (const char*)h->leafsel[half] + (copy - h->kb) * bytes, bytes, cudaMemcpyDeviceToDevice,
+                     (cudaStream_t)stream));
+  return SIM_OK;
+  API_END
+}
+
+int sim_amplitudes(sim_halves h, int contraction, int accumulate, void* out, void* stream) {
+  API_BEGIN
+  if (!h || !out) return fail(SIM_EINVAL, "halves and out must not be NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (is_device_ptr(out)) return amplitudes_impl(h, contraction, accumulate, out, st);
+  // host output: compute into a device staging buffer, copy back, wait
+  const size_t esz = contraction == SIM_FP64_PLAIN ? 16 : 8;
+  const size_t bytes = esz * (size_t)h->nsel[0] * (size_t)h->nsel[1];
+  DevBuf stage;
+  CK(stage.alloc(bytes));
+  if (accumulate) CK(cudaMemcpyAsync(stage.p, out, bytes, cudaMemcpyHostToDevice, st));
+  note_bytes(accumulate ? bytes : 0, bytes);
+  int rc = amplitudes_impl(h, contraction, accumulate, stage.p, st);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(out, stage.p, bytes, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return SIM_OK;
+  API_END
+}
+
+int sim_stats(const void* amps, int is_c128, uint64_t count, int n_qubits, double stats_out[4], uint64_t* hist_out,
+              void* stream) {
+  API_BEGIN
+  if (!amps || !stats_out) return fail(SIM_EINVAL, "amps and stats_out must not be NULL");
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf acc, hist;
+  CK(acc.alloc(4 * sizeof(double)));
+  CK(hist.alloc(SIM_KS_BINS * sizeof(unsigned long long)));
+  {
+    PhaseScope ps(SIM_PHASE_STATS, st);
+    CK(launch_stats(amps, is_c128, count, n_qubits, acc.as<double>(), hist.as<unsigned long long>(), st));
+  }
+  note_bytes(0, 3 * sizeof(double) + SIM_KS_BINS * sizeof(unsigned long long));
+  double a[3];
+  std::vector<unsigned long long> hh(SIM_KS_BINS);
+  CK(cudaMemcpyAsync(a, acc.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hh.data(), hist.p, SIM_KS_BINS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  stats_out[0] = a[0];
+  stats_out[1] = count ? a[0] * std::ldexp(1.0, n_qubits) / (double)count : 0.0;
+  stats_out[2] = a[2] > 0 ? a[1] / a[2] : -INFINITY;
+  // KS distance to Eq. 7 (alpha = 1): F(z) = 1 - exp(-e^z) at the bin edges
+  double tot = 0;
+  for (auto v : hh) tot += (double)v;
+  double ks = 0, cum = 0;
+  for (int b = 0; b < SIM_KS_BINS; ++b) {
+    cum += (double)hh[b];
+    const double edge = SIM_KS_ZMIN + (SIM_KS_ZMAX - SIM_KS_ZMIN) * (double)(b + 1) / SIM_KS_BINS;
+    const double F = b == SIM_KS_BINS - 1 ? 1.0 : 1.0 - std::exp(-std::exp(edge));
+    if (tot > 0) ks = std::max(ks, std::fabs(cum / tot - F));
+  }
+  stats_out[3] = ks;
+  if (hist_out)
+    for (int b = 0; b < SIM_KS_BINS; ++b) hist_out[b] = hh[b];
+  return SIM_OK;
+  API_END
+}
+
+int sim_select(int nq_u, uint64_t n_u, int nq_l, uint64_t n_l, uint64_t seed, uint64_t* sel_u_out,
+               uint64_t* sel_l_out) {
+  API_BEGIN
+  if (nq_u < 0 || nq_u > 40 || nq_l < 0 || nq_l > 40) return fail(SIM_EINVAL, "qubit counts must be in 0..40");
+  if (!sel_u_out || !sel_l_out) return fail(SIM_EINVAL, "outputs must not be NULL");
+  uint64_t state = seed;
+  std::vector<uint64_t> a, b;
+  select_indices(nq_u, n_u, state, a);
+  select_indices(nq_l, n_l, state, b);
+  std::copy(a.begin(), a.end(), sel_u_out);
+  std::copy(b.begin(), b.end(), sel_l_out);
+  return SIM_OK;
+  API_END
+}
+
+int sim_sample(sim_cut_plan plan, uint64_t n_u, uint64_t n_l, uint64_t seed, uint64_t* sel_u_out, uint64_t* sel_l_out,
+               void* amps_dev_out, double stats_out[4], const sim_opts* opts, void* stream) {
+  API_BEGIN
+  if (!plan || !sel_u_out || !sel_l_out || !amps_dev_out) return fail(SIM_EINVAL, "NULL argument");
+  CutPlan& P = plan->p;
+  const uint64_t uu = std::min<uint64_t>(n_u, 1ull << P.n_u), ll = std::min<uint64_t>(n_l, 1ull << P.n_l);
+  int rc = sim_select(P.n_u, uu, P.n_l, ll, seed, sel_u_out, sel_l_out);
+  if (rc) return rc;
+  sim_halves h = nullptr;
+  rc = sim_evolve_halves(plan, SIM_C64, 0, 1ull << P.c, sel_u_out, uu, sel_l_out, ll, opts, stream, &h);
+  if (rc) return rc;
+  rc = sim_amplitudes(h, SIM_SPLIT_BF16, 0, amps_dev_out, stream);
+  if (rc == SIM_OK && stats_out) rc = sim_stats(amps_dev_out, 0, uu * ll, P.circ.n, stats_out, nullptr, stream);
+  sim_destroy_halves(h);
+  if (rc) return rc;
+  return sim_status(stream);
+  API_END
+}
+
+int sim_status(void* stream) {
+  API_BEGIN
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  CK(cudaGetLastError());
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return rc;
+  return check_device_status(di);
+  API_END
+}
+
+int sim_release_cache(void) {
+  pool().release(-1);
+  return SIM_OK;
+}
+
+int sim_profile_enable(int on) {
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  P.on = on != 0;
+  return SIM_OK;
+}
+
+int sim_profile_read(double* ms_out, uint64_t* instances_out, uint64_t* launches_out, uint64_t* bytes_out,
+                     int reset) {
+  API_BEGIN
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  for (auto& r : P.recs) {
+    CK(cudaEventSynchronize(r.b));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, r.a, r.b));
+    P.ms[r.phase] += ms;
+    P.inst[r.phase] += 1;
+    P.spare.push_back(r.a);
+    P.spare.push_back(r.b);
+  }
+  P.recs.clear();
+  for (int i = 0; i < SIM_NUM_PHASES; ++i) {
+    if (ms_out) ms_out[i] = P.ms[i];
+    if (instances_out) instances_out[i] = P.inst[i];
+    if (launches_out) launches_out[i] = P.launches[i];
+  }
+  if (bytes_out) {
+    bytes_out[0] = P.h2d;
+    bytes_out[1] = P.d2h;
+  }
+  if (reset) {
+    for (int i = 0; i < SIM_NUM_PHASES; ++i) {
+      P.ms[i] = 0;
+      P.inst[i] = 0;
+      P.launches[i] = 0;
+    }
+    P.h2d = P.d2h = 0;
+  }
+  return SIM_OK;
+  API_END
+}
+
+void sim_destroy_circuit(sim_circuit circ) { delete circ; }
+
+void sim_destroy_cut(sim_cut_plan plan) {
+  if (!plan) return;
+  free_plan_ops(plan->p);
+  delete plan;
+}
+
+void sim_destroy_halves(sim_halves h) {
+  if (!h) return;
+  // buffers go back to the pool for reuse in stream order
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (int i = 0; i < 2; ++i) {
+    pool().free(h->leafsel[i]);
+    pool().free(h->d_sel[i]);
+  }
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,194 @@
+// FP64 parts of the GPU path:
+//   fp64_gemm_kernel  the plain contraction A(x_u, x_l) = sum_k U_k[x_u] L_k[x_l]
+//                     (Supplementary A, Eq. 8) with complex128 products and sums on
+//                     CUDA cores: 64 x 64 output tiles, 256 threads, 4 x 4 outputs each
+//   stats_kernel      the Section 3 statistics of an amplitude block (norm, mean of
+//                     2^n|A|^2, mean of ln 2^n|A|^2, histogram of z = ln 2^n|A|^2 for the
+//                     KS distance to Eq. 7): per-element work in the input precision,
+//                     running sums in FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sim.h"
+#include "sim_internal.h"
+
+namespace sim {
+namespace {
+
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2((double)v.x, (double)v.y); }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+
+constexpr int GT = 64;  // output tile edge
+constexpr int GK = 8;   // copies per smem stage
+
+template <typename T>
+__global__ void __launch_bounds__(256) fp64_gemm_kernel(const T* __restrict__ L, const T* __restrict__ U,
+                                                        int64_t K, int64_t M, int64_t N, int accumulate,
+                                                        double2* __restrict__ C) {
+  __shared__ double2 Ls[GK][GT];
+  __shared__ double2 Us[GK][GT];
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int64_t m0 = (int64_t)blockIdx.y * GT, j0 = (int64_t)blockIdx.x * GT;
+  double2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_double2(0.0, 0.0);
+  for (int64_t k0 = 0; k0 < K; k0 += GK) {
+    for (int t = threadIdx.x; t < GK * GT; t += blockDim.x) {
+      const int kk = t / GT, c = t % GT;
+      const int64_t k = k0 + kk;
+      Ls[kk][c] = (k < K && m0 + c < M) ? to_d2(L[k * M + m0 + c]) : make_double2(0.0, 0.0);
+      Us[kk][c] = (k < K && j0 + c < N) ? to_d2(U[k * N + j0 + c]) : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      double2 a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = Ls[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Us[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          acc[i][j].x = fma(a[i].x, b[j].x, fma(-a[i].y, b[j].y, acc[i][j].x));
+          acc[i][j].y = fma(a[i].x, b[j].y, fma(a[i].y, b[j].x, acc[i][j].y));
+        }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int64_t m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int64_t jj = j0 + tx + 16 * j;
+      if (jj >= N) continue;
+      double2* d = C + m * N + jj;
+      if (accumulate) {
+        double2 o = *d;
+        o.x += acc[i][j].x;
+        o.y += acc[i][j].y;
+        *d = o;
+      } else {
+        *d = acc[i][j];
+      }
+    }
+  }
+}
+
+// bin of z on [SIM_KS_ZMIN, SIM_KS_ZMAX); -inf (a zero amplitude) and anything
+// below go to bin 0, anything above to the last bin
+__device__ __forceinline__ int ks_bin(float z) {
+  const float f = (z - (float)SIM_KS_ZMIN) * ((float)SIM_KS_BINS / (float)(SIM_KS_ZMAX - SIM_KS_ZMIN));
+  if (!(f > 0.f)) return 0;
+  if (f >= (float)SIM_KS_BINS) return SIM_KS_BINS - 1;
+  return (int)f;
+}
+
+__device__ __forceinline__ int ks_bin_d(double z) {
+  const double f = (z - SIM_KS_ZMIN) * ((double)SIM_KS_BINS / (SIM_KS_ZMAX - SIM_KS_ZMIN));
+  if (!(f > 0.0)) return 0;  // includes -inf (zero amplitude) and NaN
+  if (f >= (double)SIM_KS_BINS) return SIM_KS_BINS - 1;
+  return (int)floor(f);
+}
+
+template <bool C128>
+__global__ void __launch_bounds__(256) stats_kernel(const void* amps, uint64_t count, int nq, double* acc,
+                                                    unsigned long long* hist) {
+  __shared__ unsigned int sh[SIM_KS_BINS];
+  for (int i = threadIdx.x; i < SIM_KS_BINS; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  double sp = 0.0, sl = 0.0, nz = 0.0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if (!C128) {
+    const float2* a = (const float2*)amps;
+    const float sc = ldexpf(1.f, nq);
+    float fp = 0.f, fl = 0.f;
+    int cnt = 0, fnz = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += stride) {
+      const float2 v = a[i];
+      const float p = v.x * v.x + v.y * v.y;
+      const float z = logf(p * sc);
+      fp += p;
+      if (p > 0.f) {
+        fl += z;
+        ++fnz;
+      }
+      atomicAdd(&sh[ks_bin(z)], 1u);
+      if (++cnt == 32) {
+        sp += fp; sl += fl; nz += fnz;
+        fp = fl = 0.f;
+        cnt = fnz = 0;
+      }
+    }
+    sp += fp; sl += fl; nz += fnz;
+  } else {
+    const double2* a = (const double2*)amps;
+    const double sc = ldexp(1.0, nq);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += stride) {
+      const double2 v = a[i];
+      const double p = v.x * v.x + v.y * v.y;
+      sp += p;
+      const double z = p > 0.0 ? log(p * sc) : -INFINITY;
+      if (p > 0.0) {
+        sl += z;
+        nz += 1.0;
+      }
+      atomicAdd(&sh[ks_bin_d(z)], 1u);
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sp += __shfl_xor_sync(0xffffffffu, sp, o);
+    sl += __shfl_xor_sync(0xffffffffu, sl, o);
+    nz += __shfl_xor_sync(0xffffffffu, nz, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&acc[0], sp);
+    atomicAdd(&acc[1], sl);
+    atomicAdd(&acc[2], nz);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < SIM_KS_BINS; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], (unsigned long long)sh[i]);
+}
+
+}  // namespace
+
+cudaError_t launch_fp64_gemm(const void* lsel, const void* usel, int in_c128, int64_t K, int64_t M, int64_t N,
+                             int accumulate, void* C, cudaStream_t s) {
+  if (M == 0 || N == 0) return cudaSuccess;
+  const int64_t gx = (N + GT - 1) / GT, gy = (M + GT - 1) / GT;
+  if (gy > 65535) return cudaErrorInvalidValue;
+  dim3 grid((unsigned)gx, (unsigned)gy);
+  if (in_c128)
+    fp64_gemm_kernel<double2><<<grid, 256, 0, s>>>((const double2*)lsel, (const double2*)usel, K, M, N, accumulate,
+                                                   (double2*)C);
+  else
+    fp64_gemm_kernel<float2><<<grid, 256, 0, s>>>((const float2*)lsel, (const float2*)usel, K, M, N, accumulate,
+                                                  (double2*)C);
+  note_launches(SIM_PHASE_FP64_GEMM, 1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const void* amps, int is_c128, uint64_t count, int nq, double* acc_dev,
+                         unsigned long long* hist_dev, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(acc_dev, 0, 3 * sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(hist_dev, 0, SIM_KS_BINS * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  if (count == 0) return cudaSuccess;
+  uint64_t blocks = (count + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  if (is_c128)
+    stats_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(amps, count, nq, acc_dev, hist_dev);
+  else
+    stats_kernel<false><<<(unsigned)blocks, 256, 0, s>>>(amps, count, nq, acc_dev, hist_dev);
+  note_launches(SIM_PHASE_STATS, 1);
+  return cudaGetLastError();
+}
+
+}  // namespace sim

@@ -1,0 +1,475 @@
+// Amplitude contraction on the 5th-generation tensor cores (tcgen05) of sm_103a:
+//   A(x_u, x_l) = sum_k U_k[x_u] L_k[x_l]                (Supplementary A, Eq. 8)
+// as one real GEMM C[M][N2] = sum_seg A_seg[M][kpad] * B_seg[N2][kpad]^T over the
+// three split segments (hi*hi, hi*lo, lo*hi) of pack.cu, fp32 accumulation in
+// tensor memory.  C is fp32 [M][N2] = complex64 [M][N2 / 2].
+//
+// Persistent, warp-specialised kernel, one CTA per SM:
+//   warp 0       TMA producer: 128x64 A tile and 256x64 B tile per stage
+//                (128-byte swizzle, K-major), STAGES-deep ring of mbarriers
+//   warp 1       TMEM allocator and MMA issuer: tcgen05.mma.cta_group::1.kind::f16,
+//                M=128, N=256, K=16, two 256-column fp32 accumulators in TMEM so the
+//                epilogue of one tile overlaps the main loop of the next
+//   warps 2..5   epilogue: tcgen05.ld 32 lanes x 32 columns, output scale, staging
+//                through swizzled shared memory, coalesced streaming stores (or
+//                load-add-store when accumulating)
+// Every mbarrier wait is bounded (about two seconds of global time); a wait that
+// gives up records an error in *d_status and makes every role leave its loop, wait
+// (bounded) for its own copies and MMAs in flight, and release tensor memory.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "../../include/sim.h"
+#include "sim_internal.h"
+
+namespace sim {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 64;            // 64 x 16-bit = 128 bytes: one swizzle row
+constexpr int STAGES = 4;
+constexpr int UMMA_K = 16;
+constexpr int A_BYTES = BM * BK * 2;   // 16 KB
+constexpr int B_BYTES = BN * BK * 2;   // 32 KB
+constexpr int EPI_WARPS = 4;
+constexpr int THREADS = 32 * (2 + EPI_WARPS);
+constexpr int ACC_COLS = BN;           // fp32 accumulator columns per tile
+constexpr int TMEM_COLS = 2 * ACC_COLS;
+constexpr int EPI_BYTES = EPI_WARPS * 32 * 128;  // 32 rows x 32 fp32 per warp
+constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * (A_BYTES + B_BYTES) + EPI_BYTES + 256;
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait for the phase of the given parity to complete.  Returns false if
+// the wait gave up (time limit) or another role raised the abort flag.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 0) {
+      if (*abort_flag) return false;
+      if (global_ns() - t0 > kWaitNs || it > (1u << 30)) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+      "l"(map), "r"(bar), "r"(x), "r"(y)
+      : "memory");
+}
+
+__device__ __forceinline__ void prefetch_map(const CUtensorMap* map) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"(map) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start address >> 4 in bits 0-13,
+// leading byte offset >> 4 in 16-29 (unused for swizzled K-major), stride byte
+// offset >> 4 in 32-45 (1024 B between 8-row groups), fixed 0b001 in 46-48,
+// base offset 0, swizzle mode 2 (128 B) in 61-63.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A and B bf16 (1) or
+// fp16 (0) in bits 7-9 / 10-12, both K-major, N >> 3 in bits 17-22, M >> 4 in 24-28.
+__host__ __device__ constexpr uint32_t instr_desc(bool fp16) {
+  return (1u << 4) | ((fp16 ? 0u : 1u) << 7) | ((fp16 ? 0u : 1u) << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                     uint32_t accum) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TileMap {
+  int64_t num_mb, num_nb;
+  int group;
+  __device__ void tile(int64_t t, int64_t& mb, int64_t& nb) const {
+    const int64_t per_group = (int64_t)group * num_nb;
+    const int64_t g = t / per_group;
+    const int64_t first = g * group;
+    const int64_t gs = (num_mb - first) < group ? (num_mb - first) : group;
+    const int64_t local = t - g * per_group;
+    mb = first + local % gs;
+    nb = local / gs;
+  }
+};
+
+struct KernelArgs {
+  int64_t M, N2;
+  int nkb;               // k-blocks per segment
+  TileMap tm;
+  int64_t num_tiles;
+  const float* scale_a;
+  const float* scale_b;
+  int accumulate;
+  float* C;
+  int vec4;              // C rows 16-byte aligned -> float4 stores
+  int* d_status;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constant__ CUtensorMap mapA_lo,
+                   const __grid_constant__ CUtensorMap mapB_hi, const __grid_constant__ CUtensorMap mapB_lo,
+                   KernelArgs args, uint32_t idesc) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = smem;
+  uint8_t* sB = smem + STAGES * A_BYTES;
+  float* sEpi = (float*)(sB + STAGES * B_BYTES);
+  uint64_t* bars = (uint64_t*)((uint8_t*)sEpi + EPI_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* acc_full = bars + 2 * STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* mma_done = acc_empty + 2;
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32;
+  const int lane = threadIdx.x % 32;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(smem_u32(&acc_full[a]), 1);
+      mbar_init(smem_u32(&acc_empty[a]), EPI_WARPS);
+    }
+    mbar_init(smem_u32(mma_done), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    prefetch_map(&mapA_hi);
+    prefetch_map(&mapA_lo);
+    prefetch_map(&mapB_hi);
+    prefetch_map(&mapB_lo);
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int nkb_total = 3 * args.nkb;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    int issued_parity[STAGES];
+    for (int s = 0; s < STAGES; ++s) issued_parity[s] = -1;
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      for (int64_t t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
+        int64_t mb, nb;
+        args.tm.tile(t, mb, nb);
+        for (int kb = 0; kb < nkb_total; ++kb) {
+          if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          const int seg = kb / args.nkb;
+          const int kx = (kb % args.nkb) * BK;
+          const CUtensorMap* ma = seg == 2 ? &mapA_lo : &mapA_hi;
+          const CUtensorMap* mb_ = seg == 1 ? &mapB_lo : &mapB_hi;
+          const uint32_t fb = smem_u32(&full[stage]);
+          mbar_arrive_expect_tx(fb, A_BYTES + B_BYTES);
+          tma_load_2d(smem_u32(sA + stage * A_BYTES), ma, fb, kx, (int)(mb * BM));
+          tma_load_2d(smem_u32(sB + stage * B_BYTES), mb_, fb, kx, (int)(nb * BN));
+          issued_parity[stage] = (int)phase;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (!ok) {
+        if (args.d_status) atomicExch(args.d_status, SIM_TIMEOUT_CODE_TMA);
+        *abort_flag = 1;
+      }
+      // drain: every load this thread issued has landed before the CTA exits
+      volatile int dummy = 0;
+      for (int s = 0; s < STAGES; ++s)
+        if (issued_parity[s] >= 0) mbar_wait(smem_u32(&full[s]), (uint32_t)issued_parity[s], &dummy);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      bool ok = true;
+      int it = 0;
+      for (int64_t t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x, ++it) {
+        const int acc = it & 1;
+        const uint32_t acc_phase = (uint32_t)(it >> 1) & 1u;
+        if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_phase ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem_base + (uint32_t)(acc * ACC_COLS);
+        for (int kb = 0; kb < nkb_total; ++kb) {
+          if (!mbar_wait(smem_u32(&full[stage]), phase, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sA + stage * A_BYTES);
+          const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+            umma(d_tmem, smem_desc(a0 + kk * UMMA_K * 2), smem_desc(b0 + kk * UMMA_K * 2), idesc,
+                 (kb > 0 || kk > 0) ? 1u : 0u);
+          }
+          umma_commit(smem_u32(&empty[stage]));
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        umma_commit(smem_u32(&acc_full[acc]));
+      }
+      if (!ok) {
+        if (args.d_status) atomicExch(args.d_status, SIM_TIMEOUT_CODE_MMA);
+        *abort_flag = 1;
+      }
+      // all MMAs issued by this thread complete before tensor memory is released
+      umma_commit(smem_u32(mma_done));
+      volatile int dummy = 0;
+      mbar_wait(smem_u32(mma_done), 0, &dummy);
+    }
+  } else {
+    // ---------------- epilogue ----------------
+    const int q = warp & 3;                   // TMEM lane quarter this warp may access
+    float* stage_buf = sEpi + (warp - 2) * (32 * 32);
+    const float sa = args.scale_a ? *args.scale_a : 1.f;
+    const float sb = args.scale_b ? *args.scale_b : 1.f;
+    const float oscale = 1.f / (sa * sb);
+    int it = 0;
+    for (int64_t t = blockIdx.x; t < args.num_tiles; t += gridDim.x, ++it) {
+      const int acc = it & 1;
+      const uint32_t acc_phase = (uint32_t)(it >> 1) & 1u;
+      if (!mbar_wait(smem_u32(&acc_full[acc]), acc_phase, abort_flag)) {
+        if (args.d_status) atomicExch(args.d_status, SIM_TIMEOUT_CODE_EPI);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      int64_t mb, nb;
+      args.tm.tile(t, mb, nb);
+      const int64_t row0 = mb * BM + q * 32;
+      const int64_t col_tile = nb * BN;
+      for (int c = 0; c < BN / 32; ++c) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * ACC_COLS + c * 32);
+        tmem_ld32(taddr, r);
+        // stage row `lane` (32 fp32 = 8 chunks of 16 B), chunk j at j ^ (lane & 7)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          float4 v = make_float4(__uint_as_float(r[4 * j]) * oscale, __uint_as_float(r[4 * j + 1]) * oscale,
+                                 __uint_as_float(r[4 * j + 2]) * oscale,
+                                 __uint_as_float(r[4 * j + 3]) * oscale);
+          *(float4*)(stage_buf + lane * 32 + ((j ^ (lane & 7)) * 4)) = v;
+        }
+        __syncwarp();
+        // write out: 8 lanes per row, 4 rows per step
+        const int64_t col0 = col_tile + c * 32;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+          const int rr = p * 4 + (lane >> 3);
+          const int ch = lane & 7;
+          const float4 v = *(const float4*)(stage_buf + rr * 32 + ((ch ^ (rr & 7)) * 4));
+          const int64_t grow = row0 + rr;
+          const int64_t gcol = col0 + ch * 4;
+          if (grow >= args.M || gcol >= args.N2) continue;
+          float* dst = args.C + grow * args.N2 + gcol;
+          if (args.vec4 && gcol + 4 <= args.N2) {
+            if (args.accumulate) {
+              float4 o = *(const float4*)dst;
+              o.x += v.x; o.y += v.y; o.z += v.z; o.w += v.w;
+              __stcs((float4*)dst, o);
+            } else {
+              __stcs((float4*)dst, v);
+            }
+          } else {
+            const float vv[4] = {v.x, v.y, v.z, v.w};
+            for (int e = 0; e < 4 && gcol + e < args.N2; ++e) dst[e] = args.accumulate ? dst[e] + vv[e] : vv[e];
+          }
+        }
+        __syncwarp();
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kpad, int box_rows, bool fp16) {
+  auto enc = get_encode_fn();
+  if (!enc) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)kpad, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)(kpad * 2)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, fp16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                   const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s) {
+  if (a.M <= 0 || a.N2 <= 0) return cudaSuccess;
+  if (a.kpad <= 0 || a.kpad % BK != 0 || a.M > (1ll << 31) - BM || a.N2 > (1ll << 31) - BN)
+    return cudaErrorInvalidValue;
+  if (((uintptr_t)a.a_hi | (uintptr_t)a.a_lo | (uintptr_t)a.b_hi | (uintptr_t)a.b_lo) & 15u)
+    return cudaErrorInvalidValue;
+  CUtensorMap mAh, mAl, mBh, mBl;
+  if (!make_map(&mAh, a.a_hi, a.M, a.kpad, BM, a.fp16) || !make_map(&mAl, a.a_lo, a.M, a.kpad, BM, a.fp16) ||
+      !make_map(&mBh, a.b_hi, a.N2, a.kpad, BN, a.fp16) || !make_map(&mBl, a.b_lo, a.N2, a.kpad, BN, a.fp16))
+    return cudaErrorInvalidValue;
+  KernelArgs k;
+  k.M = a.M;
+  k.N2 = a.N2;
+  k.nkb = (int)(a.kpad / BK);
+  k.tm.num_mb = (a.M + BM - 1) / BM;
+  k.tm.num_nb = (a.N2 + BN - 1) / BN;
+  k.tm.group = a.group_m > 0 ? a.group_m : 16;
+  k.num_tiles = k.tm.num_mb * k.tm.num_nb;
+  k.scale_a = a.scale_a;
+  k.scale_b = a.scale_b;
+  k.accumulate = a.accumulate;
+  k.C = (float*)a.C;
+  k.vec4 = ((((uintptr_t)a.C) & 15u) == 0 && (a.N2 % 4) == 0) ? 1 : 0;
+  k.d_status = a.d_status;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  int grid = a.num_sms > 0 ? a.num_sms : 148;
+  if ((int64_t)grid > k.num_tiles) grid = (int)k.num_tiles;
+  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, k, instr_desc(a.fp16 != 0));
+  note_launches(SIM_PHASE_CONTRACT, 1);
+  return cudaGetLastError();
+}
+
+}  // namespace sim

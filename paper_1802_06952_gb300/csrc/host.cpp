@@ -1,0 +1,439 @@
+// Host logic of libsim: random grid circuit generator, canonical gate-list text,
+// cut planner (E_int, copy bits, half-circuits, copy tree) and the pass scheduler
+// of the fused complex64 sweeps.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <set>
+#include <sstream>
+
+#include "sim_internal.h"
+
+namespace sim {
+
+// splitmix64 (Steele, Lea, Flood 2014), used for the X^1/2 / Y^1/2 draws and the
+// amplitude selection.
+uint64_t splitmix64_next(uint64_t& state) {
+  state += 0x9E3779B97F4A7C15ull;
+  uint64_t z = state;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+static const char* kGateName[] = {"H", "X2", "Y2", "T", "CZ"};
+
+// CZ couplers of pattern p (1..8) on an R x C grid whose cut lies above row b.
+// Patterns 1-4: horizontal (r,c)-(r,c+1) with (r%2, c%2) = (0,0), (1,1), (0,1), (1,0).
+// Patterns 5-8: vertical (r,c)-(r+1,c); 5/6 on rows of the other parity than b-1,
+// 7/8 on rows of the same parity as b-1 (these hold the couplers crossing the
+// cut); 5 and 7 take r+c even, 6 and 8 r+c odd.
+static void couplers(int R, int C, int b, int p, std::vector<std::pair<int, int>>& out) {
+  out.clear();
+  if (p <= 4) {
+    static const int want_r[4] = {0, 1, 0, 1};
+    static const int want_c[4] = {0, 1, 1, 0};
+    for (int r = 0; r < R; ++r)
+      for (int c = 0; c + 1 < C; ++c)
+        if (r % 2 == want_r[p - 1] && c % 2 == want_c[p - 1])
+          out.emplace_back(r * C + c, r * C + c + 1);
+  } else {
+    const bool cut_parity = (p == 7 || p == 8);
+    const bool even = (p == 5 || p == 7);
+    const int bp = ((b - 1) % 2 + 2) % 2;
+    for (int r = 0; r + 1 < R; ++r)
+      for (int c = 0; c < C; ++c)
+        if (((r % 2) == bp) == cut_parity && (((r + c) % 2) == 0) == even)
+          out.emplace_back(r * C + c, (r + 1) * C + c);
+  }
+}
+
+// Gate rule of the random circuits: layer 0 is H on all qubits; layer t >= 1 holds
+// the CZs of pattern ((t-1) mod 8) + 1; for t >= 2 a qubit that was in a CZ at t-1
+// and is not in one at t gets T if this is its first gate after H, else X^1/2 or
+// Y^1/2 from one splitmix64 draw (top bit 1 -> Y^1/2), in (layer, qubit) order.
+std::string generate_circuit(int R, int C, int depth, uint64_t seed, int cut_row, Circuit& out) {
+  if (R < 1 || C < 1 || R * C > 64 || depth < 1) return "grid must have 1..64 qubits and depth >= 1";
+  const int n = R * C;
+  const int b = cut_row > 0 ? cut_row : R / 2;
+  out = Circuit();
+  out.R = R; out.C = C; out.depth = depth; out.seed = seed; out.cut_row = b; out.n = n;
+  uint64_t rng = seed;
+  std::vector<char> had_first(n, 0), prev(n, 0), cur(n, 0);
+  std::vector<std::pair<int, int>> pairs;
+  for (int t = 0; t < depth; ++t) {
+    std::vector<Gate> layer;
+    if (t == 0) {
+      for (int q = 0; q < n; ++q) layer.push_back({0, G_H, q, -1});
+    } else {
+      couplers(R, C, b, ((t - 1) % 8) + 1, pairs);
+      std::fill(cur.begin(), cur.end(), 0);
+      for (auto& pr : pairs) {
+        cur[pr.first] = cur[pr.second] = 1;
+        layer.push_back({t, G_CZ, pr.first, pr.second});
+      }
+      if (t >= 2) {
+        for (int q = 0; q < n; ++q) {
+          if (prev[q] && !cur[q]) {
+            if (!had_first[q]) {
+              had_first[q] = 1;
+              layer.push_back({t, G_T, q, -1});
+            } else {
+              uint64_t r = splitmix64_next(rng);
+              layer.push_back({t, (r >> 63) ? G_Y2 : G_X2, q, -1});
+            }
+          }
+        }
+      }
+      prev = cur;
+    }
+    std::sort(layer.begin(), layer.end(), [](const Gate& a, const Gate& b2) { return a.q1 < b2.q1; });
+    out.gates.insert(out.gates.end(), layer.begin(), layer.end());
+  }
+  return "";
+}
+
+std::string circuit_text(const Circuit& c) {
+  std::string s;
+  char buf[96];
+  snprintf(buf, sizeof buf, "circuit %d %d %d %llu\n", c.R, c.C, c.depth, (unsigned long long)c.seed);
+  s += buf;
+  for (const Gate& g : c.gates) {
+    if (g.code == G_CZ)
+      snprintf(buf, sizeof buf, "%d CZ %d %d\n", g.t, g.q1, g.q2);
+    else
+      snprintf(buf, sizeof buf, "%d %s %d\n", g.t, kGateName[g.code], g.q1);
+    s += buf;
+  }
+  return s;
+}
+
+std::string parse_circuit(const char* text, Circuit& out) {
+  out = Circuit();
+  std::istringstream in(text);
+  std::string line;
+  bool have_head = false;
+  int last_t = 0;
+  std::vector<int> used_at;  // layer in which each qubit was last used
+  while (std::getline(in, line)) {
+    size_t a = line.find_first_not_of(" \t\r");
+    if (a == std::string::npos || line[a] == '#') continue;
+    std::istringstream ls(line);
+    if (!have_head) {
+      std::string kw;
+      long long R, C, d;
+      unsigned long long seed;
+      if (!(ls >> kw >> R >> C >> d >> seed) || kw != "circuit") return "gate list must start with 'circuit R C depth seed'";
+      if (R < 1 || C < 1 || R * C > 64 || d < 1) return "gate list header has a bad grid shape or depth";
+      out.R = (int)R; out.C = (int)C; out.depth = (int)d; out.seed = seed; out.n = (int)(R * C);
+      out.cut_row = out.R / 2;
+      used_at.assign(out.n, -1);
+      have_head = true;
+      continue;
+    }
+    long long t, q1, q2 = -1;
+    std::string nm;
+    if (!(ls >> t >> nm >> q1)) return "malformed gate line: " + line;
+    int code = -1;
+    for (int i = 0; i < 5; ++i)
+      if (nm == kGateName[i]) code = i;
+    if (code < 0) return "unknown gate name: " + nm;
+    if (code == G_CZ && !(ls >> q2)) return "CZ needs two qubits: " + line;
+    if (t < 0 || t >= out.depth) return "gate layer out of range: " + line;
+    if (t < last_t) return "gates must be ordered by layer";
+    last_t = (int)t;
+    if (q1 < 0 || q1 >= out.n || (code == G_CZ && (q2 < 0 || q2 >= out.n || q2 == q1)))
+      return "qubit out of range: " + line;
+    if (used_at[q1] == t || (code == G_CZ && used_at[q2] == t)) return "qubit used twice in one layer: " + line;
+    used_at[q1] = (int)t;
+    if (code == G_CZ) used_at[q2] = (int)t;
+    Gate g{(int)t, code, (int)q1, (int)(code == G_CZ ? q2 : -1)};
+    if (code == G_CZ && g.q2 < g.q1) std::swap(g.q1, g.q2);
+    out.gates.push_back(g);
+  }
+  if (!have_head) return "empty gate list";
+  return "";
+}
+
+// Amplitude selection: Floyd's algorithm over [0, 2^nq), one draw per step,
+// t = next() mod (j + 1); result sorted ascending.  count >= 2^nq gives all.
+void select_indices(int nq, uint64_t count, uint64_t& state, std::vector<uint64_t>& out) {
+  out.clear();
+  const uint64_t universe = nq >= 64 ? ~0ull : (1ull << nq);
+  if (nq < 64 && count >= universe) {
+    out.resize(universe);
+    for (uint64_t i = 0; i < universe; ++i) out[i] = i;
+    return;
+  }
+  std::set<uint64_t> chosen;
+  for (uint64_t j = universe - count; j < universe; ++j) {
+    uint64_t t = splitmix64_next(state) % (j + 1);
+    if (chosen.count(t))
+      chosen.insert(j);
+    else
+      chosen.insert(t);
+    if (j == universe - 1) break;  // guards the wrap when universe == 2^64 - 1
+  }
+  out.assign(chosen.begin(), chosen.end());
+}
+
+// ---------------------------------------------------------------------------
+// Cut plan and schedules
+// ---------------------------------------------------------------------------
+namespace {
+
+struct HalfGateLists {
+  // per layer: non-diagonal gates (qubit, code), T qubits, CZ pairs, cut slots (q, m)
+  std::vector<std::vector<std::pair<int, int>>> nondiag;
+  std::vector<uint32_t> tmask;
+  std::vector<std::vector<std::pair<int, int>>> cz;
+  std::vector<std::vector<std::pair<int, int>>> cuts;
+};
+
+void gate_matrix(int code, double m[8]) {
+  const double s = 1.0 / std::sqrt(2.0);
+  // row-major [m00, m01, m10, m11], each (re, im)
+  switch (code) {
+    case G_H: {
+      double v[8] = {s, 0, s, 0, s, 0, -s, 0};
+      memcpy(m, v, sizeof v);
+      break;
+    }
+    case G_X2: {  // 1/2 [[1+i, 1-i], [1-i, 1+i]]
+      double v[8] = {0.5, 0.5, 0.5, -0.5, 0.5, -0.5, 0.5, 0.5};
+      memcpy(m, v, sizeof v);
+      break;
+    }
+    case G_Y2: {  // 1/2 [[1+i, -1-i], [1+i, 1+i]]
+      double v[8] = {0.5, 0.5, -0.5, -0.5, 0.5, 0.5, 0.5, 0.5};
+      memcpy(m, v, sizeof v);
+      break;
+    }
+    default: {
+      double v[8] = {1, 0, 0, 0, 0, 0, 1, 0};
+      memcpy(m, v, sizeof v);
+    }
+  }
+}
+
+OpRec make_gate(int code, int q) {
+  OpRec o;
+  memset(&o, 0, sizeof o);
+  o.type = OP_GATE;
+  o.q = q;
+  o.lq = -1;
+  gate_matrix(code, o.md);
+  for (int i = 0; i < 8; ++i) o.m[i] = (float)o.md[i];
+  return o;
+}
+
+// One or more DIAG ops for a layer: T mask, CZ pairs grouped by distance
+// (x & (x >> d) & mask counts pairs (a, a + d) with both bits set), cut slots.
+void make_diags(int half, uint32_t tmask, const std::vector<std::pair<int, int>>& cz,
+                const std::vector<std::pair<int, int>>& cuts, std::vector<OpRec>& out) {
+  std::map<int, uint32_t> by_d;
+  for (auto& p : cz) {
+    int a = std::min(p.first, p.second), b = std::max(p.first, p.second);
+    by_d[b - a] |= (1u << a);
+  }
+  std::vector<std::pair<int, uint32_t>> cls(by_d.begin(), by_d.end());
+  size_t ci = 0, si = 0;
+  bool first = true;
+  while (first || ci < cls.size() || si < cuts.size()) {
+    OpRec o;
+    memset(&o, 0, sizeof o);
+    o.type = OP_DIAG;
+    o.half = half;
+    o.lq = -1;
+    o.q = -1;
+    if (first) o.tmask = tmask;
+    first = false;
+    while (ci < cls.size() && o.nsh < kMaxShift) {
+      o.sh_d[o.nsh] = (uint32_t)cls[ci].first;
+      o.sh_m[o.nsh] = cls[ci].second;
+      ++o.nsh;
+      ++ci;
+    }
+    while (si < cuts.size() && o.ncut < kMaxCutSlots) {
+      o.cutq[o.ncut] = (uint8_t)cuts[si].first;
+      o.cutm[o.ncut] = (uint8_t)cuts[si].second;
+      ++o.ncut;
+      ++si;
+    }
+    if (o.tmask || o.nsh || o.ncut) out.push_back(o);
+  }
+}
+
+// Greedy pass split of an op sequence: each pass stages k local qubits, always
+// the low `low` bits (coalesced rows) plus the qubits of the upcoming gates in
+// order; a pass ends before the first gate whose qubit no longer fits.
+void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
+                  std::vector<PassDesc>& passes, std::vector<OpRec>& ops) {
+  const int k = std::min(n, kmax);
+  const int low = std::min(k, 5);
+  size_t i = 0;
+  bool first = true;
+  if (seq.empty()) {
+    PassDesc p{k, (k >= 32 ? 0xFFFFFFFFu : ((1u << k) - 1)), (int)ops.size(), 0, first_src};
+    passes.push_back(p);
+    return;
+  }
+  while (i < seq.size()) {
+    uint32_t local = (low >= 32) ? 0xFFFFFFFFu : ((1u << low) - 1);
+    int cnt = low;
+    size_t j = i;
+    for (; j < seq.size(); ++j) {
+      if (seq[j].type != OP_GATE) continue;
+      uint32_t bit = 1u << seq[j].q;
+      if (local & bit) continue;
+      if (cnt == k) break;
+      local |= bit;
+      ++cnt;
+    }
+    // fill the remaining local slots with the lowest unused qubits
+    for (int q = 0; q < n && cnt < k; ++q)
+      if (!(local & (1u << q))) { local |= 1u << q; ++cnt; }
+    PassDesc p;
+    p.k = k;
+    p.local_mask = local;
+    p.op_begin = (int)ops.size();
+    p.op_count = (int)(j - i);
+    p.src = first ? first_src : SRC_SELF;
+    for (size_t t = i; t < j; ++t) {
+      OpRec o = seq[t];
+      if (o.type == OP_GATE) {
+        int rank = 0;
+        for (int q = 0; q < o.q; ++q)
+          if (local & (1u << q)) ++rank;
+        o.lq = rank;
+      }
+      ops.push_back(o);
+    }
+    passes.push_back(p);
+    first = false;
+    i = j;
+  }
+}
+
+}  // namespace
+
+std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan) {
+  const int b = cut_row > 0 ? cut_row : c.R / 2;
+  if (b < 1 || b >= c.R) return "cut row must lie strictly inside the grid";
+  plan = CutPlan();
+  plan.circ = c;
+  plan.n_u = b * c.C;
+  plan.n_l = c.n - plan.n_u;
+  if (plan.n_u > 32 || plan.n_l > 32) return "each half must have at most 32 qubits";
+  plan.fuse_qubits = fuse_qubits > 0 ? fuse_qubits : 12;
+  if (plan.fuse_qubits < 4 || plan.fuse_qubits > 13) return "fuse_qubits must be in 4..13";
+  const int nu = plan.n_u;
+  // E_int: CZs with one endpoint in each half, numbered by (layer, upper qubit)
+  for (const Gate& g : c.gates)
+    if (g.code == G_CZ && g.q1 < nu && g.q2 >= nu) plan.cuts.push_back({g.t, g.q1, g.q2});
+  std::sort(plan.cuts.begin(), plan.cuts.end(), [](const CutCZ& a, const CutCZ& b2) {
+    return a.t != b2.t ? a.t < b2.t : a.h < b2.h;
+  });
+  plan.c = (int)plan.cuts.size();
+  if (plan.c > 40) return "more than 40 cut CZs";
+  std::map<std::pair<int, int>, int> cut_index;
+  for (int m = 0; m < plan.c; ++m) cut_index[{plan.cuts[m].t, plan.cuts[m].h}] = m;
+
+  HalfGateLists hl[2];
+  for (int h = 0; h < 2; ++h) {
+    hl[h].nondiag.assign(c.depth, {});
+    hl[h].tmask.assign(c.depth, 0);
+    hl[h].cz.assign(c.depth, {});
+    hl[h].cuts.assign(c.depth, {});
+  }
+  for (const Gate& g : c.gates) {
+    if (g.code == G_CZ) {
+      if (g.q2 < nu) {
+        hl[0].cz[g.t].emplace_back(g.q1, g.q2);
+      } else if (g.q1 >= nu) {
+        hl[1].cz[g.t].emplace_back(g.q1 - nu, g.q2 - nu);
+      } else {
+        int m = cut_index[{g.t, g.q1}];
+        hl[0].cuts[g.t].emplace_back(g.q1, m);
+        hl[1].cuts[g.t].emplace_back(g.q2 - nu, m);
+      }
+    } else {
+      int h = g.q1 < nu ? 0 : 1;
+      int q = h ? g.q1 - nu : g.q1;
+      if (g.code == G_T)
+        hl[h].tmask[g.t] |= 1u << q;
+      else
+        hl[h].nondiag[g.t].emplace_back(q, g.code);
+    }
+  }
+  // branch layers: distinct layers holding cuts, in order
+  std::vector<int> branch;
+  for (const CutCZ& x : plan.cuts)
+    if (branch.empty() || branch.back() != x.t) branch.push_back(x.t);
+
+  for (int h = 0; h < 2; ++h) {
+    HalfSchedule& S = plan.sched[h];
+    const int n = h ? plan.n_l : plan.n_u;
+    S.n = n;
+    // plain pass count (Section 2.4): one per non-diagonal gate, one per layer
+    // holding any diagonal gate (T, CZ, or cut slot)
+    int plain = 0;
+    for (int t = 0; t < c.depth; ++t) {
+      plain += (int)hl[h].nondiag[t].size();
+      if (hl[h].tmask[t] || !hl[h].cz[t].empty() || !hl[h].cuts[t].empty()) ++plain;
+    }
+    S.plain_passes = plain;
+    // does layer 0 put H on every qubit of the half?
+    bool uniform = c.depth > 0 && (int)hl[h].nondiag[0].size() == n && hl[h].tmask[0] == 0 &&
+                   hl[h].cz[0].empty() && hl[h].cuts[0].empty();
+    if (uniform)
+      for (auto& p : hl[h].nondiag[0])
+        if (p.second != G_H) uniform = false;
+
+    const int nlev = (int)branch.size() + 1;
+    int bits = 0;
+    for (int j = 0; j < nlev; ++j) {
+      Level L;
+      L.branch_layer = j == 0 ? -1 : branch[j - 1];
+      L.bits_before = bits;
+      int nb = 0;
+      if (j > 0)
+        for (const CutCZ& x : plan.cuts)
+          if (x.t == L.branch_layer) ++nb;
+      bits += nb;
+      L.bits_total = bits;
+      const int t_begin = j == 0 ? 0 : branch[j - 1];
+      const int t_end = j + 1 < nlev ? branch[j] : c.depth - 1;  // inclusive
+      std::vector<OpRec> seq;
+      for (int t = t_begin; t <= t_end; ++t) {
+        const bool own_cut_layer = (j > 0 && t == t_begin);
+        if (own_cut_layer) {
+          // this level applies only the cut slots of its branch layer here
+          make_diags(h, 0, {}, hl[h].cuts[t], seq);
+          continue;
+        }
+        if (!(j == 0 && t == 0 && uniform))
+          for (auto& p : hl[h].nondiag[t]) seq.push_back(make_gate(p.second, p.first));
+        const bool next_branch = (j + 1 < nlev && t == t_end);
+        make_diags(h, hl[h].tmask[t], hl[h].cz[t],
+                   next_branch ? std::vector<std::pair<int, int>>() : hl[h].cuts[t], seq);
+      }
+      int first_src = j == 0 ? (uniform ? SRC_UNIFORM : SRC_ZERO) : SRC_PARENT;
+      split_passes(n, plan.fuse_qubits, seq, first_src, L.passes, S.ops);
+      S.levels.push_back(L);
+    }
+
+    // plain complex128 path: per layer, one op per non-diagonal gate, then the
+    // combined diagonal of the layer with this copy's cut slots
+    plan.plain[h].assign(c.depth, PlainLayer());
+    for (int t = 0; t < c.depth; ++t) {
+      for (auto& p : hl[h].nondiag[t]) plan.plain[h][t].gates.push_back(make_gate(p.second, p.first));
+      make_diags(h, hl[h].tmask[t], hl[h].cz[t], hl[h].cuts[t], plan.plain[h][t].diags);
+    }
+  }
+  return "";
+}
+
+}  // namespace sim

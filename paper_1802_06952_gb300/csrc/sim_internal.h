@@ -1,0 +1,205 @@
+// Internal declarations shared by the host code and the CUDA kernels of libsim.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+namespace sim {
+
+// ---------------------------------------------------------------------------
+// Circuit IR (Supplementary A, Eq. 3: layers of single-qubit gates and CZ edges)
+// ---------------------------------------------------------------------------
+enum GateCode : int { G_H = 0, G_X2 = 1, G_Y2 = 2, G_T = 3, G_CZ = 4 };
+
+struct Gate {
+  int t, code, q1, q2;
+};
+
+struct Circuit {
+  int R = 0, C = 0, depth = 0, cut_row = 0;
+  uint64_t seed = 0;
+  int n = 0;
+  std::vector<Gate> gates;  // ordered by layer, then first qubit
+};
+
+// ---------------------------------------------------------------------------
+// Device op records of the fused complex64 sweeps and the plain complex128 path
+// ---------------------------------------------------------------------------
+enum OpType : int { OP_GATE = 0, OP_DIAG = 1 };
+constexpr int kMaxShift = 6;   // CZ shift classes per diagonal op
+constexpr int kMaxCutSlots = 16;
+
+// One op of a pass.  A GATE is a 2x2 complex matrix on local bit `lq` (fused
+// path) or on qubit `q` (plain path).  A DIAG is the combined diagonal of one
+// layer (Section 2.4, Eqs. 4 and 6) plus the copy-dependent cut slots:
+//   phase(x) = w^{popc(x & tmask)} * (-1)^{sum_s popc(x & (x >> sh_d[s]) & sh_m[s])}
+//   upper half:  * [bit cutq[i] of x == bit cutm[i] of the copy id]   (P_l)
+//   lower half:  * (-1)^{bit cutq[i] of x * bit cutm[i] of the copy id} (Z^l)
+// with w = e^{i pi / 4}.
+struct OpRec {
+  int32_t type;
+  int32_t lq;
+  int32_t q;
+  int32_t nsh;
+  int32_t ncut;
+  int32_t half;
+  uint32_t tmask;
+  uint32_t pad0;
+  uint32_t sh_d[kMaxShift];
+  uint32_t sh_m[kMaxShift];
+  uint8_t cutq[kMaxCutSlots];
+  uint8_t cutm[kMaxCutSlots];
+  float m[8];
+  double md[8];
+};
+
+// One fused pass: stage 2^k amplitudes whose local bits are `local_mask`, run
+// ops [op_begin, op_begin + op_count), write back.
+enum PassSrc : int { SRC_SELF = 0, SRC_PARENT = 1, SRC_UNIFORM = 2, SRC_ZERO = 3 };
+
+struct PassDesc {
+  int k;
+  uint32_t local_mask;
+  int op_begin, op_count;
+  int src;
+};
+
+// One level of the copy tree of a half: nodes share all gates up to the branch
+// layer; a level-j node id is the copy index masked to its low `bits_total` bits.
+struct Level {
+  int branch_layer;     // layer whose cut slots this level applies first (-1: root)
+  int bits_before;      // copy bits fixed by earlier levels
+  int bits_total;       // bits fixed up to and including this level
+  std::vector<PassDesc> passes;
+};
+
+struct HalfSchedule {
+  int n = 0;                     // qubits in the half
+  std::vector<Level> levels;
+  std::vector<OpRec> ops;        // all ops of all passes
+  int plain_passes = 0;          // Section 2.4 pass count per copy (for reports)
+};
+
+// Per-layer description of a half for the plain complex128 path.
+struct PlainLayer {
+  std::vector<OpRec> gates;      // GATE ops with q set
+  std::vector<OpRec> diags;      // DIAG ops (0 or more, cut slots included)
+};
+
+struct CutCZ {
+  int t, h, k;  // layer, upper qubit, lower qubit (global indices)
+};
+
+struct CutPlan {
+  Circuit circ;
+  int n_u = 0, n_l = 0, c = 0;
+  std::vector<CutCZ> cuts;
+  HalfSchedule sched[2];
+  std::vector<PlainLayer> plain[2];
+  int fuse_qubits = 0;
+  // device copies of the op tables (uploaded lazily, freed with the plan)
+  OpRec* d_ops[2] = {nullptr, nullptr};
+  OpRec* d_plain_ops[2] = {nullptr, nullptr};
+  std::vector<int> plain_op_offsets[2];  // per layer: first op index (gates then diags)
+  std::vector<OpRec> plain_flat[2];       // host copy of the uploaded plain op table
+  int device = -1;
+};
+
+// Phase profiler hooks (api.cpp): kernel launch and host<->device byte counters.
+void note_launches(int phase, int count);
+void note_bytes(uint64_t h2d, uint64_t d2h);
+
+// Host logic (host.cpp)
+std::string generate_circuit(int R, int C, int depth, uint64_t seed, int cut_row, Circuit& out);
+std::string parse_circuit(const char* text, Circuit& out);
+std::string circuit_text(const Circuit& c);
+std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan);
+void select_indices(int nq, uint64_t count, uint64_t& state, std::vector<uint64_t>& out);
+uint64_t splitmix64_next(uint64_t& state);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files); all enqueue on `stream`.
+// ---------------------------------------------------------------------------
+struct NodeEntry {
+  uint64_t node_id;     // copy bits fixed so far (selects cut-slot values)
+  int64_t parent_slot;  // slot of the parent in the parent level buffer
+  int64_t dst_row;      // row of the destination buffer
+};
+
+struct SweepLaunch {
+  int n, k;
+  uint32_t local_mask;
+  const OpRec* ops;       // device pointer to the pass's first op
+  int op_count;
+  int src;                // PassSrc
+  const NodeEntry* nodes; // device node table for this launch
+  int64_t nslots;
+  const void* src_base;   // parent level buffer (SRC_PARENT) or the own buffer
+  void* dst_base;
+  int threads;
+};
+cudaError_t launch_sweep_c64(const SweepLaunch& L, cudaStream_t s);
+
+struct PlainLaunch {
+  int n;
+  int q;                  // target qubit of a GATE (host copy of op->q)
+  const OpRec* op;        // one GATE or DIAG op (device)
+  const uint64_t* copy_ids;  // device: copy index of each state in the batch
+  int64_t nstates;
+  void* psi;              // nstates x 2^n complex128
+};
+cudaError_t launch_plain_gate(const PlainLaunch& L, cudaStream_t s);
+cudaError_t launch_plain_diag(const PlainLaunch& L, cudaStream_t s);
+cudaError_t launch_plain_init_zero(void* psi, int n, int64_t nstates, cudaStream_t s);
+
+// leafsel[row][i] = src[slot][sel[i]] for each slot of a node table (rows = dst_row)
+cudaError_t launch_gather(const void* src, int n, const NodeEntry* nodes, int64_t nslots,
+                          const uint64_t* sel, int64_t nsel, void* dst, int is_c128,
+                          cudaStream_t s);
+
+// Split-pack (complex64 leaves [K][nsel] -> K-major split operands).
+//   A-operand (lower half, rows = n_sel_l):  row m: cols 2k, 2k+1 = (re, im) of L_k[m]
+//   B-operand (upper half, rows = 2 n_sel_u): row 2j: (re, -im), row 2j+1: (im, re)
+// hi = round(v * scale), lo = round(v * scale - hi) in bf16 or fp16; scale_dev is a
+// device float (NULL: 1).
+cudaError_t launch_pack_a(const void* leaves, int64_t K, int64_t nsel, int64_t kpad,
+                          int fp16, const float* scale_dev, void* hi, void* lo, cudaStream_t s);
+cudaError_t launch_pack_b(const void* leaves, int64_t K, int64_t nsel, int64_t kpad,
+                          int fp16, const float* scale_dev, void* hi, void* lo, cudaStream_t s);
+// out_dev[0] = max |re|, |im| over a complex64 array; out_dev[1] = the power-of-two
+// fp16 pre-scale derived from it
+cudaError_t launch_absmax_c64(const void* x, int64_t count, float* out_dev, cudaStream_t s);
+
+// tcgen05 contraction: C[M][2N] fp32 (= complex64 [M][N]) (+)= sum over 3 split
+// segments of A_seg[M][kpad] * B_seg[2N][kpad]^T.
+struct TcGemmArgs {
+  const void* a_hi; const void* a_lo; const void* b_hi; const void* b_lo;
+  int64_t M, N2, kpad;    // N2 = 2 * n_sel_u
+  int fp16;
+  const float* scale_a;   // device pre-scales of A and B (NULL: 1); output / (sa * sb)
+  const float* scale_b;
+  int accumulate;
+  void* C;
+  int group_m;
+  int num_sms;
+  int* d_status;          // device word, set non-zero if a wait gave up
+};
+cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s);
+// values written to *d_status when a bounded wait of the contraction gives up
+constexpr int SIM_TIMEOUT_CODE_TMA = 0x101;
+constexpr int SIM_TIMEOUT_CODE_MMA = 0x102;
+constexpr int SIM_TIMEOUT_CODE_EPI = 0x103;
+
+// Plain FP64 contraction C[M][N] (+)= sum_k Lsel[k][m] * Usel[k][j] (complex128 out)
+cudaError_t launch_fp64_gemm(const void* lsel, const void* usel, int in_c128, int64_t K,
+                             int64_t M, int64_t N, int accumulate, void* C, cudaStream_t s);
+
+// FP64 statistics over an amplitude block: acc[0] = sum p, acc[1] = sum ln w over
+// p > 0, acc[2] = number of p > 0 (as double); hist[SIM_KS_BINS] counts.
+cudaError_t launch_stats(const void* amps, int is_c128, uint64_t count, int nq,
+                         double* acc_dev, unsigned long long* hist_dev, cudaStream_t s);
+
+}  // namespace sim

@@ -1,0 +1,139 @@
+"""CPU tests of the C-ABI library: it loads, exports every symbol include/sim.h
+declares, and its host logic (circuit generator, gate-list text, cut planner,
+copy-tree schedule, amplitude selection, argument checks) agrees with the
+independent oracle implementation, bit for bit where the work is integer."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import circuit as oc
+import paper_1802_06952_gb300 as sim
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1802_06952_gb300 import build
+    build.build()
+    sim.lib()
+
+
+def test_exports_match_header():
+    hdr = open(os.path.join(ROOT, "include", "sim.h")).read()
+    declared = set(re.findall(r"\b(sim_[a-z0-9_]+)\s*\(", hdr))
+    assert declared == set(sim.EXPORTS)
+    for name in declared:
+        assert hasattr(sim.lib(), name), name
+
+
+@pytest.mark.parametrize("R,C,d,seed", [(4, 4, 10, 0), (6, 5, 16, 0), (6, 5, 16, 3), (6, 7, 22, 0),
+                                        (8, 8, 22, 0), (4, 2, 9, 5), (3, 5, 31, 77), (8, 7, 40, 2)])
+def test_generator_text_equals_oracle(R, C, d, seed):
+    c = sim.sim_build_circuit(R, C, d, seed)
+    try:
+        txt = sim.sim_circuit_text(c)
+        ref = oc.to_text(R, C, d, seed, oc.generate(R, C, d, seed, R // 2))
+        assert txt == ref
+        n, depth, ng = sim.sim_circuit_info(c)
+        assert (n, depth) == (R * C, d) and ng == len(ref.splitlines()) - 1
+    finally:
+        sim.sim_destroy_circuit(c)
+
+
+@pytest.mark.parametrize("R,C,d,seed", [(4, 4, 10, 0), (6, 5, 16, 1), (6, 7, 22, 0), (8, 8, 22, 0), (8, 7, 23, 0)])
+def test_cut_list_equals_oracle(R, C, d, seed):
+    gates, plan = oc.grid_cut(R, C, d, seed, R // 2)
+    c = sim.sim_build_circuit(R, C, d, seed)
+    p, ncut, copies, nu, nl = sim.sim_cut(c, R // 2)
+    try:
+        assert ncut == plan.c and copies == plan.copies and (nu, nl) == (plan.n_u, plan.n_l)
+        cuts, ne = sim.sim_cut_list(p, ncut)
+        assert cuts == [tuple(x) for x in plan.cuts]
+        assert ne == plan.n_equivalent()
+        for half in (0, 1):
+            levels, fused, plain = sim.sim_plan_schedule(p, half)
+            assert levels == len(plan.cuts_per_layer()) + 1
+            assert 1 <= fused <= plain + levels
+    finally:
+        sim.sim_destroy_cut(p)
+        sim.sim_destroy_circuit(c)
+
+
+def test_explicit_gate_list_roundtrip():
+    gates = oc.generate(4, 5, 12, 9)
+    txt = oc.to_text(4, 5, 12, 9, gates)
+    c = sim.sim_build_circuit(gate_list=txt)
+    try:
+        assert sim.sim_circuit_text(c) == txt
+    finally:
+        sim.sim_destroy_circuit(c)
+
+
+@pytest.mark.parametrize("bad", [
+    "circuit 2 2 3 0\n0 H 0\n0 H 0\n",          # qubit twice in a layer
+    "circuit 2 2 3 0\n0 H 9\n",                 # qubit out of range
+    "circuit 2 2 3 0\n1 H 0\n0 H 1\n",          # layers out of order
+    "circuit 2 2 3 0\n0 Q 0\n",                 # unknown gate
+    "0 H 0\n",                                  # missing header
+    "circuit 2 2 3 0\n0 CZ 1 1\n",              # CZ on one qubit
+])
+def test_malformed_gate_lists_rejected(bad):
+    with pytest.raises(sim.SimError) as e:
+        sim.sim_build_circuit(gate_list=bad)
+    assert e.value.code == sim.SIM_EINVAL and sim.sim_last_error()
+
+
+def test_bad_shapes_and_cuts():
+    with pytest.raises(sim.SimError):
+        sim.sim_build_circuit(0, 4, 5, 0)
+    with pytest.raises(sim.SimError):
+        sim.sim_build_circuit(9, 8, 5, 0)        # 72 qubits
+    c = sim.sim_build_circuit(4, 4, 5, 0)
+    try:
+        with pytest.raises(sim.SimError):
+            sim.sim_cut(c, 4)                    # cut on the grid edge
+    finally:
+        sim.sim_destroy_circuit(c)
+    c = sim.sim_build_circuit(2, 17, 3, 0)       # halves of 17 qubits are fine
+    p = sim.sim_cut(c, 1)[0]
+    sim.sim_destroy_cut(p)
+    sim.sim_destroy_circuit(c)
+    c = sim.sim_build_circuit(4, 11, 3, 0)       # a 33-qubit half is not
+    try:
+        with pytest.raises(sim.SimError) as e:
+            sim.sim_cut(c, 3)
+        assert e.value.code == sim.SIM_EUNSUPPORTED
+    finally:
+        sim.sim_destroy_circuit(c)
+
+
+@pytest.mark.parametrize("nqu,nu,nql,nl,seed", [(15, 300, 15, 77, 0), (21, 1 << 10, 21, 1 << 10, 5),
+                                                (4, 16, 4, 3, 1), (32, 5, 32, 5, 123)])
+def test_select_equals_oracle(nqu, nu, nql, nl, seed):
+    su, sl = sim.sim_select(nqu, nu, nql, nl, seed)
+    ru, rl = oracle.select(nqu, nu, nql, nl, seed)
+    assert np.array_equal(su, ru) and np.array_equal(sl, rl)
+
+
+def test_cut_invariance_under_gate_order_text():
+    # the planner numbers cuts by (layer, upper qubit), whatever order the list uses
+    gates = oc.generate(4, 4, 10, 0)
+    by_layer = {}
+    for g in gates:
+        by_layer.setdefault(g[0], []).append(g)
+    shuffled = []
+    for t in sorted(by_layer):
+        shuffled += list(reversed(by_layer[t]))
+    txt = oc.to_text(4, 4, 10, 0, shuffled)
+    c = sim.sim_build_circuit(gate_list=txt)
+    p, ncut, *_ = sim.sim_cut(c, 2)
+    try:
+        cuts, _ = sim.sim_cut_list(p, ncut)
+        assert cuts == [tuple(x) for x in oc.CutPlan(16, 8, gates).cuts]
+    finally:
+        sim.sim_destroy_cut(p)
+        sim.sim_destroy_circuit(c)

@@ -1,0 +1,327 @@
+"""GPU parity of libsim against the FP64 oracle, through the C-ABI.
+
+Tolerances (max|da| / max|a| over the compared amplitudes):
+  complex64 halves + split bf16 / fp16 contraction   <= 1e-5
+  complex128 plain halves + FP64 contraction         <= 1e-12
+  half-state fidelity of complex64 leaves            >= 1 - 1e-6
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import circuit as oc
+import paper_1802_06952_gb300 as sim
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_SPLIT = 1e-5
+TOL_PLAIN = 1e-12
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_06952_gb300 import build
+    build.build()
+    sim.lib()
+    torch.cuda.set_device(0)
+    yield
+    sim.sim_release_cache()
+
+
+def rel_err(got, ref):
+    return float(np.max(np.abs(got - ref)) / np.max(np.abs(ref)))
+
+
+class Run:
+    """Circuit + cut + evolved halves for one test; destroyed at exit."""
+
+    def __init__(self, R, C, d, seed, b=None, gate_list=None, n=None):
+        b = b or R // 2
+        self.circ = sim.sim_build_circuit(R, C, d, seed, b, gate_list)
+        self.plan, self.c, self.copies, self.nu, self.nl = sim.sim_cut(self.circ, b)
+        self.halves = []
+
+    def evolve(self, precision, k0=0, k1=None, sel_u=None, sel_l=None, opts=None):
+        h = sim.sim_evolve_halves(self.plan, precision, k0, self.copies if k1 is None else k1, sel_u, sel_l, opts)
+        self.halves.append(h)
+        return h
+
+    def close(self):
+        for h in self.halves:
+            sim.sim_destroy_halves(h)
+        sim.sim_destroy_cut(self.plan)
+        sim.sim_destroy_circuit(self.circ)
+
+
+def amplitudes(h, contraction, M, N, accumulate=False, out=None):
+    dt = torch.complex128 if contraction == sim.SIM_FP64_PLAIN else torch.complex64
+    if out is None:
+        out = torch.zeros((M, N), dtype=dt, device="cuda")
+    sim.sim_amplitudes(h, contraction, accumulate, out)
+    sim.sim_status()
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_config0_16q_plain_fp64(seed):
+    """4x4 grid, depth 10, c = 4: complex128 plain path, all 2^16 amplitudes."""
+    gates, plan = oc.grid_cut(4, 4, 10, seed, 2)
+    ref = oracle.statevector(16, gates).reshape(1 << 8, 1 << 8)
+    r = Run(4, 4, 10, seed)
+    try:
+        assert r.c == 4
+        h = r.evolve(sim.SIM_C128_PLAIN)
+        got = amplitudes(h, sim.SIM_FP64_PLAIN, 256, 256).cpu().numpy()
+        assert rel_err(got, ref) <= TOL_PLAIN
+    finally:
+        r.close()
+
+
+@pytest.mark.parametrize("contraction", [sim.SIM_SPLIT_BF16, sim.SIM_SPLIT_FP16, sim.SIM_FP64_PLAIN])
+def test_config0_16q_c64(contraction):
+    gates, plan = oc.grid_cut(4, 4, 10, 0, 2)
+    ref = oracle.statevector(16, gates).reshape(256, 256)
+    r = Run(4, 4, 10, 0)
+    try:
+        h = r.evolve(sim.SIM_C64)
+        got = amplitudes(h, contraction, 256, 256).cpu().numpy()
+        assert rel_err(got, ref) <= TOL_SPLIT
+    finally:
+        r.close()
+
+
+def test_leaf_half_states_fidelity():
+    gates, plan = oc.grid_cut(6, 4, 17, 2, 3)
+    r = Run(6, 4, 17, 2, 3)
+    try:
+        h = r.evolve(sim.SIM_C64)
+        hp = r.evolve(sim.SIM_C128_PLAIN)
+        for k in (0, 1, 37, r.copies - 1):
+            for half, nq in ((0, r.nu), (1, r.nl)):
+                ref = oracle.half_state(plan, half, k)
+                buf = torch.zeros(1 << nq, dtype=torch.complex64, device="cuda")
+                sim.sim_halves_leaf(h, half, k, buf)
+                got = buf.cpu().numpy().astype(np.complex128)
+                nr, ng = np.vdot(ref, ref).real, np.vdot(got, got).real
+                if nr == 0:
+                    assert ng == 0
+                    continue
+                fid = abs(np.vdot(ref, got)) ** 2 / (nr * ng)
+                assert fid >= 1 - 1e-6
+                assert np.max(np.abs(got - ref)) <= 1e-6 * max(np.max(np.abs(ref)), 1e-30) * 10
+                bp = torch.zeros(1 << nq, dtype=torch.complex128, device="cuda")
+                sim.sim_halves_leaf(hp, half, k, bp)
+                assert np.max(np.abs(bp.cpu().numpy() - ref)) <= 1e-14
+    finally:
+        r.close()
+
+
+@pytest.mark.parametrize("R,C,d,seed,nsu,nsl,k0,k1", [
+    (4, 5, 16, 0, 300, 77, 0, None),      # ragged selections, all copies
+    (4, 5, 16, 1, 1, 1, 3, 16),           # single amplitude, copy subrange
+    (6, 4, 17, 3, 129, 257, 5, 18),       # tile edges +-1, 13 copies
+    (4, 4, 10, 2, 256, 256, 0, None),     # "selection" of every index, shuffled order
+])
+def test_selection_and_copy_ranges(R, C, d, seed, nsu, nsl, k0, k1):
+    gates, plan = oc.grid_cut(R, C, d, seed, R // 2)
+    rng = np.random.default_rng(seed + 100)
+    su = rng.permutation(1 << plan.n_u)[:nsu].astype(np.uint64)
+    sl = rng.permutation(1 << plan.n_l)[:nsl].astype(np.uint64)
+    k1v = plan.copies if k1 is None else k1
+    ref = oracle.cut_amplitudes(plan, su, sl, k0, k1v)
+    r = Run(R, C, d, seed)
+    try:
+        h = r.evolve(sim.SIM_C64, k0, k1v, su, sl)
+        got = amplitudes(h, sim.SIM_SPLIT_BF16, nsl, nsu).cpu().numpy()
+        assert rel_err(got, ref) <= TOL_SPLIT
+        hp = r.evolve(sim.SIM_C128_PLAIN, k0, k1v, su, sl)
+        gotp = amplitudes(hp, sim.SIM_FP64_PLAIN, nsl, nsu).cpu().numpy()
+        assert rel_err(gotp, ref) <= TOL_PLAIN
+    finally:
+        r.close()
+
+
+def test_accumulate_over_copy_batches():
+    gates, plan = oc.grid_cut(4, 5, 16, 4, 2)
+    ref = oracle.cut_amplitudes(plan)
+    r = Run(4, 5, 16, 4)
+    try:
+        out = torch.zeros((1 << plan.n_l, 1 << plan.n_u), dtype=torch.complex64, device="cuda")
+        bounds = [0, 5, 6, 40, plan.copies]
+        for a, b in zip(bounds[:-1], bounds[1:]):
+            h = r.evolve(sim.SIM_C64, a, b)
+            sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, True, out)
+        sim.sim_status()
+        assert rel_err(out.cpu().numpy(), ref) <= TOL_SPLIT
+    finally:
+        r.close()
+
+
+def test_host_output_buffer():
+    gates, plan = oc.grid_cut(4, 4, 10, 0, 2)
+    ref = oracle.statevector(16, gates).reshape(256, 256)
+    r = Run(4, 4, 10, 0)
+    try:
+        h = r.evolve(sim.SIM_C64)
+        host = torch.zeros((256, 256), dtype=torch.complex64).pin_memory()
+        sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, host)
+        assert rel_err(host.numpy(), ref) <= TOL_SPLIT
+        pageable = torch.zeros((256, 256), dtype=torch.complex64)
+        sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, pageable)
+        assert np.array_equal(pageable.numpy(), host.numpy())
+    finally:
+        r.close()
+
+
+def diag_circuit_text(R, C, depth, b):
+    """H layer, CZ patterns, T on idle qubits of odd layers (closed form of Eqs. 4, 6)."""
+    n = R * C
+    gates = [(0, "H", q) for q in range(n)]
+    tsets, czsets = [], []
+    for t in range(1, depth):
+        pairs = oc.pattern_couplers(R, C, b, oc.pattern_of_layer(t))
+        busy = {q for p in pairs for q in p}
+        czsets.append(pairs)
+        layer = [(t, "CZ", a, c) for (a, c) in pairs]
+        if t % 2 == 1:
+            ts = [q for q in range(n) if q not in busy]
+            tsets.append(ts)
+            layer += [(t, "T", q) for q in ts]
+        layer.sort(key=lambda g: g[2])
+        gates += layer
+    return oc.to_text(R, C, depth, 0, gates), tsets, czsets
+
+
+def test_diagonal_closed_form_30q():
+    """All 2^30 amplitudes of a diagonal 30-qubit circuit with 10 cut CZs against
+    2^{-15} w^{m1(x)} (-1)^{m2(x)} at sampled x (no oracle involved)."""
+    R, C, b, depth = 6, 5, 3, 17
+    txt, ts, cz = diag_circuit_text(R, C, depth, b)
+    r = Run(R, C, depth, 0, b, gate_list=txt)
+    try:
+        assert r.c == 10
+        h = r.evolve(sim.SIM_C64)
+        out = amplitudes(h, sim.SIM_SPLIT_BF16, 1 << 15, 1 << 15)
+        rng = np.random.default_rng(3)
+        xs = rng.integers(0, 1 << 30, size=4096)
+        got = out.reshape(-1)[torch.from_numpy(xs).cuda()].cpu().numpy()
+        tm = sum(1 << q for s in ts for q in s)
+        m1 = np.array([sum((int(x) >> q) & 1 for s in ts for q in s) for x in xs])
+        m2 = np.array([sum(((int(x) >> a) & 1) & ((int(x) >> c) & 1) for p in cz for (a, c) in p) for x in xs])
+        ref = 2.0 ** -15 * np.exp(1j * np.pi / 4 * m1) * (-1.0) ** m2
+        assert tm > 0
+        assert rel_err(got, ref) <= TOL_SPLIT
+    finally:
+        r.close()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_config1_30q_split_bf16_sampled(seed):
+    """6x5 grid (30 qubits), depth 16, c = 8: the full 32768 x 256 x 32768 contraction,
+    checked on 4096 sampled amplitudes against the oracle's cut-and-sum."""
+    gates, plan = oc.grid_cut(6, 5, 16, seed, 3)
+    assert plan.c == 8
+    rng = np.random.default_rng(seed)
+    su = np.unique(rng.integers(0, 1 << 15, size=64)).astype(np.uint64)
+    sl = np.unique(rng.integers(0, 1 << 15, size=64)).astype(np.uint64)
+    ref = oracle.cut_amplitudes(plan, su, sl)
+    r = Run(6, 5, 16, seed, 3)
+    try:
+        h = r.evolve(sim.SIM_C64)
+        out = amplitudes(h, sim.SIM_SPLIT_BF16, 1 << 15, 1 << 15)
+        got = out[torch.from_numpy(sl.astype(np.int64)).cuda()][:, torch.from_numpy(su.astype(np.int64)).cuda()]
+        assert rel_err(got.cpu().numpy(), ref) <= TOL_SPLIT
+        st = sim.sim_stats(out, 0, 1 << 30, 30)
+        assert abs(st[0] - 1.0) < 1e-4      # unit norm of the full state
+        del out
+        torch.cuda.empty_cache()
+    finally:
+        r.close()
+
+
+def test_config1_30q_plain_fp64_sampled():
+    gates, plan = oc.grid_cut(6, 5, 16, 0, 3)
+    rng = np.random.default_rng(11)
+    su = np.unique(rng.integers(0, 1 << 15, size=48)).astype(np.uint64)
+    sl = np.unique(rng.integers(0, 1 << 15, size=48)).astype(np.uint64)
+    ref = oracle.cut_amplitudes(plan, su, sl)
+    r = Run(6, 5, 16, 0, 3)
+    try:
+        h = r.evolve(sim.SIM_C128_PLAIN, 0, None, su, sl)
+        got = amplitudes(h, sim.SIM_FP64_PLAIN, sl.size, su.size).cpu().numpy()
+        assert rel_err(got, ref) <= TOL_PLAIN
+    finally:
+        r.close()
+
+
+def test_stats_match_oracle():
+    gates, plan = oc.grid_cut(4, 5, 16, 7, 2)
+    ref = oracle.cut_amplitudes(plan)
+    st_ref, hist_ref = oracle.stats(ref, 20)
+    r = Run(4, 5, 16, 7)
+    try:
+        h = r.evolve(sim.SIM_C64)
+        out = amplitudes(h, sim.SIM_SPLIT_BF16, 1 << plan.n_l, 1 << plan.n_u)
+        st, hist = sim.sim_stats(out, 0, 1 << 20, 20, want_hist=True)
+        assert abs(st[0] - st_ref[0]) < 1e-5 and abs(st[1] - st_ref[1]) < 1e-5
+        assert abs(st[2] - st_ref[2]) < 1e-4
+        assert abs(st[3] - st_ref[3]) < 1e-3
+        assert hist.sum() == hist_ref.sum() == 1 << 20
+        # float32 vs float64 binning may move an entry across one bin edge
+        assert np.abs(hist.astype(np.int64) - hist_ref.astype(np.int64)).sum() <= 64
+        refd = torch.from_numpy(ref).cuda()
+        st2 = sim.sim_stats(refd, 1, 1 << 20, 20)
+        assert np.allclose(st2[:3], st_ref[:3], rtol=1e-12, atol=1e-12)
+    finally:
+        r.close()
+
+
+def test_sample_entry_point():
+    r = Run(6, 5, 16, 2, 3)
+    try:
+        out = torch.zeros((200, 300), dtype=torch.complex64, device="cuda")
+        su, sl, st = sim.sim_sample(r.plan, 300, 200, 9, out, r.nu, r.nl)
+        ru, rl = oracle.select(r.nu, 300, r.nl, 200, 9)
+        assert np.array_equal(su, ru) and np.array_equal(sl, rl)
+        gates, plan = oc.grid_cut(6, 5, 16, 2, 3)
+        ref = oracle.cut_amplitudes(plan, su, sl)
+        assert rel_err(out.cpu().numpy(), ref) <= TOL_SPLIT
+        st_ref, _ = oracle.stats(ref, 30)
+        assert abs(st[1] - st_ref[1]) < 1e-4 * max(1, st_ref[1])
+    finally:
+        r.close()
+
+
+def test_fuse_widths_agree():
+    gates, plan = oc.grid_cut(6, 4, 17, 5, 3)
+    ref = oracle.cut_amplitudes(plan)
+    for fq in (4, 7, 13):
+        r = Run(6, 4, 17, 5, 3)
+        try:
+            h = r.evolve(sim.SIM_C64, opts={"fuse_qubits": fq, "sweep_threads": 128})
+            got = amplitudes(h, sim.SIM_SPLIT_FP16, 1 << plan.n_l, 1 << plan.n_u).cpu().numpy()
+            assert rel_err(got, ref) <= TOL_SPLIT
+        finally:
+            r.close()
+
+
+def test_gpu_argument_errors():
+    r = Run(4, 4, 10, 0)
+    try:
+        with pytest.raises(sim.SimError) as e:
+            r.evolve(sim.SIM_C64, 5, 5)
+        assert e.value.code == sim.SIM_EINVAL
+        with pytest.raises(sim.SimError):
+            r.evolve(sim.SIM_C64, 0, 17)
+        with pytest.raises(sim.SimError):
+            r.evolve(sim.SIM_C64, 0, 16, np.array([256], dtype=np.uint64), None)
+        h = r.evolve(sim.SIM_C128_PLAIN)
+        out = torch.zeros((256, 256), dtype=torch.complex64, device="cuda")
+        with pytest.raises(sim.SimError):
+            sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, out)
+        sim.sim_status()
+    finally:
+        r.close()
