@@ -187,13 +187,17 @@ def gumbel_cdf(z):
     return 1.0 - np.exp(-np.exp(z))
 
 
-def stats(amps, n_qubits):
+def stats(amps, n_qubits, bin_dtype=np.float64):
     """Section 3 statistics over a block of amplitudes, FP64:
     [sum |A|^2, mean 2^n|A|^2, mean ln(2^n|A|^2), binned KS distance to Eq. 7].
 
     The KS distance is taken over KS_BINS equal bins of z = ln(2^n |A|^2) on
     [KS_ZMIN, KS_ZMAX] (values outside are clamped to the end bins): the largest
-    gap between the empirical and the Eq. 7 CDF at the bin edges.
+    gap between the empirical and the Eq. 7 CDF at the bin edges.  The bin of each
+    entry is decided in ``bin_dtype`` arithmetic (|A|^2, the logarithm and the
+    bin coordinate (z - KS_ZMIN) * KS_BINS / (KS_ZMAX - KS_ZMIN), each operation
+    rounded separately), so a check can take the decision in the precision of the
+    code it is compared with; the sums are FP64 either way.
     """
     a = np.asarray(amps).astype(np.complex128).ravel()
     p = (a.real * a.real + a.imag * a.imag)
@@ -205,9 +209,15 @@ def stats(amps, n_qubits):
         z = np.log(w)
     finite = np.isfinite(z)
     mean_ln = float(z[finite].mean()) if finite.any() else float("-inf")
-    zc = np.where(finite, z, KS_ZMIN)
-    idx = np.floor((zc - KS_ZMIN) * (KS_BINS / (KS_ZMAX - KS_ZMIN))).astype(np.int64)
-    idx = np.clip(idx, 0, KS_BINS - 1)
+    bt = np.dtype(bin_dtype).type
+    ab = np.asarray(amps).ravel()
+    re, im = ab.real.astype(bt), ab.imag.astype(bt)
+    pb = re * re + im * im
+    with np.errstate(divide="ignore", invalid="ignore"):
+        zb = np.log(pb * bt(scale))
+        fb = (zb - bt(KS_ZMIN)) * bt(KS_BINS / (KS_ZMAX - KS_ZMIN))
+    fb = np.where(fb > 0, fb, 0)
+    idx = np.minimum(np.floor(fb), KS_BINS - 1).astype(np.int64)
     hist = np.bincount(idx, minlength=KS_BINS)
     ks = ks_from_hist(hist)
     return np.array([norm, mean_w, mean_ln, ks]), hist

@@ -440,6 +440,7 @@ int evolve_c64_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t*
     SweepLaunch sl;
     sl.n = n;
     sl.k = pd.k;
+    sl.low = pd.low;
     sl.local_mask = pd.local_mask;
     sl.ops = P.d_ops[h] + pd.op_begin;
     sl.op_count = pd.op_count;

@@ -81,16 +81,19 @@ __global__ void __launch_bounds__(256) fp64_gemm_kernel(const T* __restrict__ L,
 }
 
 // bin of z on [SIM_KS_ZMIN, SIM_KS_ZMAX); -inf (a zero amplitude) and anything
-// below go to bin 0, anything above to the last bin
+// below go to bin 0, anything above to the last bin.  The bin is decided in fp32
+// with separately rounded add and multiply (no fused multiply-add), so a host
+// check can repeat the decision exactly.
 __device__ __forceinline__ int ks_bin(float z) {
-  const float f = (z - (float)SIM_KS_ZMIN) * ((float)SIM_KS_BINS / (float)(SIM_KS_ZMAX - SIM_KS_ZMIN));
+  const float f = __fmul_rn(__fadd_rn(z, -(float)SIM_KS_ZMIN),
+                            (float)SIM_KS_BINS / (float)(SIM_KS_ZMAX - SIM_KS_ZMIN));
   if (!(f > 0.f)) return 0;
   if (f >= (float)SIM_KS_BINS) return SIM_KS_BINS - 1;
   return (int)f;
 }
 
 __device__ __forceinline__ int ks_bin_d(double z) {
-  const double f = (z - SIM_KS_ZMIN) * ((double)SIM_KS_BINS / (SIM_KS_ZMAX - SIM_KS_ZMIN));
+  const double f = __dmul_rn(__dadd_rn(z, -SIM_KS_ZMIN), (double)SIM_KS_BINS / (SIM_KS_ZMAX - SIM_KS_ZMIN));
   if (!(f > 0.0)) return 0;  // includes -inf (zero amplitude) and NaN
   if (f >= (double)SIM_KS_BINS) return SIM_KS_BINS - 1;
   return (int)floor(f);
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(256) stats_kernel(const void* amps, uint64_t c
     int cnt = 0, fnz = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += stride) {
       const float2 v = a[i];
-      const float p = v.x * v.x + v.y * v.y;
+      const float p = __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
       const float z = logf(p * sc);
       fp += p;
       if (p > 0.f) {
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(256) stats_kernel(const void* amps, uint64_t c
     const double sc = ldexp(1.0, nq);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += stride) {
       const double2 v = a[i];
-      const double p = v.x * v.x + v.y * v.y;
+      const double p = __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y));
       sp += p;
       const double z = p > 0.0 ? log(p * sc) : -INFINITY;
       if (p > 0.0) {

@@ -8,6 +8,7 @@
 #include <map>
 #include <set>
 #include <sstream>
+#include <stdexcept>
 
 #include "sim_internal.h"
 
@@ -268,20 +269,23 @@ void make_diags(int half, uint32_t tmask, const std::vector<std::pair<int, int>>
 
 // Greedy pass split of an op sequence: each pass stages k local qubits, always
 // the low `low` bits (coalesced rows) plus the qubits of the upcoming gates in
-// order; a pass ends before the first gate whose qubit no longer fits.
+// order; a pass ends before the first gate whose qubit no longer fits.  With
+// k < n at most k - 1 low bits are reserved, so every pass takes at least the
+// gate it starts with.
 void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
                   std::vector<PassDesc>& passes, std::vector<OpRec>& ops) {
   const int k = std::min(n, kmax);
-  const int low = std::min(k, 5);
+  const int low = k < n ? std::min(5, k - 1) : std::min(5, k);
+  const uint32_t low_mask = (1u << low) - 1;
   size_t i = 0;
   bool first = true;
   if (seq.empty()) {
-    PassDesc p{k, (k >= 32 ? 0xFFFFFFFFu : ((1u << k) - 1)), (int)ops.size(), 0, first_src};
+    PassDesc p{k, low, (k >= 32 ? 0xFFFFFFFFu : ((1u << k) - 1)), (int)ops.size(), 0, first_src};
     passes.push_back(p);
     return;
   }
   while (i < seq.size()) {
-    uint32_t local = (low >= 32) ? 0xFFFFFFFFu : ((1u << low) - 1);
+    uint32_t local = low_mask;
     int cnt = low;
     size_t j = i;
     for (; j < seq.size(); ++j) {
@@ -292,11 +296,13 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
       local |= bit;
       ++cnt;
     }
+    if (j == i) throw std::logic_error("pass split made no progress");
     // fill the remaining local slots with the lowest unused qubits
     for (int q = 0; q < n && cnt < k; ++q)
       if (!(local & (1u << q))) { local |= 1u << q; ++cnt; }
     PassDesc p;
     p.k = k;
+    p.low = low;
     p.local_mask = local;
     p.op_begin = (int)ops.size();
     p.op_count = (int)(j - i);

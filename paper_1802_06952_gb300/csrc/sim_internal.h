@@ -62,6 +62,7 @@ enum PassSrc : int { SRC_SELF = 0, SRC_PARENT = 1, SRC_UNIFORM = 2, SRC_ZERO = 3
 
 struct PassDesc {
   int k;
+  int low;              // low bits 0..low-1 are local (coalesced global rows)
   uint32_t local_mask;
   int op_begin, op_count;
   int src;
@@ -130,7 +131,7 @@ struct NodeEntry {
 };
 
 struct SweepLaunch {
-  int n, k;
+  int n, k, low;
   uint32_t local_mask;
   const OpRec* ops;       // device pointer to the pass's first op
   int op_count;

@@ -245,7 +245,8 @@ cudaError_t launch_sweep_c64(const SweepLaunch& L, cudaStream_t s) {
   memset(&a, 0, sizeof a);
   a.n = L.n;
   a.k = L.k;
-  a.low = L.k < 5 ? L.k : 5;
+  a.low = L.low;
+  if (a.low < 0 || a.low > 5 || a.low > L.k) return cudaErrorInvalidValue;
   a.local_mask = L.local_mask;
   a.ops = L.ops;
   a.op_count = L.op_count;
