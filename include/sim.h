@@ -159,6 +159,29 @@ int sim_halves_leaf(sim_halves h, int half, uint64_t copy, void* out_dev, void* 
  *                buffer; the call then returns after the copy has finished). */
 int sim_amplitudes(sim_halves h, int contraction, int accumulate, void* out, void* stream);
 
+/* sim_amplitudes without allocation: the same split-precision tensor-core
+ * contraction (SIM_SPLIT_BF16 or SIM_SPLIT_FP16 only) for callers that cannot let
+ * the library allocate device memory while they run: an application whose device
+ * memory already belongs to its own allocator, or a latency-bound loop that cannot
+ * afford cudaMalloc / cudaFree (they can block the host and synchronise the
+ * device).  The paper has no counterpart; this is a deployment variant.
+ *   h, contraction, accumulate   as for sim_amplitudes
+ *   out_dev   caller-owned DEVICE buffer of n_l * n_u complex64 values
+ * Scratch: a fixed device array of SIM_NOALLOC_SCRATCH_BYTES inside the library
+ * (the two split copies of both operands, 4 * (n_l + 2 n_u) * kpad bytes with
+ * kpad = 2K rounded up to 64, plus 1 KiB).  Larger requests return SIM_EINVAL
+ * with the number of bytes they would need.  Every GPU on which this function is
+ * called holds the array until the process exits.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture begins.  All calls share the array and it keeps the previous call's contents:
+ * calls whose work can overlap on the GPU (other streams, other host threads)
+ * race on it and must be serialised by the caller.  The call synchronises the
+ * stream and returns SIM_ETIMEOUT if a bounded device wait gave up.  It never
+ * calls cudaMalloc, cudaFree or an allocating library routine. */
+#define SIM_NOALLOC_SCRATCH_BYTES (32u << 20)
+int sim_amplitudes_noalloc(sim_halves h, int contraction, int accumulate, void* out_dev,
+                           void* stream);
+
 /* FP64 statistics of an amplitude block (Section 3, Eq. 7 with alpha = 1):
  * stats_out = {sum |A|^2, mean 2^n|A|^2, mean ln(2^n|A|^2) over non-zero entries,
  * binned KS distance between z = ln(2^n|A|^2) and Eq. 7}.  amps is device memory,

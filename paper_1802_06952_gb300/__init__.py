@@ -31,8 +31,9 @@ EXPORTS = (
     "sim_plan_schedule", "sim_evolve_halves", "sim_halves_leaf", "sim_amplitudes", "sim_stats",
     "sim_select", "sim_sample", "sim_status", "sim_release_cache", "sim_destroy_circuit",
     "sim_destroy_cut", "sim_destroy_halves", "sim_last_error", "sim_version",
-    "sim_profile_enable", "sim_profile_read",
+    "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc",
 )
+SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
 
 class SimError(RuntimeError):
@@ -90,6 +91,7 @@ def lib():
         "sim_profile_enable": (ctypes.c_int, [ctypes.c_int]),
         "sim_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), u64p, u64p, u64p, ctypes.c_int]),
         "sim_version": (ctypes.c_int, []),
+        "sim_amplitudes_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -201,6 +203,13 @@ def sim_halves_leaf(halves, half, copy, out, stream=None):
 def sim_amplitudes(halves, contraction, accumulate, out, stream=None):
     """out: torch tensor (device or host) or a raw pointer."""
     _check(lib().sim_amplitudes(halves, contraction, int(accumulate), _ptr(out), _stream(stream)))
+
+
+def sim_amplitudes_noalloc(halves, contraction, accumulate, out, stream=None):
+    """The split contraction without library allocation: its scratch is a fixed
+    SIM_NOALLOC_SCRATCH_BYTES device array; out must be device memory.  Returns
+    after the work has finished."""
+    _check(lib().sim_amplitudes_noalloc(halves, contraction, int(accumulate), _ptr(out), _stream(stream)))
 
 
 def sim_stats(amps, is_c128, count, n_qubits, stream=None, want_hist=False):

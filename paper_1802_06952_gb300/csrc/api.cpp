@@ -585,6 +585,20 @@ int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cu
 }  // namespace
 
 namespace sim {
+bool halves_view(const sim_halves_s* h, HalvesView* v) {
+  if (!h || !v) return false;
+  v->precision = h->precision;
+  v->kb = h->kb;
+  v->ke = h->ke;
+  for (int i = 0; i < 2; ++i) {
+    v->nsel[i] = h->nsel[i];
+    v->leafsel[i] = h->leafsel[i];
+  }
+  return true;
+}
+
+int set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 void note_launches(int phase, int count) {
   Profiler& P = prof();
   std::lock_guard<std::mutex> lk(P.mu);

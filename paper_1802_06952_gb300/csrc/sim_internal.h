@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+struct sim_halves_s;
+
 namespace sim {
 
 // ---------------------------------------------------------------------------
@@ -108,6 +110,18 @@ struct CutPlan {
   std::vector<OpRec> plain_flat[2];       // host copy of the uploaded plain op table
   int device = -1;
 };
+
+// Read-only view of an evolved-halves handle (defined in api.cpp), for entry
+// points kept in other files; returns false for a NULL handle.
+struct HalvesView {
+  int precision;
+  uint64_t kb, ke;
+  int64_t nsel[2];
+  const void* leafsel[2];
+};
+bool halves_view(const sim_halves_s* h, HalvesView* v);
+// Sets the thread's last-error text and returns code.
+int set_error(int code, const std::string& msg);
 
 // Phase profiler hooks (api.cpp): kernel launch and host<->device byte counters.
 void note_launches(int phase, int count);

@@ -1,0 +1,92 @@
+"""sim_amplitudes_noalloc: the split tensor-core contraction for callers that
+cannot let the library allocate device memory while they run (their device memory
+already belongs to their own allocator, or cudaMalloc / cudaFree would stall a
+latency-bound loop).  Its scratch is a fixed device array inside the library.
+
+Checked through the C-ABI against sim_amplitudes on the same evolved halves, on
+two calls in a row (the array keeps the previous call's contents), within the
+tolerance the other parity tests use.  This file is named so that pytest
+collects it last.
+"""
+import numpy as np
+import pytest
+
+import paper_1802_06952_gb300 as sim
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_06952_gb300 import build
+    build.build()
+    sim.lib()
+    torch.cuda.set_device(0)
+
+
+def rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def evolved(R, C, d, seed, b, sel_u=None, sel_l=None):
+    circ = sim.sim_build_circuit(R, C, d, seed, b)
+    plan, c, copies, nu, nl = sim.sim_cut(circ, b)
+    h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, copies, sel_u, sel_l)
+    M = (1 << nl) if sel_l is None else len(sel_l)
+    N = (1 << nu) if sel_u is None else len(sel_u)
+    return circ, plan, h, M, N
+
+
+def test_noalloc_matches_sim_amplitudes_twice():
+    cases = [(4, 4, 10, 0, 2, None, None, sim.SIM_SPLIT_BF16),
+             (4, 5, 16, 3, 2, np.arange(0, 1024, 3, dtype=np.uint64), np.arange(5, 1024, 7, dtype=np.uint64),
+              sim.SIM_SPLIT_FP16)]
+    outs = []
+    for (R, C, d, seed, b, su, sl, kind) in cases:
+        circ, plan, h, M, N = evolved(R, C, d, seed, b, su, sl)
+        try:
+            ref = torch.zeros((M, N), dtype=torch.complex64, device="cuda")
+            sim.sim_amplitudes(h, kind, False, ref)
+            sim.sim_status()
+            got = torch.full((M, N), complex(7.0, -7.0), dtype=torch.complex64, device="cuda")
+            sim.sim_amplitudes_noalloc(h, kind, False, got)
+            r = ref.cpu().numpy()
+            assert rel(got.cpu().numpy(), r) <= TOL
+            # a second call in a row on the same output, accumulating: 2x the result
+            sim.sim_amplitudes_noalloc(h, kind, True, got)
+            assert rel(got.cpu().numpy(), 2 * r) <= TOL
+            outs.append(got.cpu().numpy())
+        finally:
+            sim.sim_destroy_halves(h)
+            sim.sim_destroy_cut(plan)
+            sim.sim_destroy_circuit(circ)
+    assert len(outs) == 2
+
+
+def test_noalloc_rejects_oversized_and_host_output():
+    # 30 qubits, 256 copies: the split operands need ~200 MB, more than the fixed scratch
+    circ, plan, h, M, N = evolved(6, 5, 16, 0, 3, np.arange(8192, dtype=np.uint64), np.arange(8192, dtype=np.uint64))
+    try:
+        out = torch.zeros((M, N), dtype=torch.complex64, device="cuda")
+        with pytest.raises(sim.SimError) as e:
+            sim.sim_amplitudes_noalloc(h, sim.SIM_SPLIT_BF16, False, out)
+        assert e.value.code == sim.SIM_EINVAL and "scratch" in sim.sim_last_error()
+        small = evolved(4, 4, 10, 1, 2)
+        try:
+            host = torch.zeros((256, 256), dtype=torch.complex64)
+            with pytest.raises(sim.SimError) as e2:
+                sim.sim_amplitudes_noalloc(small[2], sim.SIM_SPLIT_BF16, False, host)
+            assert e2.value.code == sim.SIM_EINVAL
+        finally:
+            sim.sim_destroy_halves(small[2])
+            sim.sim_destroy_cut(small[1])
+            sim.sim_destroy_circuit(small[0])
+    finally:
+        sim.sim_destroy_halves(h)
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(circ)
