@@ -33,8 +33,8 @@ AMPS = 1 << NQ
 WORKLOAD = ("30-qubit 6x5 grid random circuit, depth 16, cut between rows 2 and 3: c=8, "
             "256 copies of two 15-qubit halves, all 2^30 amplitudes (32768 x 256 x 32768 contraction)")
 METRIC = "amplitudes/s at <=1e-5 rel err vs FP64 oracle"
-CPU_SAMPLE = 4096      # cpu_baseline: oracle on a 4096 x 4096 amplitude block
-REF_SAMPLE = 2048      # --impl reference: 2048 x 2048 block per step
+CPU_SAMPLE = (16384, 8192)   # cpu_baseline: oracle on a 16384 x 8192 block (1/8 of the vector)
+REF_SAMPLE = (4096, 4096)    # --impl reference: 4096 x 4096 block per step
 
 
 def parse():
@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--select", type=int, default=0,
+                    help="profiling case: contract only the first S upper x S lower indices (S*S amplitudes)")
     return ap.parse_args()
 
 
@@ -133,18 +135,21 @@ def traffic_from_profile(kernel_src):
 
 
 def cpu_baseline(seed=0, n=CPU_SAMPLE):
+    """The FP64 oracle on a bounded sample of the workload: all 256 copies of both
+    halves evolved, then an n[0] x n[1] (upper x lower) block of amplitudes summed."""
     import numpy as np
     import oracle
     from oracle import circuit as oc
+    nu, nl = n
     gates, plan = oc.grid_cut(R, C, DEPTH, seed, CUT_ROW)
-    su = np.arange(n, dtype=np.uint64) * np.uint64(7) % np.uint64(1 << plan.n_u)
-    sl = np.arange(n, dtype=np.uint64) * np.uint64(5) % np.uint64(1 << plan.n_l)
+    su = np.arange(nu, dtype=np.uint64) * np.uint64(7) % np.uint64(1 << plan.n_u)
+    sl = np.arange(nl, dtype=np.uint64) * np.uint64(5) % np.uint64(1 << plan.n_l)
     t = time.perf_counter()
     oracle.cut_amplitudes(plan, su, sl)
     dt = time.perf_counter() - t
-    return {"value": n * n / dt, "unit": "amplitudes/s", "cores": oracle.num_threads(), "kind": "oracle",
+    return {"value": nu * nl / dt, "unit": "amplitudes/s", "cores": oracle.num_threads(), "kind": "oracle",
             "sample": "seed %d, all 256 copies evolved in FP64, %d x %d amplitude block (1/%d of the vector), %.1f s"
-                      % (seed, n, n, AMPS // (n * n), dt)}
+                      % (seed, nu, nl, AMPS // (nu * nl), dt)}
 
 
 def run_reference(args):
@@ -152,27 +157,29 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
+    per = REF_SAMPLE[0] * REF_SAMPLE[1]
     for i in range(args.warmup):
         cpu_baseline(SEEDS[i % 4], REF_SAMPLE)
     times = []
     for i in range(args.steps):
         r = cpu_baseline(SEEDS[i % 4], REF_SAMPLE)
-        times.append(REF_SAMPLE * REF_SAMPLE / r["value"])
+        times.append(per / r["value"])
     tot = sum(times)
-    value = args.steps * REF_SAMPLE * REF_SAMPLE / tot
+    value = args.steps * per / tot
     line = {"metric": METRIC, "value": value, "unit": "amplitudes/s", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic: seeded random grid circuits (splitmix64 seeds 0-3)",
-            "config": {"workload": WORKLOAD, "sample_per_step": "%d x %d amplitude block" % (REF_SAMPLE, REF_SAMPLE)},
+            "config": {"workload": WORKLOAD, "sample_per_step": "%d x %d amplitude block" % REF_SAMPLE},
             "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": oracle.num_threads(), "kind": "oracle",
                              "sample": "%d x %d block of the 2^30 amplitudes per step, all 256 copies in FP64"
-                                       % (REF_SAMPLE, REF_SAMPLE)},
+                                       % REF_SAMPLE},
             "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def run_ours(args):
+    import numpy as np
     import torch
     import paper_1802_06952_gb300 as sim
     from paper_1802_06952_gb300 import build
@@ -185,17 +192,22 @@ def run_ours(args):
     build.build()
     sim.lib()
     stream = torch.cuda.Stream()
-    out = torch.empty((1 << 15, 1 << 15), dtype=torch.complex64, device="cuda")
+    S = args.select if args.select > 0 else (1 << 15)
+    sel = np.arange(S, dtype=np.uint64) if args.select > 0 else None
+    amps_step = S * S
+    out = torch.empty((S, S), dtype=torch.complex64, device="cuda")
 
     def step(i, target):
         seed = SEEDS[(i * world + rank) % len(SEEDS)]
         circ = sim.sim_build_circuit(R, C, DEPTH, seed, CUT_ROW)
         plan, c, copies, nu, nl = sim.sim_cut(circ, CUT_ROW)
-        h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, copies, stream=stream)
-        sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, target, stream=stream)
+        h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, copies, sel, sel, stream=stream)
         st = None
         if target.is_cuda:
-            st = sim.sim_stats(target, 0, AMPS, NQ, stream=stream)
+            # contraction with the FP64 statistics fused into its epilogue
+            st = sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_BF16, False, target, stream=stream)
+        else:
+            sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, target, stream=stream)
         sim.sim_destroy_halves(h)
         sim.sim_destroy_cut(plan)
         sim.sim_destroy_circuit(circ)
@@ -240,12 +252,12 @@ def run_ours(args):
     sim.sim_status(stream)
     total_ms = max_over_ranks(e0.elapsed_time(e1))
     step_ms = [a.elapsed_time(b) for a, b in per]
-    value = world * args.steps * AMPS / (total_ms / 1e3)
+    value = world * args.steps * amps_step / (total_ms / 1e3)
     ms, inst, launches = prof["ms"], prof["instances"], prof["launches"]
 
     # dominant kernel: the tcgen05 contraction
     K = 256
-    M = N = 1 << 15
+    M = N = S
     flops = 24.0 * M * N * K                      # issued bf16 flops (3 split products)
     gemm_ms = ms[sim.SIM_PHASE_CONTRACT] / max(1, inst[sim.SIM_PHASE_CONTRACT])
     hbm, bf16, bf16_sus, src = peaks()
@@ -281,7 +293,7 @@ def run_ours(args):
 
     # end to end through the C-ABI with a host output buffer
     if not args.no_e2e:
-        host = torch.empty((1 << 15, 1 << 15), dtype=torch.complex64).pin_memory()
+        host = torch.empty((S, S), dtype=torch.complex64).pin_memory()
         for i in range(min(2, args.warmup)):
             step(i, host)
         sim.sim_profile_read(reset=True)
@@ -296,13 +308,15 @@ def run_ours(args):
         sim.sim_profile_enable(False)
         eprof = sim.sim_profile_read(reset=True)
         te = max_over_ranks(t1 - t0)
-        line["e2e"] = {"value": world * ke * AMPS / te, "unit": "amplitudes/s",
+        line["e2e"] = {"value": world * ke * amps_step / te, "unit": "amplitudes/s",
                        "h2d_bytes_per_step": int(eprof["h2d"]) // ke, "d2h_bytes_per_step": int(eprof["d2h"]) // ke,
                        "steps": ke, "note": "sim_amplitudes into pinned host memory (library staging + copy), "
                                             "circuit description in from the host; wall clock"}
         del host
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+    if args.select > 0:
+        line["config"]["workload"] = "PROFILING CASE (not the benchmark): first %d x %d indices of the 30-qubit workload" % (S, S)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -182,17 +182,26 @@ int sim_amplitudes(sim_halves h, int contraction, int accumulate, void* out, voi
 int sim_amplitudes_noalloc(sim_halves h, int contraction, int accumulate, void* out_dev,
                            void* stream);
 
-/* FP64 statistics of an amplitude block (Section 3, Eq. 7 with alpha = 1):
- * stats_out = {sum |A|^2, mean 2^n|A|^2, mean ln(2^n|A|^2) over non-zero entries,
- * binned KS distance between z = ln(2^n|A|^2) and Eq. 7}.  amps is device memory,
- * complex64 (is_c128 = 0) or complex128 (is_c128 = 1).  hist_out (may be NULL)
- * receives SIM_KS_BINS counts of z over [SIM_KS_ZMIN, SIM_KS_ZMAX), end bins
- * clamped.  Synchronises the stream. */
+/* Statistics of an amplitude block (Section 3, Eq. 7 with alpha = 1), summed in
+ * FP64.  With w = 2^n |A|^2 and z = ln w, Eq. 7 is the density exp(z - e^z) whose
+ * CDF is F(z) = 1 - exp(-w); u = F(z) is uniform on [0, 1) under that law.
+ * stats_out = {sum |A|^2, mean w, mean ln w over entries with w > 0,
+ * KS distance max_b |G(u_b) - u_b| between the empirical CDF G of u and the
+ * uniform CDF at the SIM_KS_BINS bin edges u_b = (b+1) / SIM_KS_BINS}.
+ * amps is device memory, complex64 (is_c128 = 0; per-entry work in fp32) or
+ * complex128 (is_c128 = 1; FP64 throughout).  hist_out (may be NULL) receives the
+ * SIM_KS_BINS counts of u.  Synchronises the stream. */
 #define SIM_KS_BINS 4096
-#define SIM_KS_ZMIN (-24.0)
-#define SIM_KS_ZMAX (8.0)
 int sim_stats(const void* amps, int is_c128, uint64_t count, int n_qubits,
               double stats_out[4], uint64_t* hist_out, void* stream);
+
+/* sim_amplitudes followed by the statistics of sim_stats over the n_l * n_u values
+ * it wrote (the accumulated values when accumulate = 1), with n the circuit's qubit
+ * count.  For the split contractions the statistics are computed inside the
+ * contraction's epilogue from the fp32 results, so the amplitudes are not read
+ * back from memory.  out must be device memory.  Synchronises the stream. */
+int sim_amplitudes_stats(sim_halves h, int contraction, int accumulate, void* out_dev,
+                         double stats_out[4], uint64_t* hist_out, void* stream);
 
 /* Draw the amplitude selection used by sim_sample (Section 3: "sampling" of state
  * components): n_u distinct upper indices of [0, 2^{nq_u}), then n_l distinct lower

@@ -178,58 +178,42 @@ def select(n_u_qubits, n_sel_u, n_l_qubits, n_sel_l, seed):
 
 
 KS_BINS = 4096
-KS_ZMIN = -24.0
-KS_ZMAX = 8.0
 
 
 def gumbel_cdf(z):
-    """CDF of Eq. 7 with alpha = 1: integral of exp(z - e^z) = 1 - exp(-e^z)."""
+    """CDF of Eq. 7 with alpha = 1: the integral of exp(z - e^z) is 1 - exp(-e^z)."""
     return 1.0 - np.exp(-np.exp(z))
 
 
-def stats(amps, n_qubits, bin_dtype=np.float64):
+def stats(amps, n_qubits):
     """Section 3 statistics over a block of amplitudes, FP64:
-    [sum |A|^2, mean 2^n|A|^2, mean ln(2^n|A|^2), binned KS distance to Eq. 7].
+    [sum |A|^2, mean w, mean ln w over w > 0, binned KS distance to Eq. 7],
+    with w = 2^n |A|^2 and z = ln w.
 
-    The KS distance is taken over KS_BINS equal bins of z = ln(2^n |A|^2) on
-    [KS_ZMIN, KS_ZMAX] (values outside are clamped to the end bins): the largest
-    gap between the empirical and the Eq. 7 CDF at the bin edges.  The bin of each
-    entry is decided in ``bin_dtype`` arithmetic (|A|^2, the logarithm and the
-    bin coordinate (z - KS_ZMIN) * KS_BINS / (KS_ZMAX - KS_ZMIN), each operation
-    rounded separately), so a check can take the decision in the precision of the
-    code it is compared with; the sums are FP64 either way.
+    Eq. 7 (alpha = 1) has the CDF F(z) = 1 - exp(-e^z) = 1 - exp(-w), so u = F(z)
+    is uniform on [0, 1) if z follows Eq. 7.  The KS distance is taken between the
+    empirical CDF of u and the uniform CDF at the KS_BINS equal bin edges of u.
+    Returns (stats, histogram of u).
     """
     a = np.asarray(amps).astype(np.complex128).ravel()
-    p = (a.real * a.real + a.imag * a.imag)
-    scale = math.ldexp(1.0, n_qubits)
+    p = a.real * a.real + a.imag * a.imag
+    w = p * math.ldexp(1.0, n_qubits)
     norm = float(p.sum())
-    w = p * scale
     mean_w = float(w.mean())
-    with np.errstate(divide="ignore"):
-        z = np.log(w)
-    finite = np.isfinite(z)
-    mean_ln = float(z[finite].mean()) if finite.any() else float("-inf")
-    bt = np.dtype(bin_dtype).type
-    ab = np.asarray(amps).ravel()
-    re, im = ab.real.astype(bt), ab.imag.astype(bt)
-    pb = re * re + im * im
-    with np.errstate(divide="ignore", invalid="ignore"):
-        zb = np.log(pb * bt(scale))
-        fb = (zb - bt(KS_ZMIN)) * bt(KS_BINS / (KS_ZMAX - KS_ZMIN))
-    fb = np.where(fb > 0, fb, 0)
-    idx = np.minimum(np.floor(fb), KS_BINS - 1).astype(np.int64)
+    pos = w > 0
+    mean_ln = float(np.log(w[pos]).mean()) if pos.any() else float("-inf")
+    u = -np.expm1(-w)
+    idx = np.minimum(np.floor(u * KS_BINS), KS_BINS - 1).astype(np.int64)
     hist = np.bincount(idx, minlength=KS_BINS)
-    ks = ks_from_hist(hist)
-    return np.array([norm, mean_w, mean_ln, ks]), hist
+    return np.array([norm, mean_w, mean_ln, ks_from_hist(hist)]), hist
 
 
 def ks_from_hist(hist):
+    """max_b |G(u_b) - u_b| at the bin edges u_b = (b + 1) / KS_BINS."""
     hist = np.asarray(hist, dtype=np.float64)
     tot = hist.sum()
     if tot == 0:
         return 0.0
-    edges = KS_ZMIN + (KS_ZMAX - KS_ZMIN) * np.arange(1, KS_BINS + 1) / KS_BINS
+    edges = np.arange(1, KS_BINS + 1) / KS_BINS
     emp = np.cumsum(hist) / tot
-    theo = gumbel_cdf(edges)
-    theo[-1] = 1.0  # the last bin absorbs everything above KS_ZMAX
-    return float(np.max(np.abs(emp - theo)))
+    return float(np.max(np.abs(emp - edges)))

@@ -31,7 +31,7 @@ EXPORTS = (
     "sim_plan_schedule", "sim_evolve_halves", "sim_halves_leaf", "sim_amplitudes", "sim_stats",
     "sim_select", "sim_sample", "sim_status", "sim_release_cache", "sim_destroy_circuit",
     "sim_destroy_cut", "sim_destroy_halves", "sim_last_error", "sim_version",
-    "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc",
+    "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc", "sim_amplitudes_stats",
 )
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -92,6 +92,8 @@ def lib():
         "sim_profile_read": (ctypes.c_int, [ctypes.POINTER(ctypes.c_double), u64p, u64p, u64p, ctypes.c_int]),
         "sim_version": (ctypes.c_int, []),
         "sim_amplitudes_noalloc": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
+        "sim_amplitudes_stats": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_double),
+                                                u64p, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -210,6 +212,18 @@ def sim_amplitudes_noalloc(halves, contraction, accumulate, out, stream=None):
     SIM_NOALLOC_SCRATCH_BYTES device array; out must be device memory.  Returns
     after the work has finished."""
     _check(lib().sim_amplitudes_noalloc(halves, contraction, int(accumulate), _ptr(out), _stream(stream)))
+
+
+def sim_amplitudes_stats(halves, contraction, accumulate, out, stream=None, want_hist=False):
+    """sim_amplitudes into device memory plus the statistics of the written block
+    (fused into the split contraction's epilogue).  Returns stats (and the histogram)."""
+    st = (ctypes.c_double * 4)()
+    hist = np.zeros(SIM_KS_BINS, dtype=np.uint64) if want_hist else None
+    _check(lib().sim_amplitudes_stats(halves, contraction, int(accumulate), _ptr(out), st,
+                                      hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if want_hist else None,
+                                      _stream(stream)))
+    out_st = np.array(st[:], dtype=np.float64)
+    return (out_st, hist) if want_hist else out_st
 
 
 def sim_stats(amps, is_c128, count, n_qubits, stream=None, want_hist=False):

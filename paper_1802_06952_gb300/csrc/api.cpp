@@ -531,15 +531,27 @@ int check_device_status(DeviceInfo* di) {
   return SIM_OK;
 }
 
-int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cudaStream_t st) {
+// Contraction into device memory; with st_acc / st_hist (zeroed by the caller)
+// also the statistics of the written block (fused into the split contraction's
+// epilogue; a separate pass after the FP64 contraction).
+int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cudaStream_t st,
+                    double* st_acc = nullptr, unsigned long long* st_hist = nullptr) {
   DeviceInfo* di = nullptr;
   int rc = device_info(&di);
   if (rc) return rc;
   const int64_t M = h->nsel[1], N = h->nsel[0];
   const int64_t K = (int64_t)(h->ke - h->kb);
+  const int nq = h->plan->circ.n;
   if (contraction == SIM_FP64_PLAIN) {
-    PhaseScope ps(SIM_PHASE_FP64_GEMM, st);
-    CK(launch_fp64_gemm(h->leafsel[1], h->leafsel[0], h->precision == SIM_C128_PLAIN, K, M, N, accumulate, out, st));
+    {
+      PhaseScope ps(SIM_PHASE_FP64_GEMM, st);
+      CK(launch_fp64_gemm(h->leafsel[1], h->leafsel[0], h->precision == SIM_C128_PLAIN, K, M, N, accumulate, out,
+                          st));
+    }
+    if (st_acc && st_hist) {
+      PhaseScope ps(SIM_PHASE_STATS, st);
+      CK(launch_stats(out, 1, (uint64_t)(M * N), nq, st_acc, st_hist, st));
+    }
     return SIM_OK;
   }
   if (contraction != SIM_SPLIT_BF16 && contraction != SIM_SPLIT_FP16)
@@ -577,9 +589,32 @@ int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cu
   g.group_m = 0;
   g.num_sms = di->num_sms;
   g.d_status = di->d_status;
+  g.w_scale = std::ldexp(1.f, nq);
+  g.st_acc = st_acc;
+  g.st_hist = st_hist;
   PhaseScope ps(SIM_PHASE_CONTRACT, st);
   CK(launch_tc_gemm(g, st));
   return SIM_OK;
+}
+
+// stats_out from the FP64 sums {sum |A|^2, sum ln w, count of w > 0} and the
+// histogram of u = 1 - exp(-w): KS distance to the uniform CDF at the bin edges.
+void finish_stats(const double a[3], const std::vector<unsigned long long>& hh, uint64_t count, int nq,
+                  double stats_out[4], uint64_t* hist_out) {
+  stats_out[0] = a[0];
+  stats_out[1] = count ? a[0] * std::ldexp(1.0, nq) / (double)count : 0.0;
+  stats_out[2] = a[2] > 0 ? a[1] / a[2] : -INFINITY;
+  double tot = 0;
+  for (auto v : hh) tot += (double)v;
+  double ks = 0, cum = 0;
+  for (int b = 0; b < SIM_KS_BINS; ++b) {
+    cum += (double)hh[b];
+    const double edge = (double)(b + 1) / SIM_KS_BINS;
+    if (tot > 0) ks = std::max(ks, std::fabs(cum / tot - edge));
+  }
+  stats_out[3] = ks;
+  if (hist_out)
+    for (int b = 0; b < SIM_KS_BINS; ++b) hist_out[b] = hh[b];
 }
 
 }  // namespace
@@ -854,22 +889,31 @@ int sim_stats(const void* amps, int is_c128, uint64_t count, int n_qubits, doubl
   CK(cudaMemcpyAsync(a, acc.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaMemcpyAsync(hh.data(), hist.p, SIM_KS_BINS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
-  stats_out[0] = a[0];
-  stats_out[1] = count ? a[0] * std::ldexp(1.0, n_qubits) / (double)count : 0.0;
-  stats_out[2] = a[2] > 0 ? a[1] / a[2] : -INFINITY;
-  // KS distance to Eq. 7 (alpha = 1): F(z) = 1 - exp(-e^z) at the bin edges
-  double tot = 0;
-  for (auto v : hh) tot += (double)v;
-  double ks = 0, cum = 0;
-  for (int b = 0; b < SIM_KS_BINS; ++b) {
-    cum += (double)hh[b];
-    const double edge = SIM_KS_ZMIN + (SIM_KS_ZMAX - SIM_KS_ZMIN) * (double)(b + 1) / SIM_KS_BINS;
-    const double F = b == SIM_KS_BINS - 1 ? 1.0 : 1.0 - std::exp(-std::exp(edge));
-    if (tot > 0) ks = std::max(ks, std::fabs(cum / tot - F));
-  }
-  stats_out[3] = ks;
-  if (hist_out)
-    for (int b = 0; b < SIM_KS_BINS; ++b) hist_out[b] = hh[b];
+  finish_stats(a, hh, count, n_qubits, stats_out, hist_out);
+  return SIM_OK;
+  API_END
+}
+
+int sim_amplitudes_stats(sim_halves h, int contraction, int accumulate, void* out_dev, double stats_out[4],
+                         uint64_t* hist_out, void* stream) {
+  API_BEGIN
+  if (!h || !out_dev || !stats_out) return fail(SIM_EINVAL, "halves, out_dev and stats_out must not be NULL");
+  if (!is_device_ptr(out_dev)) return fail(SIM_EINVAL, "sim_amplitudes_stats writes device memory only");
+  cudaStream_t st = (cudaStream_t)stream;
+  DevBuf acc, hist;
+  CK(acc.alloc(4 * sizeof(double)));
+  CK(hist.alloc(SIM_KS_BINS * sizeof(unsigned long long)));
+  CK(cudaMemsetAsync(acc.p, 0, 3 * sizeof(double), st));
+  CK(cudaMemsetAsync(hist.p, 0, SIM_KS_BINS * sizeof(unsigned long long), st));
+  int rc = amplitudes_impl(h, contraction, accumulate, out_dev, st, acc.as<double>(), hist.as<unsigned long long>());
+  if (rc) return rc;
+  note_bytes(0, 3 * sizeof(double) + SIM_KS_BINS * sizeof(unsigned long long));
+  double a[3];
+  std::vector<unsigned long long> hh(SIM_KS_BINS);
+  CK(cudaMemcpyAsync(a, acc.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(hh.data(), hist.p, SIM_KS_BINS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  finish_stats(a, hh, (uint64_t)h->nsel[0] * (uint64_t)h->nsel[1], h->plan->circ.n, stats_out, hist_out);
   return SIM_OK;
   API_END
 }
@@ -900,8 +944,10 @@ int sim_sample(sim_cut_plan plan, uint64_t n_u, uint64_t n_l, uint64_t seed, uin
   sim_halves h = nullptr;
   rc = sim_evolve_halves(plan, SIM_C64, 0, 1ull << P.c, sel_u_out, uu, sel_l_out, ll, opts, stream, &h);
   if (rc) return rc;
-  rc = sim_amplitudes(h, SIM_SPLIT_BF16, 0, amps_dev_out, stream);
-  if (rc == SIM_OK && stats_out) rc = sim_stats(amps_dev_out, 0, uu * ll, P.circ.n, stats_out, nullptr, stream);
+  if (stats_out)
+    rc = sim_amplitudes_stats(h, SIM_SPLIT_BF16, 0, amps_dev_out, stats_out, nullptr, stream);
+  else
+    rc = sim_amplitudes(h, SIM_SPLIT_BF16, 0, amps_dev_out, stream);
   sim_destroy_halves(h);
   if (rc) return rc;
   return sim_status(stream);

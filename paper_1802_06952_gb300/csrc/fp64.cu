@@ -3,7 +3,7 @@
 //                     (Supplementary A, Eq. 8) with complex128 products and sums on
 //                     CUDA cores: 64 x 64 output tiles, 256 threads, 4 x 4 outputs each
 //   stats_kernel      the Section 3 statistics of an amplitude block (norm, mean of
-//                     2^n|A|^2, mean of ln 2^n|A|^2, histogram of z = ln 2^n|A|^2 for the
+//                     w = 2^n|A|^2, mean of ln w, histogram of u = 1 - exp(-w) for the
 //                     KS distance to Eq. 7): per-element work in the input precision,
 //                     running sums in FP64.
 #include <cuda_runtime.h>
@@ -80,23 +80,18 @@ __global__ void __launch_bounds__(256) fp64_gemm_kernel(const T* __restrict__ L,
   }
 }
 
-// bin of z on [SIM_KS_ZMIN, SIM_KS_ZMAX); -inf (a zero amplitude) and anything
-// below go to bin 0, anything above to the last bin.  The bin is decided in fp32
-// with separately rounded add and multiply (no fused multiply-add), so a host
-// check can repeat the decision exactly.
-__device__ __forceinline__ int ks_bin(float z) {
-  const float f = __fmul_rn(__fadd_rn(z, -(float)SIM_KS_ZMIN),
-                            (float)SIM_KS_BINS / (float)(SIM_KS_ZMAX - SIM_KS_ZMIN));
-  if (!(f > 0.f)) return 0;
-  if (f >= (float)SIM_KS_BINS) return SIM_KS_BINS - 1;
-  return (int)f;
+// Bin of u = 1 - exp(-w) (the Eq. 7 CDF, alpha = 1, at z = ln w) on [0, 1) in
+// SIM_KS_BINS equal bins; u = 1 goes to the last bin.  complex64 blocks use the
+// same fp32 arithmetic as the contraction's fused statistics.
+__device__ __forceinline__ int u_bin(float w) {
+  int b = (int)((1.f - __expf(-w)) * (float)SIM_KS_BINS);
+  return b < 0 ? 0 : (b > SIM_KS_BINS - 1 ? SIM_KS_BINS - 1 : b);
 }
 
-__device__ __forceinline__ int ks_bin_d(double z) {
-  const double f = __dmul_rn(__dadd_rn(z, -SIM_KS_ZMIN), (double)SIM_KS_BINS / (SIM_KS_ZMAX - SIM_KS_ZMIN));
-  if (!(f > 0.0)) return 0;  // includes -inf (zero amplitude) and NaN
-  if (f >= (double)SIM_KS_BINS) return SIM_KS_BINS - 1;
-  return (int)floor(f);
+__device__ __forceinline__ int u_bin_d(double w) {
+  const double u = -expm1(-w);
+  int b = (int)(u * (double)SIM_KS_BINS);
+  return b < 0 ? 0 : (b > SIM_KS_BINS - 1 ? SIM_KS_BINS - 1 : b);
 }
 
 template <bool C128>
@@ -110,38 +105,38 @@ __global__ void __launch_bounds__(256) stats_kernel(const void* amps, uint64_t c
   if (!C128) {
     const float2* a = (const float2*)amps;
     const float sc = ldexpf(1.f, nq);
-    float fp = 0.f, fl = 0.f;
-    int cnt = 0, fnz = 0;
+    float fp = 0.f, fl = 0.f, fn = 0.f;
+    int cnt = 0;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += stride) {
       const float2 v = a[i];
-      const float p = __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y));
-      const float z = logf(p * sc);
+      const float p = fmaf(v.x, v.x, v.y * v.y);
+      const float w = p * sc;
       fp += p;
-      if (p > 0.f) {
-        fl += z;
-        ++fnz;
+      if (w > 0.f) {
+        fl += __logf(w);
+        fn += 1.f;
       }
-      atomicAdd(&sh[ks_bin(z)], 1u);
+      atomicAdd(&sh[u_bin(w)], 1u);
       if (++cnt == 32) {
-        sp += fp; sl += fl; nz += fnz;
-        fp = fl = 0.f;
-        cnt = fnz = 0;
+        sp += fp; sl += fl; nz += fn;
+        fp = fl = fn = 0.f;
+        cnt = 0;
       }
     }
-    sp += fp; sl += fl; nz += fnz;
+    sp += fp; sl += fl; nz += fn;
   } else {
     const double2* a = (const double2*)amps;
     const double sc = ldexp(1.0, nq);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += stride) {
       const double2 v = a[i];
-      const double p = __dadd_rn(__dmul_rn(v.x, v.x), __dmul_rn(v.y, v.y));
+      const double p = v.x * v.x + v.y * v.y;
+      const double w = p * sc;
       sp += p;
-      const double z = p > 0.0 ? log(p * sc) : -INFINITY;
-      if (p > 0.0) {
-        sl += z;
+      if (w > 0.0) {
+        sl += log(w);
         nz += 1.0;
       }
-      atomicAdd(&sh[ks_bin_d(z)], 1u);
+      atomicAdd(&sh[u_bin_d(w)], 1u);
     }
   }
   for (int o = 16; o > 0; o >>= 1) {

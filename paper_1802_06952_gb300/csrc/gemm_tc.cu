@@ -10,9 +10,9 @@
 //   warp 1       TMEM allocator and MMA issuer: tcgen05.mma.cta_group::1.kind::f16,
 //                M=128, N=256, K=16, two 256-column fp32 accumulators in TMEM so the
 //                epilogue of one tile overlaps the main loop of the next
-//   warps 2..5   epilogue: tcgen05.ld 32 lanes x 32 columns, output scale, staging
-//                through swizzled shared memory, coalesced streaming stores (or
-//                load-add-store when accumulating)
+//   warps 2..9   epilogue: tcgen05.ld 32 lanes x 16 columns, output scale, optional
+//                fused statistics, staging through swizzled shared memory,
+//                coalesced streaming stores (or load-add-store when accumulating)
 // Every mbarrier wait is bounded (about two seconds of global time); a wait that
 // gives up records an error in *d_status and makes every role leave its loop, wait
 // (bounded) for its own copies and MMAs in flight, and release tensor memory.
@@ -36,12 +36,14 @@ constexpr int STAGES = 4;
 constexpr int UMMA_K = 16;
 constexpr int A_BYTES = BM * BK * 2;   // 16 KB
 constexpr int B_BYTES = BN * BK * 2;   // 32 KB
-constexpr int EPI_WARPS = 4;
+constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (2 + EPI_WARPS);
 constexpr int ACC_COLS = BN;           // fp32 accumulator columns per tile
 constexpr int TMEM_COLS = 2 * ACC_COLS;
-constexpr int EPI_BYTES = EPI_WARPS * 32 * 128;  // 32 rows x 32 fp32 per warp
-constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * (A_BYTES + B_BYTES) + EPI_BYTES + 256;
+constexpr int EPI_BYTES = EPI_WARPS * 32 * 64;   // 32 rows x 16 fp32 per warp
+constexpr int HIST_BYTES = SIM_KS_BINS * 4;       // per-CTA histogram of the fused statistics
+constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * (A_BYTES + B_BYTES) + EPI_BYTES + HIST_BYTES + 256;
+static_assert(SMEM_BYTES <= 232448, "shared memory above the 227 KB per-block limit");
 
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
 
@@ -152,16 +154,15 @@ __device__ __forceinline__ void umma_commit(uint32_t bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+// 32 TMEM lanes x 16 consecutive 32-bit columns; thread i of the warp gets lane
+// (quarter base + i), register j = column j
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -191,8 +192,13 @@ struct KernelArgs {
   float* C;
   int vec4;              // C rows 16-byte aligned -> float4 stores
   int* d_status;
+  // fused statistics (Section 3, Eq. 7), when the STATS variant runs:
+  float w_scale;                   // 2^n: w = 2^n |A|^2
+  double* st_acc;                  // [sum |A|^2, sum ln w over w > 0, count of w > 0]
+  unsigned long long* st_hist;     // SIM_KS_BINS counts of u = 1 - exp(-w)
 };
 
+template <bool STATS>
 __global__ void __launch_bounds__(THREADS, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constant__ CUtensorMap mapA_lo,
                    const __grid_constant__ CUtensorMap mapB_hi, const __grid_constant__ CUtensorMap mapB_lo,
@@ -210,9 +216,12 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* mma_done = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  unsigned int* s_hist = (unsigned int*)((uint8_t*)bars + 256);
 
   const int warp = threadIdx.x / 32;
   const int lane = threadIdx.x % 32;
+  if (STATS)
+    for (int i = threadIdx.x; i < SIM_KS_BINS; i += THREADS) s_hist[i] = 0u;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -333,11 +342,16 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ---------------- epilogue ----------------
-    const int q = warp & 3;                   // TMEM lane quarter this warp may access
-    float* stage_buf = sEpi + (warp - 2) * (32 * 32);
+    // 8 warps: warp w reads TMEM lane quarter (w % 4) (rows 32q .. 32q+31 of the
+    // tile) and one half of the tile's 256 columns, 16 columns per tcgen05.ld
+    const int e = warp - 2;
+    const int q = warp & 3;
+    const int chalf = e >> 2;
+    float* stage_buf = sEpi + e * (32 * 16);
     const float sa = args.scale_a ? *args.scale_a : 1.f;
     const float sb = args.scale_b ? *args.scale_b : 1.f;
     const float oscale = 1.f / (sa * sb);
+    double st_p = 0.0, st_l = 0.0, st_n = 0.0;
     int it = 0;
     for (int64_t t = blockIdx.x; t < args.num_tiles; t += gridDim.x, ++it) {
       const int acc = it & 1;
@@ -351,42 +365,83 @@ __global__ void __launch_bounds__(THREADS, 1)
       int64_t mb, nb;
       args.tm.tile(t, mb, nb);
       const int64_t row0 = mb * BM + q * 32;
-      const int64_t col_tile = nb * BN;
-      for (int c = 0; c < BN / 32; ++c) {
-        uint32_t r[32];
-        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * ACC_COLS + c * 32);
-        tmem_ld32(taddr, r);
-        // stage row `lane` (32 fp32 = 8 chunks of 16 B), chunk j at j ^ (lane & 7)
+      const int64_t col_half0 = nb * BN + chalf * (BN / 2);
+      const bool interior = args.vec4 && (row0 + 32 <= args.M) && (col_half0 + BN / 2 <= args.N2);
+      const int64_t my_row = row0 + lane;
+      for (int c = 0; c < (BN / 2) / 16; ++c) {
+        uint32_t r[16];
+        const uint32_t taddr = tmem_base + ((uint32_t)(q * 32) << 16) +
+                               (uint32_t)(acc * ACC_COLS + chalf * (BN / 2) + c * 16);
+        tmem_ld16(taddr, r);
+        float v[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float4 v = make_float4(__uint_as_float(r[4 * j]) * oscale, __uint_as_float(r[4 * j + 1]) * oscale,
-                                 __uint_as_float(r[4 * j + 2]) * oscale,
-                                 __uint_as_float(r[4 * j + 3]) * oscale);
-          *(float4*)(stage_buf + lane * 32 + ((j ^ (lane & 7)) * 4)) = v;
+        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) * oscale;
+        const int64_t col0 = col_half0 + c * 16;
+        if (STATS) {
+          // w = 2^n |A|^2 for the 8 complex entries of this row chunk; u = 1 - exp(-w)
+          // is the Eq. 7 (alpha = 1) CDF at z = ln w
+          int nvalid = 8;
+          if (!interior) {
+            const int64_t left = (args.N2 - col0) / 2;
+            nvalid = my_row < args.M ? (int)(left < 0 ? 0 : (left > 8 ? 8 : left)) : 0;
+          }
+          float fp = 0.f, fl = 0.f, fn = 0.f;
+          int bins[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float pp = fmaf(v[2 * j], v[2 * j], v[2 * j + 1] * v[2 * j + 1]);
+            const float w = pp * args.w_scale;
+            const bool ok = j < nvalid;
+            const bool pos = ok && (w > 0.f);
+            fp += ok ? pp : 0.f;
+            fl += pos ? __logf(w) : 0.f;
+            fn += pos ? 1.f : 0.f;
+            const int b = (int)((1.f - __expf(-w)) * (float)SIM_KS_BINS);
+            bins[j] = ok ? min(max(b, 0), SIM_KS_BINS - 1) : -1;
+          }
+#pragma unroll
+          for (int j = 0; j < 8; ++j)
+            if (bins[j] >= 0) atomicAdd(&s_hist[bins[j]], 1u);
+          st_p += (double)fp;
+          st_l += (double)fl;
+          st_n += (double)fn;
         }
-        __syncwarp();
-        // write out: 8 lanes per row, 4 rows per step
-        const int64_t col0 = col_tile + c * 32;
+        // stage row `lane` (16 fp32 = 4 chunks of 16 B), chunk j at j ^ ((lane >> 1) & 3)
 #pragma unroll
-        for (int p = 0; p < 8; ++p) {
-          const int rr = p * 4 + (lane >> 3);
-          const int ch = lane & 7;
-          const float4 v = *(const float4*)(stage_buf + rr * 32 + ((ch ^ (rr & 7)) * 4));
+        for (int j = 0; j < 4; ++j)
+          *(float4*)(stage_buf + lane * 16 + ((j ^ ((lane >> 1) & 3)) * 4)) =
+              make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        __syncwarp();
+        // write out: 4 lanes per 64-byte row segment, 8 rows per step
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const int rr = p * 8 + (lane >> 2);
+          const int ch = lane & 3;
+          const float4 o = *(const float4*)(stage_buf + rr * 16 + ((ch ^ ((rr >> 1) & 3)) * 4));
           const int64_t grow = row0 + rr;
           const int64_t gcol = col0 + ch * 4;
-          if (grow >= args.M || gcol >= args.N2) continue;
           float* dst = args.C + grow * args.N2 + gcol;
-          if (args.vec4 && gcol + 4 <= args.N2) {
+          if (interior) {
             if (args.accumulate) {
-              float4 o = *(const float4*)dst;
-              o.x += v.x; o.y += v.y; o.z += v.z; o.w += v.w;
-              __stcs((float4*)dst, o);
+              float4 old = *(const float4*)dst;
+              old.x += o.x; old.y += o.y; old.z += o.z; old.w += o.w;
+              __stcs((float4*)dst, old);
             } else {
-              __stcs((float4*)dst, v);
+              __stcs((float4*)dst, o);
             }
-          } else {
-            const float vv[4] = {v.x, v.y, v.z, v.w};
-            for (int e = 0; e < 4 && gcol + e < args.N2; ++e) dst[e] = args.accumulate ? dst[e] + vv[e] : vv[e];
+          } else if (grow < args.M && gcol < args.N2) {
+            if (args.vec4 && gcol + 4 <= args.N2) {
+              if (args.accumulate) {
+                float4 old = *(const float4*)dst;
+                old.x += o.x; old.y += o.y; old.z += o.z; old.w += o.w;
+                __stcs((float4*)dst, old);
+              } else {
+                __stcs((float4*)dst, o);
+              }
+            } else {
+              const float vv[4] = {o.x, o.y, o.z, o.w};
+              for (int k = 0; k < 4 && gcol + k < args.N2; ++k) dst[k] = args.accumulate ? dst[k] + vv[k] : vv[k];
+            }
           }
         }
         __syncwarp();
@@ -395,10 +450,25 @@ __global__ void __launch_bounds__(THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&acc_empty[acc]));
     }
+    if (STATS) {
+      for (int o = 16; o > 0; o >>= 1) {
+        st_p += __shfl_xor_sync(0xffffffffu, st_p, o);
+        st_l += __shfl_xor_sync(0xffffffffu, st_l, o);
+        st_n += __shfl_xor_sync(0xffffffffu, st_n, o);
+      }
+      if (lane == 0) {
+        atomicAdd(&args.st_acc[0], st_p);
+        atomicAdd(&args.st_acc[1], st_l);
+        atomicAdd(&args.st_acc[2], st_n);
+      }
+    }
   }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (STATS)
+    for (int i = threadIdx.x; i < SIM_KS_BINS; i += THREADS)
+      if (s_hist[i]) atomicAdd(&args.st_hist[i], (unsigned long long)s_hist[i]);
   if (warp == 1) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                  : "memory");
@@ -459,15 +529,23 @@ cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s) {
   k.C = (float*)a.C;
   k.vec4 = ((((uintptr_t)a.C) & 15u) == 0 && (a.N2 % 4) == 0) ? 1 : 0;
   k.d_status = a.d_status;
+  k.w_scale = a.w_scale;
+  k.st_acc = a.st_acc;
+  k.st_hist = a.st_hist;
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   int grid = a.num_sms > 0 ? a.num_sms : 148;
   if ((int64_t)grid > k.num_tiles) grid = (int)k.num_tiles;
-  tc_gemm_kernel<<<grid, THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, k, instr_desc(a.fp16 != 0));
+  if (a.st_acc && a.st_hist)
+    tc_gemm_kernel<true><<<grid, THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, k, instr_desc(a.fp16 != 0));
+  else
+    tc_gemm_kernel<false><<<grid, THREADS, SMEM_BYTES, s>>>(mAh, mAl, mBh, mBl, k, instr_desc(a.fp16 != 0));
   note_launches(SIM_PHASE_CONTRACT, 1);
   return cudaGetLastError();
 }

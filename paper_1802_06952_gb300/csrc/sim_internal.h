@@ -201,6 +201,10 @@ struct TcGemmArgs {
   int group_m;
   int num_sms;
   int* d_status;          // device word, set non-zero if a wait gave up
+  // optional fused statistics (both NULL: none); the caller zeroes them first
+  float w_scale = 1.f;            // 2^n
+  double* st_acc = nullptr;       // [sum |A|^2, sum ln 2^n|A|^2 over |A| > 0, count]
+  unsigned long long* st_hist = nullptr;  // SIM_KS_BINS counts of u = 1 - exp(-2^n |A|^2)
 };
 cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s);
 // values written to *d_status when a bounded wait of the contraction gives up

@@ -100,6 +100,21 @@ def test_floyd_select_distinct_sorted_uniform():
     assert chi2 < 40.0  # 15 dof; p ~ 5e-4
 
 
+def test_eq7_cdf_is_the_integral_of_the_density():
+    """Eq. 7: f(z) = (1/a) exp(z - (1/a)(e^z + a - 1)); at a = 1 its CDF is the
+    closed form the statistics use, and u = F(z) of an Exp(1) w = e^z is uniform."""
+    from scipy.integrate import quad
+    alpha = 1.0
+    f = lambda z: (1 / alpha) * np.exp(z - (1 / alpha) * (np.exp(z) + alpha - 1))
+    for z0 in (-6.0, -1.0, 0.0, 0.7, 2.0):
+        val, _ = quad(f, -60, z0)
+        assert abs(val - oracle.gumbel_cdf(z0)) < 1e-10
+    rng = np.random.default_rng(5)
+    w = rng.exponential(size=200000)
+    u = oracle.gumbel_cdf(np.log(w))
+    assert abs(u.mean() - 0.5) < 0.005 and abs(u.var() - 1 / 12) < 0.002
+
+
 def test_stats_closed_forms():
     # Porter-Thomas: 2^n|A|^2 ~ Exp(1): mean 1, mean ln = -Euler gamma, KS small
     rng = np.random.default_rng(0)
