@@ -45,6 +45,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the large-half sweep bandwidth measurement")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="profiling case: only the large-half sweep measurement (prints its JSON object)")
+    ap.add_argument("--sweep-cols", type=int, default=10,
+                    help="columns of the 6-row sweep grid (10: two 30-qubit halves)")
     ap.add_argument("--select", type=int, default=0,
                     help="profiling case: contract only the first S upper x S lower indices (S*S amplitudes)")
     return ap.parse_args()
@@ -178,6 +183,64 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+SWEEP_GRID = (6, 10, 16, 3)   # rows, cols, depth, cut row: two 30-qubit halves
+
+
+def sweep_hbm(sim, torch, stream, reps=3, cols=10):
+    """Gate-sweep bandwidth on halves too large for L2: one copy of a 60-qubit
+    6x10 grid circuit (depth 16, cut between rows 2 and 3), i.e. two 30-qubit
+    half-states of 8 GB (complex64) or 16 GB (complex128).  The fused complex64
+    sweeps are timed against the plain complex128 path of Section 2.4 (one pass
+    per non-diagonal gate, one combined diagonal pass per layer) on the same copy.
+    Algorithmic bytes: 16 B per amplitude per fused pass (8 B for the first pass,
+    which generates the H-layer state), 32 B per amplitude per plain pass."""
+    import numpy as np
+    Rr, Cc, Dd, b = SWEEP_GRID
+    Cc = cols
+    circ = sim.sim_build_circuit(Rr, Cc, Dd, 0, b)
+    plan, c, copies, nu, nl = sim.sim_cut(circ, b)
+    sel = np.zeros(1, dtype=np.uint64)
+    info = {}
+    try:
+        fused = [sim.sim_plan_schedule(plan, hh)[1] for hh in (0, 1)]
+        plain = [sim.sim_plan_schedule(plan, hh)[2] for hh in (0, 1)]
+        best = {}
+        for name, prec, phase in (("fused_c64", sim.SIM_C64, sim.SIM_PHASE_SWEEP),
+                                  ("plain_c128", sim.SIM_C128_PLAIN, sim.SIM_PHASE_PLAIN)):
+            ts = []
+            for _ in range(reps):
+                sim.sim_profile_read(reset=True)
+                sim.sim_profile_enable(True)
+                h = sim.sim_evolve_halves(plan, prec, 0, 1, sel, sel, stream=stream)
+                sim.sim_status(stream)
+                sim.sim_profile_enable(False)
+                ts.append(sim.sim_profile_read(reset=True)["ms"][phase])
+                sim.sim_destroy_halves(h)
+            best[name] = min(ts)
+        sim.sim_release_cache()
+        amps = 1 << nu
+        fused_bytes = sum(16 * f - 8 for f in fused) * amps
+        plain_bytes_c128 = sum(32 * p for p in plain) * amps
+        plain_equiv_c64 = sum(16 * p for p in plain) * amps
+        hbm = peaks()[0]
+        fg = fused_bytes / (best["fused_c64"] / 1e3) / 1e9
+        info = {"workload": "one copy of a %d-qubit 6x%d grid circuit, depth 16: two %d-qubit halves "
+                            "(%.1f GB complex64 each)" % (6 * Cc, Cc, 3 * Cc, 8 * 2.0 ** (3 * Cc) / 1e9),
+                "fused_passes": fused, "plain_passes": plain,
+                "fused_ms": best["fused_c64"], "fused_gbs": fg, "fused_frac_of_hbm": fg / hbm,
+                "plain_equiv_gbs": plain_equiv_c64 / (best["fused_c64"] / 1e3) / 1e9,
+                "plain_c128_ms": best["plain_c128"],
+                "plain_c128_gbs": plain_bytes_c128 / (best["plain_c128"] / 1e3) / 1e9,
+                "speedup_vs_plain": best["plain_c128"] / best["fused_c64"],
+                "peak_gbs": hbm,
+                "note": "fused_gbs counts the bytes the fused passes must move; plain_equiv_gbs counts the "
+                        "complex64 bytes the Section 2.4 scheme would move for the same circuit in the same time"}
+    finally:
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(circ)
+    return info
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -195,6 +258,10 @@ def run_ours(args):
     S = args.select if args.select > 0 else (1 << 15)
     sel = np.arange(S, dtype=np.uint64) if args.select > 0 else None
     amps_step = S * S
+    if args.sweep_only:
+        if rank == 0:
+            print(json.dumps(sweep_hbm(sim, torch, stream, reps=1, cols=args.sweep_cols)), flush=True)
+        return
     out = torch.empty((S, S), dtype=torch.complex64, device="cuda")
 
     def step(i, target):
@@ -290,6 +357,9 @@ def run_ours(args):
         "clocks": clocks,
         "stats_last_step": [float(x) for x in stats[-1]] if stats[-1] is not None else None,
     }
+
+    if not args.no_sweep:
+        line["sweep_hbm"] = sweep_hbm(sim, torch, stream)
 
     # end to end through the C-ABI with a host output buffer
     if not args.no_e2e:

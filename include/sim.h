@@ -87,13 +87,16 @@ typedef struct {
 
 /* Tuning knobs; pass NULL for defaults.  Zero fields mean "choose automatically".
  *   fuse_qubits    local qubits staged per thread block in a fused sweep (4..13)
- *   sweep_threads  threads per sweep block (64..1024, multiple of 32)
- *   gemm_group_m   m-blocks per raster group of the persistent contraction */
+ *   sweep_threads  threads per block of the staged sweep (64..256, multiple of 32)
+ *   gemm_group_m   m-blocks per raster group of the persistent contraction
+ *   sweep_kernel   1: staged shared-memory sweep; 0 or 2: register-blocked sweep
+ *                  wherever the pass allows it (8 <= k <= 13), staged otherwise */
 typedef struct {
   int fuse_qubits;
   int sweep_threads;
   int gemm_group_m;
-  int reserved[5];
+  int sweep_kernel;
+  int reserved[4];
 } sim_opts;
 
 /* Build a circuit (Supplementary A, Eq. 3 circuit model; gate rules of the random

@@ -49,7 +49,7 @@ class _Desc(ctypes.Structure):
 
 class SimOpts(ctypes.Structure):
     _fields_ = [("fuse_qubits", ctypes.c_int), ("sweep_threads", ctypes.c_int),
-                ("gemm_group_m", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("gemm_group_m", ctypes.c_int), ("sweep_kernel", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 _lib = None

@@ -450,7 +450,15 @@ int evolve_c64_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t*
     sl.src_base = pd.src == SRC_PARENT ? lvl[r.src_buf].p : dstp;
     sl.dst_base = dstp;
     sl.threads = threads;
-    CK(launch_sweep_c64(sl, st));
+    memcpy(sl.order, pd.order, sizeof sl.order);
+    sl.warp_gates = pd.warp_gates;
+    sl.general_gates = pd.general_gates;
+    sl.scale = pd.scale;
+    const int kernel_choice = opts ? opts->sweep_kernel : 0;
+    if (kernel_choice != 1 && sweep2_supported(sl))
+      CK(launch_sweep2_c64(sl, st));
+    else
+      CK(launch_sweep_c64(sl, st));
   }
   // the pool may hand these buffers to the next call on this stream only after
   // the launches above have been enqueued, which keeps reuse stream-ordered

@@ -46,6 +46,11 @@ constexpr int SMEM_BYTES = 1024 /*align slack*/ + STAGES * (A_BYTES + B_BYTES) +
 static_assert(SMEM_BYTES <= 232448, "shared memory above the 227 KB per-block limit");
 
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s
+// Copies accumulated in one tensor-memory run before the partial is added to the
+// output with IEEE fp32 adds: the tensor-core accumulation error grows with the
+// number of products of one run (measured: 4.5e-5 relative at 4096 copies of a
+// 24-qubit circuit with 12 cuts, 5e-6 at 256).
+constexpr int kChunkCopies = 256;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -184,6 +189,20 @@ struct TileMap {
 struct KernelArgs {
   int64_t M, N2;
   int nkb;               // k-blocks per segment
+  int ckb;               // k-blocks per segment in one copy chunk
+  int nchunks;           // copy chunks accumulated separately in TMEM
+  // k-blocks of copy chunk c (all three split segments) and the i-th of them
+  __device__ int chunk_kblocks(int c) const {
+    const int b0 = c * ckb;
+    const int b1 = b0 + ckb < nkb ? b0 + ckb : nkb;
+    return 3 * (b1 - b0);
+  }
+  __device__ void kblock(int c, int i, int& seg, int& kx) const {
+    const int b0 = c * ckb;
+    const int per = (b0 + ckb < nkb ? b0 + ckb : nkb) - b0;
+    seg = i / per;
+    kx = (b0 + i % per) * BK;
+  }
   TileMap tm;
   int64_t num_tiles;
   const float* scale_a;
@@ -251,7 +270,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
-  const int nkb_total = 3 * args.nkb;
 
   if (warp == 0) {
     // ---------------- TMA producer ----------------
@@ -264,13 +282,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int64_t t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x) {
         int64_t mb, nb;
         args.tm.tile(t, mb, nb);
-        for (int kb = 0; kb < nkb_total; ++kb) {
+        for (int c = 0; c < args.nchunks && ok; ++c)
+        for (int i = 0; i < args.chunk_kblocks(c); ++i) {
           if (!mbar_wait(smem_u32(&empty[stage]), phase ^ 1u, abort_flag)) {
             ok = false;
             break;
           }
-          const int seg = kb / args.nkb;
-          const int kx = (kb % args.nkb) * BK;
+          int seg, kx;
+          args.kblock(c, i, seg, kx);
           const CUtensorMap* ma = seg == 2 ? &mapA_lo : &mapA_hi;
           const CUtensorMap* mb_ = seg == 1 ? &mapB_lo : &mapB_hi;
           const uint32_t fb = smem_u32(&full[stage]);
@@ -299,8 +318,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
-      int it = 0;
-      for (int64_t t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x, ++it) {
+      int it = 0;  // accumulation jobs: one per (tile, copy chunk)
+      for (int64_t t = blockIdx.x; t < args.num_tiles && ok; t += gridDim.x)
+      for (int c = 0; c < args.nchunks && ok; ++c, ++it) {
         const int acc = it & 1;
         const uint32_t acc_phase = (uint32_t)(it >> 1) & 1u;
         if (!mbar_wait(smem_u32(&acc_empty[acc]), acc_phase ^ 1u, abort_flag)) {
@@ -309,7 +329,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         tc_fence_after();
         const uint32_t d_tmem = tmem_base + (uint32_t)(acc * ACC_COLS);
-        for (int kb = 0; kb < nkb_total; ++kb) {
+        const int nkbc = args.chunk_kblocks(c);
+        for (int kb = 0; kb < nkbc; ++kb) {
           if (!mbar_wait(smem_u32(&full[stage]), phase, abort_flag)) {
             ok = false;
             break;
@@ -353,12 +374,20 @@ __global__ void __launch_bounds__(THREADS, 1)
     const float oscale = 1.f / (sa * sb);
     double st_p = 0.0, st_l = 0.0, st_n = 0.0;
     int it = 0;
-    for (int64_t t = blockIdx.x; t < args.num_tiles; t += gridDim.x, ++it) {
+    bool stop = false;
+    for (int64_t t = blockIdx.x; t < args.num_tiles && !stop; t += gridDim.x)
+    for (int kc = 0; kc < args.nchunks; ++kc, ++it) {
+      // copy chunk kc of tile t: the first chunk stores (or adds, when the caller
+      // accumulates), later chunks add their fp32 partial to what this same thread
+      // stored before; the statistics see the final values of the last chunk
+      const bool rmw = args.accumulate || kc > 0;
+      const bool last = kc == args.nchunks - 1;
       const int acc = it & 1;
       const uint32_t acc_phase = (uint32_t)(it >> 1) & 1u;
       if (!mbar_wait(smem_u32(&acc_full[acc]), acc_phase, abort_flag)) {
         if (args.d_status) atomicExch(args.d_status, SIM_TIMEOUT_CODE_EPI);
         *abort_flag = 1;
+        stop = true;
         break;
       }
       tc_fence_after();
@@ -377,35 +406,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
         for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]) * oscale;
         const int64_t col0 = col_half0 + c * 16;
-        if (STATS) {
-          // w = 2^n |A|^2 for the 8 complex entries of this row chunk; u = 1 - exp(-w)
-          // is the Eq. 7 (alpha = 1) CDF at z = ln w
-          int nvalid = 8;
-          if (!interior) {
-            const int64_t left = (args.N2 - col0) / 2;
-            nvalid = my_row < args.M ? (int)(left < 0 ? 0 : (left > 8 ? 8 : left)) : 0;
-          }
-          float fp = 0.f, fl = 0.f, fn = 0.f;
-          int bins[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float pp = fmaf(v[2 * j], v[2 * j], v[2 * j + 1] * v[2 * j + 1]);
-            const float w = pp * args.w_scale;
-            const bool ok = j < nvalid;
-            const bool pos = ok && (w > 0.f);
-            fp += ok ? pp : 0.f;
-            fl += pos ? __logf(w) : 0.f;
-            fn += pos ? 1.f : 0.f;
-            const int b = (int)((1.f - __expf(-w)) * (float)SIM_KS_BINS);
-            bins[j] = ok ? min(max(b, 0), SIM_KS_BINS - 1) : -1;
-          }
-#pragma unroll
-          for (int j = 0; j < 8; ++j)
-            if (bins[j] >= 0) atomicAdd(&s_hist[bins[j]], 1u);
-          st_p += (double)fp;
-          st_l += (double)fl;
-          st_n += (double)fn;
-        }
+        (void)my_row;
         // stage row `lane` (16 fp32 = 4 chunks of 16 B), chunk j at j ^ ((lane >> 1) & 3)
 #pragma unroll
         for (int j = 0; j < 4; ++j)
@@ -413,36 +414,54 @@ __global__ void __launch_bounds__(THREADS, 1)
               make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         __syncwarp();
         // write out: 4 lanes per 64-byte row segment, 8 rows per step
+        float fp = 0.f, fl = 0.f, fn = 0.f;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           const int rr = p * 8 + (lane >> 2);
           const int ch = lane & 3;
-          const float4 o = *(const float4*)(stage_buf + rr * 16 + ((ch ^ ((rr >> 1) & 3)) * 4));
+          float4 o = *(const float4*)(stage_buf + rr * 16 + ((ch ^ ((rr >> 1) & 3)) * 4));
           const int64_t grow = row0 + rr;
           const int64_t gcol = col0 + ch * 4;
           float* dst = args.C + grow * args.N2 + gcol;
-          if (interior) {
-            if (args.accumulate) {
-              float4 old = *(const float4*)dst;
-              old.x += o.x; old.y += o.y; old.z += o.z; old.w += o.w;
-              __stcs((float4*)dst, old);
-            } else {
-              __stcs((float4*)dst, o);
+          int nvalid = 0;  // complex entries of this float4 that exist in C
+          if (interior || (args.vec4 && grow < args.M && gcol + 4 <= args.N2)) {
+            if (rmw) {
+              const float4 old = __ldcg((const float4*)dst);
+              o.x += old.x; o.y += old.y; o.z += old.z; o.w += old.w;
             }
+            __stcs((float4*)dst, o);
+            nvalid = 2;
           } else if (grow < args.M && gcol < args.N2) {
-            if (args.vec4 && gcol + 4 <= args.N2) {
-              if (args.accumulate) {
-                float4 old = *(const float4*)dst;
-                old.x += o.x; old.y += o.y; old.z += o.z; old.w += o.w;
-                __stcs((float4*)dst, old);
-              } else {
-                __stcs((float4*)dst, o);
-              }
-            } else {
-              const float vv[4] = {o.x, o.y, o.z, o.w};
-              for (int k = 0; k < 4 && gcol + k < args.N2; ++k) dst[k] = args.accumulate ? dst[k] + vv[k] : vv[k];
+            float vv[4] = {o.x, o.y, o.z, o.w};
+            for (int k = 0; k < 4 && gcol + k < args.N2; ++k) {
+              if (rmw) vv[k] += __ldcg(dst + k);
+              dst[k] = vv[k];
+            }
+            o = make_float4(vv[0], vv[1], vv[2], vv[3]);
+            nvalid = (int)((args.N2 - gcol) / 2 < 2 ? (args.N2 - gcol) / 2 : 2);
+          }
+          if (STATS && last) {
+            // w = 2^n |A|^2 of the final values; u = 1 - exp(-w) is the Eq. 7
+            // (alpha = 1) CDF at z = ln w
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              const float re = j ? o.z : o.x, im = j ? o.w : o.y;
+              const float pp = fmaf(re, re, im * im);
+              const float w = pp * args.w_scale;
+              const bool ok = j < nvalid;
+              const bool pos = ok && (w > 0.f);
+              fp += ok ? pp : 0.f;
+              fl += pos ? __logf(w) : 0.f;
+              fn += pos ? 1.f : 0.f;
+              const int b = (int)((1.f - __expf(-w)) * (float)SIM_KS_BINS);
+              if (ok) atomicAdd(&s_hist[min(max(b, 0), SIM_KS_BINS - 1)], 1u);
             }
           }
+        }
+        if (STATS && last) {
+          st_p += (double)fp;
+          st_l += (double)fl;
+          st_n += (double)fn;
         }
         __syncwarp();
       }
@@ -519,6 +538,8 @@ cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s) {
   k.M = a.M;
   k.N2 = a.N2;
   k.nkb = (int)(a.kpad / BK);
+  k.ckb = kChunkCopies * 2 / BK;
+  k.nchunks = (k.nkb + k.ckb - 1) / k.ckb;
   k.tm.num_mb = (a.M + BM - 1) / BM;
   k.tm.num_nb = (a.N2 + BN - 1) / BN;
   k.tm.group = a.group_m > 0 ? a.group_m : 16;

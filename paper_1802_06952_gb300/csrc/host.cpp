@@ -225,6 +225,7 @@ OpRec make_gate(int code, int q) {
   o.type = OP_GATE;
   o.q = q;
   o.lq = -1;
+  o.kind = code == G_X2 ? 1 : code == G_Y2 ? 2 : code == G_H ? 3 : 0;
   gate_matrix(code, o.md);
   for (int i = 0; i < 8; ++i) o.m[i] = (float)o.md[i];
   return o;
@@ -280,7 +281,16 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
   size_t i = 0;
   bool first = true;
   if (seq.empty()) {
-    PassDesc p{k, low, (k >= 32 ? 0xFFFFFFFFu : ((1u << k) - 1)), (int)ops.size(), 0, first_src};
+    PassDesc p;
+    memset(&p, 0, sizeof p);
+    p.k = k;
+    p.low = low;
+    p.local_mask = (k >= 32 ? 0xFFFFFFFFu : ((1u << k) - 1));
+    p.op_begin = (int)ops.size();
+    p.op_count = 0;
+    p.src = first_src;
+    p.scale = 1.f;
+    for (int r = 0; r < k; ++r) p.order[r] = (uint8_t)r;
     passes.push_back(p);
     return;
   }
@@ -301,22 +311,54 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
     for (int q = 0; q < n && cnt < k; ++q)
       if (!(local & (1u << q))) { local |= 1u << q; ++cnt; }
     PassDesc p;
+    memset(&p, 0, sizeof p);
     p.k = k;
     p.low = low;
     p.local_mask = local;
     p.op_begin = (int)ops.size();
     p.op_count = (int)(j - i);
     p.src = first ? first_src : SRC_SELF;
+    // rank order: the low bits first; then (k >= 8) three warp-bit ranks and k-8
+    // register-bit ranks; the qubits with the most gates in the pass take the
+    // register ranks, qubits without gates the warp ranks
+    int gates_on[32] = {0};
+    for (size_t t = i; t < j; ++t)
+      if (seq[t].type == OP_GATE) ++gates_on[seq[t].q];
+    std::vector<int> hi;
+    for (int q = low; q < n; ++q)
+      if (local & (1u << q)) hi.push_back(q);
+    std::stable_sort(hi.begin(), hi.end(), [&](int a, int b2) { return gates_on[a] > gates_on[b2]; });
+    const int nreg = k >= 8 ? k - 8 : 0;
+    const int nwarp = (int)hi.size() - nreg;          // ranks low .. low+nwarp-1
+    int r = 0;
+    for (int q = 0; q < low; ++q) p.order[r++] = (uint8_t)q;
+    // warp ranks: the qubits after the first nreg (fewest gates), lowest first
+    std::vector<int> warp_q(hi.begin() + nreg, hi.end());
+    std::sort(warp_q.begin(), warp_q.end());
+    for (int q : warp_q) p.order[r++] = (uint8_t)q;
+    for (int t2 = 0; t2 < nreg; ++t2) p.order[r++] = (uint8_t)hi[t2];
+    (void)nwarp;
+    int rank_of[32];
+    for (int t2 = 0; t2 < 32; ++t2) rank_of[t2] = -1;
+    for (int t2 = 0; t2 < k; ++t2) rank_of[p.order[t2]] = t2;
+    p.warp_gates = 0;
+    p.general_gates = 0;
+    double scale = 1.0;
     for (size_t t = i; t < j; ++t) {
       OpRec o = seq[t];
       if (o.type == OP_GATE) {
-        int rank = 0;
-        for (int q = 0; q < o.q; ++q)
-          if (local & (1u << q)) ++rank;
-        o.lq = rank;
+        o.lq = rank_of[o.q];
+        if (k >= 8 && o.lq >= 5 && o.lq < 8) ++p.warp_gates;
+        if (o.kind == 1 || o.kind == 2)
+          scale *= 0.5;
+        else if (o.kind == 3)
+          scale *= 0.70710678118654752440;
+        else
+          ++p.general_gates;
       }
       ops.push_back(o);
     }
+    p.scale = (float)scale;
     passes.push_back(p);
     first = false;
     i = j;

@@ -49,7 +49,7 @@ struct OpRec {
   int32_t ncut;
   int32_t half;
   uint32_t tmask;
-  uint32_t pad0;
+  int32_t kind;          // GATE: 0 general 2x2, 1 X^1/2, 2 Y^1/2, 3 H (closed-form updates)
   uint32_t sh_d[kMaxShift];
   uint32_t sh_m[kMaxShift];
   uint8_t cutq[kMaxCutSlots];
@@ -68,6 +68,14 @@ struct PassDesc {
   uint32_t local_mask;
   int op_begin, op_count;
   int src;
+  // qubit held by each local rank r (bit r of the staged index): ranks 0..low-1
+  // are qubits 0..low-1; with k >= 8 ranks 5..7 are the warp bits and ranks
+  // 8..k-1 the register bits of the register-blocked sweep, which take the qubits
+  // with the most gates in the pass
+  uint8_t order[16];
+  int warp_gates;       // gates of the pass on warp-bit ranks (need a smem exchange)
+  int general_gates;    // gates of the pass without a closed-form update (kind 0)
+  float scale;          // product over the pass's gates of 1/2 (X^1/2, Y^1/2), 1/sqrt2 (H)
 };
 
 // One level of the copy tree of a half: nodes share all gates up to the branch
@@ -155,8 +163,16 @@ struct SweepLaunch {
   const void* src_base;   // parent level buffer (SRC_PARENT) or the own buffer
   void* dst_base;
   int threads;
+  uint8_t order[16];      // qubit of each local rank (PassDesc::order)
+  int warp_gates;
+  int general_gates;
+  float scale;
 };
+// staged-block sweep (any k, any threads)
 cudaError_t launch_sweep_c64(const SweepLaunch& L, cudaStream_t s);
+// register-blocked sweep (k in 8..13, low == 5): preferred when supported
+bool sweep2_supported(const SweepLaunch& L);
+cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s);
 
 struct PlainLaunch {
   int n;

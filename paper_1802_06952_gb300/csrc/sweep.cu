@@ -68,7 +68,9 @@ __device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, Dia
 __device__ __forceinline__ int diag_exp(const DiagState& d, uint32_t x, bool& keep) {
   int e = __popc(x & d.tmask);
   int s2 = __popc(x & d.zmask);
-  for (int s = 0; s < d.nsh; ++s) s2 += __popc(x & (x >> d.sh_d[s]) & d.sh_m[s]);
+#pragma unroll
+  for (int s = 0; s < kMaxShift; ++s)
+    if (s < d.nsh) s2 += __popc(x & (x >> d.sh_d[s]) & d.sh_m[s]);
   keep = (x & d.pmask) == d.pval;
   return (e + 4 * s2) & 7;
 }
@@ -254,17 +256,20 @@ cudaError_t launch_sweep_c64(const SweepLaunch& L, cudaStream_t s) {
   a.nodes = L.nodes;
   a.src_base = (const float2*)L.src_base;
   a.dst_base = (float2*)L.dst_base;
+  // local ranks follow the pass's rank order (ranks 0..low-1 are qubits 0..low-1)
   int nh = 0, nn = 0;
-  for (int q = 0; q < L.n; ++q) {
-    if (L.local_mask & (1u << q)) {
-      if (q >= a.low) a.hi_pos[nh++] = (uint8_t)q;
+  for (int r = 0; r < L.k; ++r) {
+    const int q = L.order[r];
+    if (q >= L.n || !(L.local_mask & (1u << q))) return cudaErrorInvalidValue;
+    if (r < a.low) {
+      if (q != r) return cudaErrorInvalidValue;
     } else {
-      a.nonlocal[nn++] = (uint8_t)q;
+      a.hi_pos[nh++] = (uint8_t)q;
     }
   }
+  for (int q = 0; q < L.n; ++q)
+    if (!(L.local_mask & (1u << q))) a.nonlocal[nn++] = (uint8_t)q;
   if (nh != L.k - a.low || nn != L.n - L.k) return cudaErrorInvalidValue;
-  for (int q = 0; q < a.low; ++q)
-    if (!(L.local_mask & (1u << q))) return cudaErrorInvalidValue;
   // 2^{-n/2}
   a.init_val = (float)ldexp(1.0, -(L.n / 2)) * ((L.n & 1) ? 0.70710678118654752f : 1.f);
   const int threads = L.threads > 0 ? L.threads : 256;

@@ -166,6 +166,33 @@ def test_accumulate_over_copy_batches():
         r.close()
 
 
+def test_many_copies_chunked_accumulation():
+    """c = 12 (4096 copies of 12-qubit halves): the contraction accumulates 256 copies
+    per tensor-memory run and adds the runs in fp32; a 300-copy range (one full and
+    one partial run) is added into an existing output."""
+    R, C, d, seed, b = 4, 6, 23, 8, 2
+    gates, plan = oc.grid_cut(R, C, d, seed, b)
+    assert plan.c == 12
+    rng = np.random.default_rng(4)
+    su = np.unique(rng.integers(0, 1 << plan.n_u, 700)).astype(np.uint64)
+    sl = np.unique(rng.integers(0, 1 << plan.n_l, 500)).astype(np.uint64)
+    ref = oracle.cut_amplitudes(plan, su, sl)
+    r = Run(R, C, d, seed, b)
+    try:
+        for kind in (sim.SIM_SPLIT_BF16, sim.SIM_SPLIT_FP16):
+            h = r.evolve(sim.SIM_C64, 0, None, su, sl)
+            got = amplitudes(h, kind, sl.size, su.size).cpu().numpy()
+            assert rel_err(got, ref) <= TOL_SPLIT
+        part = oracle.cut_amplitudes(plan, su, sl, 1000, 1300)
+        out = torch.from_numpy(ref.astype(np.complex64)).cuda()
+        h = r.evolve(sim.SIM_C64, 1000, 1300, su, sl)
+        sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, True, out)
+        sim.sim_status()
+        assert rel_err(out.cpu().numpy(), ref + part) <= TOL_SPLIT
+    finally:
+        r.close()
+
+
 def test_host_output_buffer():
     gates, plan = oc.grid_cut(4, 4, 10, 0, 2)
     ref = oracle.statevector(16, gates).reshape(256, 256)
@@ -314,15 +341,28 @@ def test_sample_entry_point():
         r.close()
 
 
-def test_fuse_widths_agree():
-    gates, plan = oc.grid_cut(6, 4, 17, 5, 3)
+@pytest.mark.parametrize("R,C,d,seed,b", [(6, 4, 17, 5, 3), (4, 6, 23, 8, 2)])
+def test_fuse_widths_and_sweep_kernels_agree(R, C, d, seed, b):
+    """Staged (shared-memory) and register-blocked sweeps, fuse widths 4..13: the
+    register-blocked kernel runs for 8 <= k <= 13 (rank 0-4 lane gates by shuffle,
+    5-7 warp gates through smem, 8+ register gates), the staged one otherwise."""
+    gates, plan = oc.grid_cut(R, C, d, seed, b)
     ref = oracle.cut_amplitudes(plan)
-    for fq in (4, 7, 13):
-        r = Run(6, 4, 17, 5, 3)
+    for fq, kern in ((4, 0), (7, 0), (8, 0), (9, 0), (10, 1), (10, 2), (12, 1), (12, 2), (13, 0)):
+        r = Run(R, C, d, seed, b)
         try:
-            h = r.evolve(sim.SIM_C64, opts={"fuse_qubits": fq, "sweep_threads": 128})
+            h = r.evolve(sim.SIM_C64, opts={"fuse_qubits": fq, "sweep_threads": 128, "sweep_kernel": kern})
             got = amplitudes(h, sim.SIM_SPLIT_FP16, 1 << plan.n_l, 1 << plan.n_u).cpu().numpy()
-            assert rel_err(got, ref) <= TOL_SPLIT
+            assert rel_err(got, ref) <= TOL_SPLIT, (fq, kern)
+            for k in (0, plan.copies - 1):
+                for half, nq in ((0, plan.n_u), (1, plan.n_l)):
+                    buf = torch.zeros(1 << nq, dtype=torch.complex64, device="cuda")
+                    sim.sim_halves_leaf(h, half, k, buf)
+                    hs = oracle.half_state(plan, half, k)
+                    # a leaf can be exactly zero (two projectors on one cut qubit with
+                    # opposite bits): the floor is the state's natural scale 2^{-n/2}
+                    scale = max(np.max(np.abs(hs)), 2.0 ** (-nq / 2))
+                    assert np.max(np.abs(buf.cpu().numpy() - hs)) <= 1e-5 * scale, (fq, kern)
         finally:
             r.close()
 
