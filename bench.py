@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the large-half sweep bandwidth measurement")
     ap.add_argument("--sweep-only", action="store_true",
                     help="profiling case: only the large-half sweep measurement (prints its JSON object)")
+    ap.add_argument("--sweep-fuse", type=int, default=0, help="fuse width k of the sweep measurement (0: library default)")
     ap.add_argument("--sweep-cols", type=int, default=10,
                     help="columns of the 6-row sweep grid (10: two 30-qubit halves)")
     ap.add_argument("--select", type=int, default=0,
@@ -186,7 +187,7 @@ def run_reference(args):
 SWEEP_GRID = (6, 10, 16, 3)   # rows, cols, depth, cut row: two 30-qubit halves
 
 
-def sweep_hbm(sim, torch, stream, reps=3, cols=10):
+def sweep_hbm(sim, torch, stream, reps=3, cols=10, fuse=0):
     """Gate-sweep bandwidth on halves too large for L2: one copy of a 60-qubit
     6x10 grid circuit (depth 16, cut between rows 2 and 3), i.e. two 30-qubit
     half-states of 8 GB (complex64) or 16 GB (complex128).  The fused complex64
@@ -202,8 +203,6 @@ def sweep_hbm(sim, torch, stream, reps=3, cols=10):
     sel = np.zeros(1, dtype=np.uint64)
     info = {}
     try:
-        fused = [sim.sim_plan_schedule(plan, hh)[1] for hh in (0, 1)]
-        plain = [sim.sim_plan_schedule(plan, hh)[2] for hh in (0, 1)]
         best = {}
         for name, prec, phase in (("fused_c64", sim.SIM_C64, sim.SIM_PHASE_SWEEP),
                                   ("plain_c128", sim.SIM_C128_PLAIN, sim.SIM_PHASE_PLAIN)):
@@ -211,13 +210,17 @@ def sweep_hbm(sim, torch, stream, reps=3, cols=10):
             for _ in range(reps):
                 sim.sim_profile_read(reset=True)
                 sim.sim_profile_enable(True)
-                h = sim.sim_evolve_halves(plan, prec, 0, 1, sel, sel, stream=stream)
+                h = sim.sim_evolve_halves(plan, prec, 0, 1, sel, sel, opts={"fuse_qubits": fuse} if fuse else None,
+                                          stream=stream)
                 sim.sim_status(stream)
                 sim.sim_profile_enable(False)
                 ts.append(sim.sim_profile_read(reset=True)["ms"][phase])
                 sim.sim_destroy_halves(h)
             best[name] = min(ts)
         sim.sim_release_cache()
+        # the pass counts of the schedule that ran (evolve re-plans for another fuse width)
+        fused = [sim.sim_plan_schedule(plan, hh)[1] for hh in (0, 1)]
+        plain = [sim.sim_plan_schedule(plan, hh)[2] for hh in (0, 1)]
         amps = 1 << nu
         fused_bytes = sum(16 * f - 8 for f in fused) * amps
         plain_bytes_c128 = sum(32 * p for p in plain) * amps
@@ -260,7 +263,8 @@ def run_ours(args):
     amps_step = S * S
     if args.sweep_only:
         if rank == 0:
-            print(json.dumps(sweep_hbm(sim, torch, stream, reps=1, cols=args.sweep_cols)), flush=True)
+            print(json.dumps(sweep_hbm(sim, torch, stream, reps=1, cols=args.sweep_cols, fuse=args.sweep_fuse)),
+                  flush=True)
         return
     out = torch.empty((S, S), dtype=torch.complex64, device="cuda")
 

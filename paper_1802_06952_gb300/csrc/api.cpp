@@ -454,6 +454,9 @@ int evolve_c64_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t*
     sl.warp_gates = pd.warp_gates;
     sl.general_gates = pd.general_gates;
     sl.scale = pd.scale;
+    memcpy(sl.sorder, pd.sorder, sizeof sl.sorder);
+    memcpy(sl.swz, pd.swz, sizeof sl.swz);
+    sl.transpose = pd.transpose;
     const int kernel_choice = opts ? opts->sweep_kernel : 0;
     if (kernel_choice != 1 && sweep2_supported(sl))
       CK(launch_sweep2_c64(sl, st));

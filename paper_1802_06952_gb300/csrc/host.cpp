@@ -329,15 +329,76 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
       if (local & (1u << q)) hi.push_back(q);
     std::stable_sort(hi.begin(), hi.end(), [&](int a, int b2) { return gates_on[a] > gates_on[b2]; });
     const int nreg = k >= 8 ? k - 8 : 0;
-    const int nwarp = (int)hi.size() - nreg;          // ranks low .. low+nwarp-1
     int r = 0;
-    for (int q = 0; q < low; ++q) p.order[r++] = (uint8_t)q;
-    // warp ranks: the qubits after the first nreg (fewest gates), lowest first
-    std::vector<int> warp_q(hi.begin() + nreg, hi.end());
-    std::sort(warp_q.begin(), warp_q.end());
-    for (int q : warp_q) p.order[r++] = (uint8_t)q;
-    for (int t2 = 0; t2 < nreg; ++t2) p.order[r++] = (uint8_t)hi[t2];
-    (void)nwarp;
+    if (k >= 8 && low == 5) {
+      // storage order: qubits 0..4, then the other local qubits ascending
+      for (int q = 0; q < 5; ++q) p.sorder[r++] = (uint8_t)q;
+      std::vector<int> rest_s;
+      for (int q = 5; q < n; ++q)
+        if (local & (1u << q)) rest_s.push_back(q);
+      for (int q : rest_s) p.sorder[r++] = (uint8_t)q;
+      // compute order: the 5 + nreg local qubits with the most gates take the lane
+      // and register ranks (ties: qubits 0..4 first, so that no transpose is needed
+      // when the low qubits are as busy), the rest the three warp ranks
+      std::vector<int> all;
+      for (int q = 0; q < n; ++q)
+        if (local & (1u << q)) all.push_back(q);
+      std::stable_sort(all.begin(), all.end(), [&](int a, int b2) {
+        if (gates_on[a] != gates_on[b2]) return gates_on[a] > gates_on[b2];
+        return a < b2;
+      });
+      std::vector<int> lanes(all.begin(), all.begin() + 5);
+      std::vector<int> regs(all.begin() + 5, all.begin() + 5 + nreg);
+      std::vector<int> warps(all.begin() + 5 + nreg, all.end());
+      // keep a low qubit on the lane rank equal to its storage rank when it is a lane
+      std::vector<int> lane_slot(5, -1);
+      for (int q : lanes)
+        if (q < 5) lane_slot[q] = q;
+      size_t li = 0;
+      for (int s = 0; s < 5; ++s) {
+        if (lane_slot[s] >= 0) continue;
+        while (lanes[li] < 5) ++li;
+        lane_slot[s] = lanes[li++];
+      }
+      std::sort(warps.begin(), warps.end());
+      r = 0;
+      for (int s = 0; s < 5; ++s) p.order[r++] = (uint8_t)lane_slot[s];
+      for (int q : warps) p.order[r++] = (uint8_t)q;
+      for (int q : regs) p.order[r++] = (uint8_t)q;
+      p.transpose = 0;
+      for (int t2 = 0; t2 < k; ++t2)
+        if (p.order[t2] != p.sorder[t2]) p.transpose = 1;
+      // swizzle: the compute lanes, read at their storage ranks, must reach all 16
+      // low slots of shared memory (two lanes per 8-byte bank pair): storage ranks
+      // 0..3 cover their own low bits; each compute lane at a storage rank >= 4 adds
+      // one low bit not yet covered
+      int srank_of[32];
+      for (int t2 = 0; t2 < 32; ++t2) srank_of[t2] = -1;
+      for (int t2 = 0; t2 < k; ++t2) srank_of[p.sorder[t2]] = t2;
+      unsigned covered = 0;
+      for (int s = 0; s < 5; ++s) {
+        const int sr = srank_of[p.order[s]];
+        if (sr < 4) covered |= 1u << sr;
+      }
+      for (int s = 0; s < 5; ++s) {
+        const int sr = srank_of[p.order[s]];
+        if (sr < 4) continue;
+        for (int b = 0; b < 4; ++b)
+          if (!(covered & (1u << b))) {
+            p.swz[sr] = (uint8_t)(1u << b);
+            covered |= 1u << b;
+            break;
+          }
+      }
+    } else {
+      for (int q = 0; q < low; ++q) p.order[r++] = (uint8_t)q;
+      // warp ranks: the qubits after the first nreg (fewest gates), lowest first
+      std::vector<int> warp_q(hi.begin() + nreg, hi.end());
+      std::sort(warp_q.begin(), warp_q.end());
+      for (int q : warp_q) p.order[r++] = (uint8_t)q;
+      for (int t2 = 0; t2 < nreg; ++t2) p.order[r++] = (uint8_t)hi[t2];
+      for (int t2 = 0; t2 < k; ++t2) p.sorder[t2] = p.order[t2];
+    }
     int rank_of[32];
     for (int t2 = 0; t2 < 32; ++t2) rank_of[t2] = -1;
     for (int t2 = 0; t2 < k; ++t2) rank_of[p.order[t2]] = t2;
@@ -359,6 +420,37 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
       ops.push_back(o);
     }
     p.scale = (float)scale;
+    // register-part tables of the diagonal ops for the register-blocked sweep
+    if (k >= 8 && low == 5) {
+      const int R = k - 8;
+      uint32_t regmask = 0;
+      for (int t2 = 0; t2 < R; ++t2) regmask |= 1u << p.order[8 + t2];
+      for (size_t oi = (size_t)p.op_begin; oi < ops.size(); ++oi) {
+        OpRec& o = ops[oi];
+        if (o.type != OP_DIAG) continue;
+        memset(o.ereg, 0, sizeof o.ereg);
+        for (int jj = 0; jj < (1 << R); ++jj) {
+          uint32_t xr = 0;
+          for (int t2 = 0; t2 < R; ++t2)
+            if ((jj >> t2) & 1) xr |= 1u << p.order[8 + t2];
+          int s2 = 0;
+          for (int sc = 0; sc < o.nsh; ++sc) s2 += __builtin_popcount(xr & (xr >> o.sh_d[sc]) & o.sh_m[sc]);
+          const int e = (__builtin_popcount(xr & o.tmask) + 4 * s2) & 7;
+          o.ereg[jj / 8] |= (uint32_t)e << (4 * (jj % 8));
+        }
+        for (int t2 = 0; t2 < 8; ++t2) o.pq[t2] = 0xFF;
+        for (int t2 = 0; t2 < R; ++t2) {
+          const int q = p.order[8 + t2];
+          for (int sc = 0; sc < o.nsh; ++sc) {
+            const int d = (int)o.sh_d[sc];
+            int partner = -1;
+            if ((o.sh_m[sc] >> q) & 1u) partner = q + d;                      // pair (q, q + d)
+            if (q - d >= 0 && ((o.sh_m[sc] >> (q - d)) & 1u)) partner = q - d;  // pair (q - d, q)
+            if (partner >= 0 && !((regmask >> partner) & 1u)) o.pq[t2] = (uint8_t)partner;
+          }
+        }
+      }
+    }
     passes.push_back(p);
     first = false;
     i = j;

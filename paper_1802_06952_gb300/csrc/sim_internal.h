@@ -56,6 +56,13 @@ struct OpRec {
   uint8_t cutm[kMaxCutSlots];
   float m[8];
   double md[8];
+  // DIAG in the register-blocked sweep (set per pass by the scheduler): with x the
+  // thread part of the index plus the register part r(j) of element j,
+  //   ereg: exponent (mod 8) of the T and CZ terms within the register qubits,
+  //         4 bits per j (entry j at bits 4(j % 8) of ereg[j / 8])
+  //   pq[r]: the non-register CZ partner qubit of register rank r (0xFF: none)
+  uint32_t ereg[4];
+  uint8_t pq[8];
 };
 
 // One fused pass: stage 2^k amplitudes whose local bits are `local_mask`, run
@@ -76,6 +83,14 @@ struct PassDesc {
   int warp_gates;       // gates of the pass on warp-bit ranks (need a smem exchange)
   int general_gates;    // gates of the pass without a closed-form update (kind 0)
   float scale;          // product over the pass's gates of 1/2 (X^1/2, Y^1/2), 1/sqrt2 (H)
+  // register-blocked sweep with k >= 8: `order` is the compute order (lane ranks
+  // 0..4 may be any qubits); `sorder` is the storage order used for the global
+  // loads and stores (ranks 0..4 = qubits 0..4, coalesced); `swz[r]` is the 4-bit
+  // XOR mask storage rank r adds to the low bits of the shared-memory slot so
+  // both orders read and write shared memory without bank conflicts
+  uint8_t sorder[16];
+  uint8_t swz[16];
+  int transpose;        // compute order differs from storage order
 };
 
 // One level of the copy tree of a half: nodes share all gates up to the branch
@@ -167,6 +182,9 @@ struct SweepLaunch {
   int warp_gates;
   int general_gates;
   float scale;
+  uint8_t sorder[16];     // PassDesc::sorder, swz, transpose
+  uint8_t swz[16];
+  int transpose;
 };
 // staged-block sweep (any k, any threads)
 cudaError_t launch_sweep_c64(const SweepLaunch& L, cudaStream_t s);

@@ -100,6 +100,7 @@ struct SweepArgs {
 __global__ void __launch_bounds__(256) sweep_c64_kernel(SweepArgs a) {
   extern __shared__ float2 sm[];
   __shared__ uint32_t hi_off[256];
+  __shared__ uint32_t hi_off2[32];
   const int n = a.n, k = a.k, low = a.low;
   const uint32_t nb_log = (uint32_t)(n - k);
   const uint64_t bid = blockIdx.x;
@@ -110,22 +111,31 @@ __global__ void __launch_bounds__(256) sweep_c64_kernel(SweepArgs a) {
   float2* dst = a.dst_base + (uint64_t)ne.dst_row * stride;
   const float2* src = a.src == SRC_PARENT ? a.src_base + (uint64_t)ne.parent_slot * stride
                                           : (const float2*)dst;
-  // global index of local element i: base | (i & lowmask) | hi_off[i >> low]
+  // global index of local element i: base | (i & lowmask) | (hi_off[(i >> low) & 255] | hi_off2[i >> (low + 8)])
   uint32_t base = 0;
   for (uint32_t i = 0; i < nb_log; ++i)
     if ((g >> i) & 1u) base |= 1u << a.nonlocal[i];
+  // offsets of the local ranks above the identity prefix: ranks low..low+7 by
+  // hi_off, ranks low+8.. by hi_off2
   const int nhi = k - low;
-  for (int t = threadIdx.x; t < (1 << nhi); t += blockDim.x) {
+  const int n1 = nhi < 8 ? nhi : 8;
+  for (int t = threadIdx.x; t < (1 << n1); t += blockDim.x) {
     uint32_t off = 0;
-    for (int i = 0; i < nhi; ++i)
+    for (int i = 0; i < n1; ++i)
       if ((t >> i) & 1) off |= 1u << a.hi_pos[i];
     hi_off[t] = off;
+  }
+  for (int t = threadIdx.x; t < (1 << (nhi - n1)); t += blockDim.x) {
+    uint32_t off = 0;
+    for (int i = 0; i < nhi - n1; ++i)
+      if ((t >> i) & 1) off |= 1u << a.hi_pos[8 + i];
+    hi_off2[t] = off;
   }
   __syncthreads();
   const uint32_t lowmask = (1u << low) - 1;
   const int size = 1 << k;
   for (int i = threadIdx.x; i < size; i += blockDim.x) {
-    const uint32_t x = base | (i & lowmask) | hi_off[i >> low];
+    const uint32_t x = base | (i & lowmask) | (hi_off[(i >> low) & 255] | hi_off2[i >> (low + 8)]);
     float2 v;
     if (a.src == SRC_UNIFORM)
       v = make_float2(a.init_val, 0.f);
@@ -160,7 +170,7 @@ __global__ void __launch_bounds__(256) sweep_c64_kernel(SweepArgs a) {
       DiagState d;
       load_diag(op, ne.node_id, d);
       for (int i = threadIdx.x; i < size; i += blockDim.x) {
-        const uint32_t x = base | (i & lowmask) | hi_off[i >> low];
+        const uint32_t x = base | (i & lowmask) | (hi_off[(i >> low) & 255] | hi_off2[i >> (low + 8)]);
         bool keep;
         const int e = diag_exp(d, x, keep);
         sm[i] = keep ? cmul(sm[i], kOmegaF[e]) : make_float2(0.f, 0.f);
@@ -169,7 +179,7 @@ __global__ void __launch_bounds__(256) sweep_c64_kernel(SweepArgs a) {
     __syncthreads();
   }
   for (int i = threadIdx.x; i < size; i += blockDim.x) {
-    const uint32_t x = base | (i & lowmask) | hi_off[i >> low];
+    const uint32_t x = base | (i & lowmask) | (hi_off[(i >> low) & 255] | hi_off2[i >> (low + 8)]);
     dst[x] = sm[i];
   }
 }
@@ -247,8 +257,10 @@ cudaError_t launch_sweep_c64(const SweepLaunch& L, cudaStream_t s) {
   memset(&a, 0, sizeof a);
   a.n = L.n;
   a.k = L.k;
-  a.low = L.low;
-  if (a.low < 0 || a.low > 5 || a.low > L.k) return cudaErrorInvalidValue;
+  // the leading ranks that hold qubits 0, 1, ... in order index global memory
+  // directly (coalesced); any rank order is accepted
+  a.low = 0;
+  while (a.low < 5 && a.low < L.k && L.order[a.low] == a.low) ++a.low;
   a.local_mask = L.local_mask;
   a.ops = L.ops;
   a.op_count = L.op_count;
@@ -256,16 +268,11 @@ cudaError_t launch_sweep_c64(const SweepLaunch& L, cudaStream_t s) {
   a.nodes = L.nodes;
   a.src_base = (const float2*)L.src_base;
   a.dst_base = (float2*)L.dst_base;
-  // local ranks follow the pass's rank order (ranks 0..low-1 are qubits 0..low-1)
   int nh = 0, nn = 0;
   for (int r = 0; r < L.k; ++r) {
     const int q = L.order[r];
     if (q >= L.n || !(L.local_mask & (1u << q))) return cudaErrorInvalidValue;
-    if (r < a.low) {
-      if (q != r) return cudaErrorInvalidValue;
-    } else {
-      a.hi_pos[nh++] = (uint8_t)q;
-    }
+    if (r >= a.low) a.hi_pos[nh++] = (uint8_t)q;
   }
   for (int q = 0; q < L.n; ++q)
     if (!(L.local_mask & (1u << q))) a.nonlocal[nn++] = (uint8_t)q;

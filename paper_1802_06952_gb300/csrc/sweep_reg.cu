@@ -1,0 +1,455 @@
+// Register-blocked fused gate sweep over complex64 half-states (Supplementary A,
+// Eq. 4 gate by gate; the diagonal gates of a layer combined into one phase and
+// mask per amplitude, Section 2.4, Eqs. 3-6).
+//
+// A block of 256 threads handles the 2^k amplitudes (k = 8 + R) of one assignment
+// of the pass's non-local qubits.  Two bit orders of the staged index are used:
+//   storage order  ranks 0..4 = qubits 0..4 (the warp lanes), so every warp loads
+//                  and stores 256 contiguous bytes of the state
+//   compute order  ranks 0..4 (lanes), 8..k-1 (the R register bits of each thread)
+//                  hold the pass's busiest gate qubits, ranks 5..7 (warps) the rest
+// When the two differ, the block transposes once after the load and once before
+// the store through shared memory, in a layout whose low 4 slot bits are XORed
+// with a per-pass mask of the high bits so that both orders are bank-conflict free.
+// In compute order each thread keeps its 2^R amplitudes in registers:
+//   gate on a register rank  register pairs, no data exchange
+//   gate on a lane rank      partner value by warp shuffle
+//   gate on a warp rank      partner value through shared memory (two barriers)
+//   diagonal op              per amplitude phase w^e and projector test
+// X^1/2, Y^1/2 and H are applied as 2 X^1/2, 2 Y^1/2 and sqrt2 H (additions only);
+// the pass multiplies by the product of the omitted factors when it stores.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "../../include/sim.h"
+#include "sim_internal.h"
+
+namespace sim {
+namespace {
+
+constexpr float kS2 = 0.70710678118654752f;  // 1/sqrt(2)
+
+struct RegArgs {
+  int n, k;
+  const OpRec* ops;
+  int op_count;
+  int src;
+  const NodeEntry* nodes;
+  int64_t slot_begin;
+  const float2* src_base;
+  float2* dst_base;
+  uint8_t cpos[16];      // qubit of each compute rank
+  uint8_t spos[16];      // qubit of each storage rank
+  uint8_t c2s[16];       // storage rank of each compute rank
+  uint8_t swz[16];       // slot XOR mask of each storage rank (0 below rank 4)
+  uint8_t cswz[16];      // swz of the storage rank of each compute rank
+  uint8_t nonlocal[32];  // non-local qubits (block index bits)
+  float init_val;
+  float scale;           // product of the factors the unscaled gate updates leave out
+  int transpose;
+};
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// (a0, a1) <- 2 X^1/2, 2 Y^1/2 or sqrt2 H applied to the pair
+//   2 X^1/2 = [[1+i, 1-i], [1-i, 1+i]]:  s + i d, s - i d   (s = a0 + a1, d = a0 - a1)
+//   2 Y^1/2 = [[1+i, -1-i], [1+i, 1+i]]: (1+i) d, (1+i) s
+//   sqrt2 H = [[1, 1], [1, -1]]:         s, d
+template <int KIND>
+__device__ __forceinline__ void pair_update(float2& a0, float2& a1) {
+  const float2 s = make_float2(a0.x + a1.x, a0.y + a1.y);
+  const float2 d = make_float2(a0.x - a1.x, a0.y - a1.y);
+  if (KIND == 1) {
+    a0 = make_float2(s.x - d.y, s.y + d.x);
+    a1 = make_float2(s.x + d.y, s.y - d.x);
+  } else if (KIND == 2) {
+    a0 = make_float2(d.x - d.y, d.x + d.y);
+    a1 = make_float2(s.x - s.y, s.x + s.y);
+  } else {
+    a0 = s;
+    a1 = d;
+  }
+}
+
+template <int R, int B, int KIND>
+__device__ __forceinline__ void reg_pairs(float2 (&v)[1 << R]) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j)
+    if (!(j & (1 << B))) pair_update<KIND>(v[j], v[j | (1 << B)]);
+}
+
+template <int R, int B>
+__device__ __forceinline__ void reg_gate_b(float2 (&v)[1 << R], int kind) {
+  if constexpr (B < R) {
+    if (kind == 1)
+      reg_pairs<R, B, 1>(v);
+    else if (kind == 2)
+      reg_pairs<R, B, 2>(v);
+    else
+      reg_pairs<R, B, 3>(v);
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void reg_gate(float2 (&v)[1 << R], int b, int kind) {
+  switch (b) {
+    case 0: reg_gate_b<R, 0>(v, kind); break;
+    case 1: reg_gate_b<R, 1>(v, kind); break;
+    case 2: reg_gate_b<R, 2>(v, kind); break;
+    case 3: reg_gate_b<R, 3>(v, kind); break;
+    case 4: reg_gate_b<R, 4>(v, kind); break;
+    default: break;
+  }
+}
+
+// One side of a pair from its own value and the partner's value p; side 0 holds
+// a0 and side 1 holds a1 (same unscaled updates as pair_update).
+template <int KIND>
+__device__ __forceinline__ float2 side_update(float2 o, float2 p, float sg) {
+  if (KIND == 1) {  // (1+i) o + (1-i) p on both sides
+    return make_float2(o.x - o.y + p.x + p.y, o.x + o.y - p.x + p.y);
+  } else if (KIND == 2) {  // (1+i)(o + sg p), sg = -1 on side 0, +1 on side 1
+    const float2 z = make_float2(fmaf(sg, p.x, o.x), fmaf(sg, p.y, o.y));
+    return make_float2(z.x - z.y, z.x + z.y);
+  } else {  // p - sg o: side 0 o + p, side 1 p - o
+    return make_float2(fmaf(-sg, o.x, p.x), fmaf(-sg, o.y, p.y));
+  }
+}
+
+template <int R, int KIND>
+__device__ __forceinline__ void lane_gate_k(float2 (&v)[1 << R], int mask, float sg) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) {
+    float2 p;
+    p.x = __shfl_xor_sync(0xffffffffu, v[j].x, mask);
+    p.y = __shfl_xor_sync(0xffffffffu, v[j].y, mask);
+    v[j] = side_update<KIND>(v[j], p, sg);
+  }
+}
+
+template <int R, int KIND>
+__device__ __forceinline__ void smem_gate_k(float2 (&v)[1 << R], float2* xs, int t, int pt, float sg) {
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) xs[j * 256 + t] = v[j];
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < (1 << R); ++j) v[j] = side_update<KIND>(v[j], xs[j * 256 + pt], sg);
+  __syncthreads();
+}
+
+struct Diag {
+  uint32_t tmask, pmask, pval, zmask;
+  int nsh;
+  uint32_t sh_d[kMaxShift], sh_m[kMaxShift];
+};
+
+__device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, Diag& d) {
+  d.tmask = __ldg(&op->tmask);
+  d.nsh = __ldg(&op->nsh);
+#pragma unroll
+  for (int s = 0; s < kMaxShift; ++s) {
+    d.sh_d[s] = __ldg(&op->sh_d[s]);
+    d.sh_m[s] = __ldg(&op->sh_m[s]);
+  }
+  const int ncut = __ldg(&op->ncut);
+  const int half = __ldg(&op->half);
+  d.pmask = d.pval = d.zmask = 0;
+  for (int i = 0; i < ncut; ++i) {
+    const uint32_t qb = 1u << op->cutq[i];
+    const uint32_t l = (uint32_t)((node_id >> op->cutm[i]) & 1ull);
+    if (half == 0) {
+      d.pmask |= qb;
+      if (l) d.pval |= qb;
+    } else if (l) {
+      d.zmask |= qb;
+    }
+  }
+}
+
+// slot XOR mask of a storage index built from the thread bits t (ranks 0..7)
+__device__ __forceinline__ uint32_t swz_thread(const RegArgs& a, uint32_t t) {
+  uint32_t z = 0;
+#pragma unroll
+  for (int r = 4; r < 8; ++r)
+    if ((t >> r) & 1u) z ^= a.swz[r];
+  return z;
+}
+
+template <int R>
+__global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArgs a) {
+  constexpr int NE = 1 << R;
+  extern __shared__ float2 xs[];  // 2^k slots: transposes and warp-rank gates
+  __shared__ float2 s_omega[8];   // w^e, w = e^{i pi / 4}
+  const int t = threadIdx.x;
+  const int lane = t & 31;
+  if (t < 8) {
+    // w^t: (+-1, 0), (0, +-1) for even t; (+-1/sqrt2, +-1/sqrt2) for odd t
+    const int quad = t >> 1;
+    float re, im;
+    if (t & 1) {
+      re = (quad == 0 || quad == 3) ? kS2 : -kS2;
+      im = (quad <= 1) ? kS2 : -kS2;
+    } else {
+      re = quad == 0 ? 1.f : (quad == 2 ? -1.f : 0.f);
+      im = quad == 1 ? 1.f : (quad == 3 ? -1.f : 0.f);
+    }
+    s_omega[t] = make_float2(re, im);
+  }
+  const uint32_t nb_log = (uint32_t)(a.n - a.k);
+  const uint64_t bid = blockIdx.x;
+  const int64_t slot = a.slot_begin + (int64_t)(bid >> nb_log);
+  const uint32_t g = (uint32_t)(bid & ((1ull << nb_log) - 1));
+  const NodeEntry ne = a.nodes[slot];
+  const uint64_t stride = 1ull << a.n;
+  float2* dst = a.dst_base + (uint64_t)ne.dst_row * stride;
+  const float2* src = a.src == SRC_PARENT ? a.src_base + (uint64_t)ne.parent_slot * stride : (const float2*)dst;
+  uint32_t base = 0;
+  for (uint32_t i = 0; i < nb_log; ++i)
+    if ((g >> i) & 1u) base |= 1u << a.nonlocal[i];
+  // storage-order address of this thread's elements: st | sreg(j)
+  uint32_t st = base;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+    if ((t >> r) & 1) st |= 1u << a.spos[r];
+  auto sreg = [&](int j) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if ((j >> r) & 1) o |= 1u << a.spos[8 + r];
+    return o;
+  };
+  float2 v[NE];
+  if (a.src == SRC_UNIFORM) {
+#pragma unroll
+    for (int j = 0; j < NE; ++j) v[j] = make_float2(a.init_val, 0.f);
+  } else if (a.src == SRC_ZERO) {
+#pragma unroll
+    for (int j = 0; j < NE; ++j) v[j] = make_float2((st | sreg(j)) == 0 ? 1.f : 0.f, 0.f);
+  } else {
+#pragma unroll
+    for (int j = 0; j < NE; ++j) v[j] = src[st | sreg(j)];
+  }
+  // shared-memory slots: storage index s = t + 256 j sits at s ^ swz(s); the
+  // compute-order element (t, j) is storage index P(t) | P(j)
+  const uint32_t sslot_t = (uint32_t)t ^ swz_thread(a, (uint32_t)t);
+  auto sslot_j = [&](int j) {
+    uint32_t z = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if ((j >> r) & 1) z ^= a.swz[8 + r];
+    return ((uint32_t)j << 8) ^ z;
+  };
+  uint32_t cslot_t = 0;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+    if ((t >> r) & 1) cslot_t |= 1u << a.c2s[r];
+  {
+    uint32_t z = 0;
+#pragma unroll
+    for (int r = 0; r < 8; ++r)
+      if ((t >> r) & 1) z ^= a.cswz[r];
+    cslot_t ^= z;
+  }
+  auto cslot_j = [&](int j) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if ((j >> r) & 1) o ^= (1u << a.c2s[8 + r]) ^ a.cswz[8 + r];
+    return o;
+  };
+  __syncthreads();  // s_omega
+  if (a.transpose) {
+#pragma unroll
+    for (int j = 0; j < NE; ++j) xs[sslot_t ^ sslot_j(j)] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NE; ++j) v[j] = xs[cslot_t ^ cslot_j(j)];
+    __syncthreads();
+  }
+  // compute-order global index bits for the diagonal ops
+  uint32_t xt = base;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+    if ((t >> r) & 1) xt |= 1u << a.cpos[r];
+  uint32_t regmask = 0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) regmask |= 1u << a.cpos[8 + r];
+  for (int o = 0; o < a.op_count; ++o) {
+    const OpRec* op = a.ops + o;
+    if (__ldg(&op->type) == OP_GATE) {
+      const int lq = __ldg(&op->lq);
+      const int kind = __ldg(&op->kind);
+      if (lq >= 8) {
+        reg_gate<R>(v, lq - 8, kind);
+      } else if (lq < 5) {
+        const float sg = ((lane >> lq) & 1) ? 1.f : -1.f;
+        const int mask = 1 << lq;
+        if (kind == 1)
+          lane_gate_k<R, 1>(v, mask, sg);
+        else if (kind == 2)
+          lane_gate_k<R, 2>(v, mask, sg);
+        else
+          lane_gate_k<R, 3>(v, mask, sg);
+      } else {
+        const float sg = ((t >> lq) & 1) ? 1.f : -1.f;
+        const int pt = t ^ (1 << lq);
+        if (kind == 1)
+          smem_gate_k<R, 1>(v, xs, t, pt, sg);
+        else if (kind == 2)
+          smem_gate_k<R, 2>(v, xs, t, pt, sg);
+        else
+          smem_gate_k<R, 3>(v, xs, t, pt, sg);
+      }
+    } else {
+      // exponent of w at x = xt | r(j): the thread part (T and CZ terms within xt)
+      // once per op, the register part from the op's table, and the CZ pairs between
+      // a register qubit and a thread or non-local qubit as 4 popc(j & B)
+      const uint32_t tmask = __ldg(&op->tmask);
+      const int nsh = __ldg(&op->nsh);
+      int s2 = 0;
+#pragma unroll
+      for (int s = 0; s < kMaxShift; ++s)
+        if (s < nsh) s2 += __popc(xt & (xt >> __ldg(&op->sh_d[s])) & __ldg(&op->sh_m[s]));
+      int et = __popc(xt & tmask) + 4 * s2;
+      uint32_t B = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t pq = __ldg(&op->pq[r]);
+        if (pq != 0xFFu && ((xt >> pq) & 1u)) B |= 1u << r;
+      }
+      // cut slots of this copy-tree node: Z^l signs (lower half), P_l projectors
+      // (upper half) split the same way
+      bool proj = false, keep_t = true;
+      uint32_t pm_r = 0, pv_r = 0;
+      if (__ldg(&op->ncut)) {
+        Diag d;
+        load_diag(op, ne.node_id, d);
+        et += 4 * __popc(xt & d.zmask);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t qb = 1u << a.cpos[8 + r];
+          if (d.zmask & qb) B ^= 1u << r;
+          if (d.pmask & qb) {
+            pm_r |= 1u << r;
+            if (d.pval & qb) pv_r |= 1u << r;
+          }
+        }
+        if (d.pmask) {
+          proj = true;
+          keep_t = (xt & d.pmask & ~regmask) == (d.pval & ~regmask);
+        }
+      }
+      uint32_t ew[4];
+#pragma unroll
+      for (int w4 = 0; w4 < 4; ++w4) ew[w4] = (w4 * 8 < NE) ? __ldg(&op->ereg[w4]) : 0u;
+#pragma unroll
+      for (int j = 0; j < NE; ++j) {
+        const int e = (et + (int)((ew[j >> 3] >> (4 * (j & 7))) & 7u) + 4 * __popc(B & (uint32_t)j)) & 7;
+        v[j] = cmul(v[j], s_omega[e]);
+        if (proj && !(keep_t && (((uint32_t)j & pm_r) == pv_r))) v[j] = make_float2(0.f, 0.f);
+      }
+    }
+  }
+  if (a.transpose) {
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NE; ++j) xs[cslot_t ^ cslot_j(j)] = v[j];
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NE; ++j) v[j] = xs[sslot_t ^ sslot_j(j)];
+  }
+#pragma unroll
+  for (int j = 0; j < NE; ++j) dst[st | sreg(j)] = make_float2(v[j].x * a.scale, v[j].y * a.scale);
+}
+
+template <int R>
+cudaError_t launch_r(const RegArgs& a, int64_t nslots, int use_smem, cudaStream_t s) {
+  const size_t smem = use_smem ? (sizeof(float2) << (8 + R)) : 0;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(sweep_reg_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(float2) << (8 + R)));
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const uint64_t bps = 1ull << (a.n - a.k);
+  const int64_t max_slots = (int64_t)((1ull << 30) / bps) > 0 ? (int64_t)((1ull << 30) / bps) : 1;
+  RegArgs b = a;
+  for (int64_t s0 = 0; s0 < nslots; s0 += max_slots) {
+    const int64_t ns = (nslots - s0) < max_slots ? (nslots - s0) : max_slots;
+    b.slot_begin = s0;
+    sweep_reg_kernel<R><<<(unsigned)(ns * bps), 256, smem, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    note_launches(SIM_PHASE_SWEEP, 1);
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+
+bool sweep2_supported(const SweepLaunch& L) {
+  return L.k >= 8 && L.k <= 13 && L.low == 5 && L.n >= L.k && !L.general_gates;
+}
+
+cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s) {
+  if (!sweep2_supported(L)) return cudaErrorInvalidValue;
+  RegArgs a;
+  memset(&a, 0, sizeof a);
+  a.n = L.n;
+  a.k = L.k;
+  a.ops = L.ops;
+  a.op_count = L.op_count;
+  a.src = L.src;
+  a.nodes = L.nodes;
+  a.src_base = (const float2*)L.src_base;
+  a.dst_base = (float2*)L.dst_base;
+  // validate both orders: permutations of the same k local qubits, storage ranks
+  // 0..4 = qubits 0..4, slot masks only on storage ranks >= 4 and below 16
+  uint32_t seen_c = 0, seen_s = 0;
+  int srank[32];
+  for (int q = 0; q < 32; ++q) srank[q] = -1;
+  for (int r = 0; r < L.k; ++r) {
+    const int qc = L.order[r], qs = L.sorder[r];
+    if (qc >= L.n || qs >= L.n || (seen_c & (1u << qc)) || (seen_s & (1u << qs))) return cudaErrorInvalidValue;
+    if (r < 5 && qs != r) return cudaErrorInvalidValue;
+    if ((r < 4 && L.swz[r] != 0) || L.swz[r] > 15) return cudaErrorInvalidValue;
+    seen_c |= 1u << qc;
+    seen_s |= 1u << qs;
+    srank[qs] = r;
+    a.cpos[r] = (uint8_t)qc;
+    a.spos[r] = (uint8_t)qs;
+    a.swz[r] = L.swz[r];
+  }
+  if (seen_c != seen_s) return cudaErrorInvalidValue;
+  if (!L.transpose)
+    for (int r = 0; r < L.k; ++r)
+      if (L.order[r] != L.sorder[r]) return cudaErrorInvalidValue;
+  for (int r = 0; r < L.k; ++r) {
+    a.c2s[r] = (uint8_t)srank[L.order[r]];
+    a.cswz[r] = L.swz[a.c2s[r]];
+  }
+  int nn = 0;
+  for (int q = 0; q < L.n; ++q)
+    if (!(seen_c & (1u << q))) a.nonlocal[nn++] = (uint8_t)q;
+  if (nn != L.n - L.k) return cudaErrorInvalidValue;
+  a.init_val = (float)ldexp(1.0, -(L.n / 2)) * ((L.n & 1) ? 0.70710678118654752f : 1.f);
+  a.scale = L.scale;
+  a.transpose = L.transpose;
+  const int use_smem = L.warp_gates > 0 || L.transpose;
+  switch (L.k - 8) {
+    case 0: return launch_r<0>(a, L.nslots, use_smem, s);
+    case 1: return launch_r<1>(a, L.nslots, use_smem, s);
+    case 2: return launch_r<2>(a, L.nslots, use_smem, s);
+    case 3: return launch_r<3>(a, L.nslots, use_smem, s);
+    case 4: return launch_r<4>(a, L.nslots, use_smem, s);
+    default: return launch_r<5>(a, L.nslots, use_smem, s);
+  }
+}
+
+}  // namespace sim
