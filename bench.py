@@ -120,10 +120,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_from_profile(kernel_src):
+def traffic_from_profile(kernel_src, summary):
     """dram bytes per launch from the committed ncu summary, if it was taken on the
     current source of the kernel (sha256 of the .cu file recorded beside it)."""
-    p = os.path.join(ROOT, "profiles", "tc_gemm_30q_ncu.md")
+    p = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(p):
         return None
     sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()
@@ -330,8 +330,10 @@ def run_ours(args):
     gemm_ms = ms[sim.SIM_PHASE_CONTRACT] / max(1, inst[sim.SIM_PHASE_CONTRACT])
     hbm, bf16, bf16_sus, src = peaks()
     achieved = flops / (gemm_ms / 1e3) / 1e12
-    kernel_src = os.path.join(ROOT, "paper_1802_06952_gb300", "csrc", "gemm_tc.cu")
-    traffic = traffic_from_profile(kernel_src)
+    # the CTA-pair kernel unless SIM_TC_PAIR=0 selects the single-CTA one
+    pair = os.environ.get("SIM_TC_PAIR", "1") != "0"
+    kernel_src = os.path.join(ROOT, "paper_1802_06952_gb300", "csrc", "gemm_tc_pair.cu" if pair else "gemm_tc.cu")
+    traffic = traffic_from_profile(kernel_src, "tc_gemm_pair_30q_ncu.md" if pair else "tc_gemm_30q_ncu.md")
     sweep_ms = ms[0] / max(1, args.steps)
     phases = {sim.PHASE_NAMES[i]: {"ms_per_step": ms[i] / args.steps, "launches": int(launches[i])}
               for i in range(sim.SIM_NUM_PHASES) if inst[i] or launches[i]}
@@ -348,7 +350,8 @@ def run_ours(args):
                    "step_ms_median": statistics.median(step_ms)},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
                      "frac": achieved / bf16, "traffic": traffic,
-                     "kernel": "tc_gemm_kernel (split-bf16 contraction)",
+                     "kernel": ("tc_gemm_pair_kernel (split-bf16 contraction, CTA pairs)" if pair
+                                else "tc_gemm_kernel (split-bf16 contraction)"),
                      "peak_source": "%s bf16 burst" % src,
                      "achieved_def": "24*M*N*K issued bf16 flops (M=N=32768, K=256) / avg launch ms (CUDA events)",
                      "launch_ms": gemm_ms},

@@ -241,6 +241,10 @@ struct TcGemmArgs {
   unsigned long long* st_hist = nullptr;  // SIM_KS_BINS counts of u = 1 - exp(-2^n |A|^2)
 };
 cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s);
+// CTA-pair variant of the same contraction (tcgen05 cta_group::2, M = 256 per pair)
+bool tc_gemm_pair_enabled();
+bool tc_gemm_pair_supported(const TcGemmArgs& a);
+cudaError_t launch_tc_gemm_pair(const TcGemmArgs& a, cudaStream_t s);
 // values written to *d_status when a bounded wait of the contraction gives up
 constexpr int SIM_TIMEOUT_CODE_TMA = 0x101;
 constexpr int SIM_TIMEOUT_CODE_MMA = 0x102;

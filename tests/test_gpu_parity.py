@@ -129,6 +129,7 @@ def test_leaf_half_states_fidelity():
     (4, 5, 16, 0, 300, 77, 0, None),      # ragged selections, all copies
     (4, 5, 16, 1, 1, 1, 3, 16),           # single amplitude, copy subrange
     (6, 4, 17, 3, 129, 257, 5, 18),       # tile edges +-1, 13 copies
+    (6, 4, 17, 3, 130, 257, 0, None),     # CTA-pair tiles with ragged rows and columns
     (4, 4, 10, 2, 256, 256, 0, None),     # "selection" of every index, shuffled order
 ])
 def test_selection_and_copy_ranges(R, C, d, seed, nsu, nsl, k0, k1):
@@ -189,6 +190,42 @@ def test_many_copies_chunked_accumulation():
         sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, True, out)
         sim.sim_status()
         assert rel_err(out.cpu().numpy(), ref + part) <= TOL_SPLIT
+    finally:
+        r.close()
+
+
+def test_stats_fused_with_chunked_and_accumulated_contraction():
+    """Statistics fused into the contraction when the final amplitudes are formed by
+    a read-modify-write: 4096 copies (16 tensor-memory runs of 256 copies), and a
+    second copy batch added into an existing output."""
+    R, C, d, seed, b = 4, 6, 23, 8, 2
+    gates, plan = oc.grid_cut(R, C, d, seed, b)
+    rng = np.random.default_rng(5)
+    su = np.unique(rng.integers(0, 1 << plan.n_u, 800)).astype(np.uint64)
+    su = su[: su.size & ~1]  # an even count: 16-byte output rows (CTA-pair kernel)
+    sl = np.unique(rng.integers(0, 1 << plan.n_l, 600)).astype(np.uint64)
+    nq = plan.n_u + plan.n_l
+    ref = oracle.cut_amplitudes(plan, su, sl)
+    st_ref, hist_ref = oracle.stats(ref, nq)
+    n = ref.size
+    r = Run(R, C, d, seed, b)
+    try:
+        out = torch.zeros((sl.size, su.size), dtype=torch.complex64, device="cuda")
+        h = r.evolve(sim.SIM_C64, 0, None, su, sl)
+        results = [sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_BF16, False, out, want_hist=True)]
+        assert rel_err(out.cpu().numpy(), ref) <= TOL_SPLIT
+        out.zero_()
+        h = r.evolve(sim.SIM_C64, 0, 1000, su, sl)
+        sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, out)
+        h = r.evolve(sim.SIM_C64, 1000, None, su, sl)
+        results.append(sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_BF16, True, out, want_hist=True))
+        assert rel_err(out.cpu().numpy(), ref) <= TOL_SPLIT
+        for st, hist in results:
+            assert abs(st[0] - st_ref[0]) <= 1e-5 * st_ref[0]
+            assert abs(st[1] - st_ref[1]) <= 1e-5 * st_ref[1]
+            assert abs(st[2] - st_ref[2]) < 1e-4
+            assert hist.sum() == hist_ref.sum() == n
+            assert np.abs(hist.astype(np.int64) - hist_ref.astype(np.int64)).sum() <= n // 50
     finally:
         r.close()
 
