@@ -454,6 +454,8 @@ int evolve_c64_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t*
     sl.warp_gates = pd.warp_gates;
     sl.general_gates = pd.general_gates;
     sl.scale = pd.scale;
+    sl.phase_e = pd.phase_e;
+    sl.phase_op = pd.phase_op;
     memcpy(sl.sorder, pd.sorder, sizeof sl.sorder);
     memcpy(sl.swz, pd.swz, sizeof sl.swz);
     sl.transpose = pd.transpose;

@@ -290,6 +290,8 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
     p.op_count = 0;
     p.src = first_src;
     p.scale = 1.f;
+    p.phase_e = 0;
+    p.phase_op = -1;
     for (int r = 0; r < k; ++r) p.order[r] = (uint8_t)r;
     passes.push_back(p);
     return;
@@ -299,6 +301,7 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
     int cnt = low;
     size_t j = i;
     for (; j < seq.size(); ++j) {
+      if ((int)(j - i) >= kMaxPassOps) break;
       if (seq[j].type != OP_GATE) continue;
       uint32_t bit = 1u << seq[j].q;
       if (local & bit) continue;
@@ -404,22 +407,27 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
     for (int t2 = 0; t2 < k; ++t2) rank_of[p.order[t2]] = t2;
     p.warp_gates = 0;
     p.general_gates = 0;
-    double scale = 1.0;
+    int n_xy = 0, n_h = 0;
+    p.phase_op = -1;
     for (size_t t = i; t < j; ++t) {
       OpRec o = seq[t];
       if (o.type == OP_GATE) {
         o.lq = rank_of[o.q];
         if (k >= 8 && o.lq >= 5 && o.lq < 8) ++p.warp_gates;
         if (o.kind == 1 || o.kind == 2)
-          scale *= 0.5;
+          ++n_xy;
         else if (o.kind == 3)
-          scale *= 0.70710678118654752440;
+          ++n_h;
         else
           ++p.general_gates;
+      } else {
+        p.phase_op = (int)(t - i);
       }
       ops.push_back(o);
     }
-    p.scale = (float)scale;
+    p.scale = (float)std::ldexp(n_xy + n_h == 0 ? 1.0 : ((n_xy + n_h) & 1 ? 0.70710678118654752440 : 1.0),
+                                -((n_xy + n_h) / 2));
+    p.phase_e = n_xy & 7;
     // register-part tables of the diagonal ops for the register-blocked sweep
     if (k >= 8 && low == 5) {
       const int R = k - 8;

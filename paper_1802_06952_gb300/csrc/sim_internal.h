@@ -65,6 +65,10 @@ struct OpRec {
   uint8_t pq[8];
 };
 
+// At most this many ops per fused pass (the register-blocked sweep copies a pass's
+// ops into shared memory).
+constexpr int kMaxPassOps = 64;
+
 // One fused pass: stage 2^k amplitudes whose local bits are `local_mask`, run
 // ops [op_begin, op_begin + op_count), write back.
 enum PassSrc : int { SRC_SELF = 0, SRC_PARENT = 1, SRC_UNIFORM = 2, SRC_ZERO = 3 };
@@ -82,7 +86,13 @@ struct PassDesc {
   uint8_t order[16];
   int warp_gates;       // gates of the pass on warp-bit ranks (need a smem exchange)
   int general_gates;    // gates of the pass without a closed-form update (kind 0)
-  float scale;          // product over the pass's gates of 1/2 (X^1/2, Y^1/2), 1/sqrt2 (H)
+  // The register-blocked sweep applies X^1/2, Y^1/2 and H without their common
+  // factors ((1+i)/2, (1+i)/2, 1/sqrt2): scale = 2^(-(n_xy + n_h)/2) is applied when
+  // the pass stores, and the phase w^(n_xy) (w = e^{i pi/4}) is added to the exponent
+  // of diagonal op phase_op of the pass (relative index; -1: applied at the store).
+  float scale;
+  int phase_e;
+  int phase_op;
   // register-blocked sweep with k >= 8: `order` is the compute order (lane ranks
   // 0..4 may be any qubits); `sorder` is the storage order used for the global
   // loads and stores (ranks 0..4 = qubits 0..4, coalesced); `swz[r]` is the 4-bit
@@ -182,6 +192,7 @@ struct SweepLaunch {
   int warp_gates;
   int general_gates;
   float scale;
+  int phase_e, phase_op;  // PassDesc::phase_e, phase_op
   uint8_t sorder[16];     // PassDesc::sorder, swz, transpose
   uint8_t swz[16];
   int transpose;

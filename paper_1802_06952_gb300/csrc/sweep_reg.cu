@@ -16,8 +16,10 @@
 //   gate on a lane rank      partner value by warp shuffle
 //   gate on a warp rank      partner value through shared memory (two barriers)
 //   diagonal op              per amplitude phase w^e and projector test
-// X^1/2, Y^1/2 and H are applied as 2 X^1/2, 2 Y^1/2 and sqrt2 H (additions only);
-// the pass multiplies by the product of the omitted factors when it stores.
+// X^1/2 = (1+i)/2 [[1, -i], [-i, 1]], Y^1/2 = (1+i)/2 [[1, -1], [1, 1]] and
+// H = 1/sqrt2 [[1, 1], [1, -1]] are applied without their scalar factors (additions
+// only); the pass multiplies by 2^(-(n_xy + n_h)/2) when it stores and adds the
+// phase w^(n_xy) to one of its diagonal ops (or applies it at the store).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -48,31 +50,39 @@ struct RegArgs {
   uint8_t cswz[16];      // swz of the storage rank of each compute rank
   uint8_t nonlocal[32];  // non-local qubits (block index bits)
   float init_val;
-  float scale;           // product of the factors the unscaled gate updates leave out
+  float scale;           // 2^(-(n_xy + n_h)/2): the real part of the factors left out
+  int phase_e;           // w^phase_e: their phase
+  int phase_op;          // diagonal op that takes the phase (-1: the store)
   int transpose;
+  uint32_t xs_bytes;     // shared-memory slots before the copy of the ops
 };
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
-// (a0, a1) <- 2 X^1/2, 2 Y^1/2 or sqrt2 H applied to the pair
-//   2 X^1/2 = [[1+i, 1-i], [1-i, 1+i]]:  s + i d, s - i d   (s = a0 + a1, d = a0 - a1)
-//   2 Y^1/2 = [[1+i, -1-i], [1+i, 1+i]]: (1+i) d, (1+i) s
-//   sqrt2 H = [[1, 1], [1, -1]]:         s, d
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// (a0, a1) <- the unscaled update of the pair
+//   [[1, -i], [-i, 1]] (X^1/2):  a0 - i a1, a1 - i a0
+//   [[1, -1], [1, 1]]  (Y^1/2):  a0 - a1,   a0 + a1
+//   [[1, 1], [1, -1]]  (H):      a0 + a1,   a0 - a1
+// The last two are the same on both components (packed fp32x2 additions).
 template <int KIND>
 __device__ __forceinline__ void pair_update(float2& a0, float2& a1) {
-  const float2 s = make_float2(a0.x + a1.x, a0.y + a1.y);
-  const float2 d = make_float2(a0.x - a1.x, a0.y - a1.y);
   if (KIND == 1) {
-    a0 = make_float2(s.x - d.y, s.y + d.x);
-    a1 = make_float2(s.x + d.y, s.y - d.x);
+    const float2 b0 = make_float2(a0.x + a1.y, a0.y - a1.x);
+    a1 = make_float2(a1.x + a0.y, a1.y - a0.x);
+    a0 = b0;
   } else if (KIND == 2) {
-    a0 = make_float2(d.x - d.y, d.x + d.y);
-    a1 = make_float2(s.x - s.y, s.x + s.y);
+    const float2 b0 = sub2(a0, a1);
+    a1 = add2(a0, a1);
+    a0 = b0;
   } else {
-    a0 = s;
-    a1 = d;
+    const float2 b0 = add2(a0, a1);
+    a1 = sub2(a0, a1);
+    a0 = b0;
   }
 }
 
@@ -107,17 +117,17 @@ __device__ __forceinline__ void reg_gate(float2 (&v)[1 << R], int b, int kind) {
   }
 }
 
-// One side of a pair from its own value and the partner's value p; side 0 holds
-// a0 and side 1 holds a1 (same unscaled updates as pair_update).
+// One side of a pair from its own value o and the partner's value p; side 0 holds
+// a0 and side 1 holds a1, sg = -1 on side 0 and +1 on side 1 (same unscaled updates
+// as pair_update).
 template <int KIND>
 __device__ __forceinline__ float2 side_update(float2 o, float2 p, float sg) {
-  if (KIND == 1) {  // (1+i) o + (1-i) p on both sides
-    return make_float2(o.x - o.y + p.x + p.y, o.x + o.y - p.x + p.y);
-  } else if (KIND == 2) {  // (1+i)(o + sg p), sg = -1 on side 0, +1 on side 1
-    const float2 z = make_float2(fmaf(sg, p.x, o.x), fmaf(sg, p.y, o.y));
-    return make_float2(z.x - z.y, z.x + z.y);
-  } else {  // p - sg o: side 0 o + p, side 1 p - o
-    return make_float2(fmaf(-sg, o.x, p.x), fmaf(-sg, o.y, p.y));
+  if (KIND == 1) {  // o - i p on both sides
+    return __ffma2_rn(make_float2(1.f, -1.f), make_float2(p.y, p.x), o);
+  } else if (KIND == 2) {  // side 0: o - p, side 1: o + p
+    return __ffma2_rn(make_float2(sg, sg), p, o);
+  } else {  // side 0: p + o, side 1: p - o
+    return __ffma2_rn(make_float2(-sg, -sg), o, p);
   }
 }
 
@@ -149,15 +159,15 @@ struct Diag {
 };
 
 __device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, Diag& d) {
-  d.tmask = __ldg(&op->tmask);
-  d.nsh = __ldg(&op->nsh);
+  d.tmask = op->tmask;
+  d.nsh = op->nsh;
 #pragma unroll
   for (int s = 0; s < kMaxShift; ++s) {
-    d.sh_d[s] = __ldg(&op->sh_d[s]);
-    d.sh_m[s] = __ldg(&op->sh_m[s]);
+    d.sh_d[s] = op->sh_d[s];
+    d.sh_m[s] = op->sh_m[s];
   }
-  const int ncut = __ldg(&op->ncut);
-  const int half = __ldg(&op->half);
+  const int ncut = op->ncut;
+  const int half = op->half;
   d.pmask = d.pval = d.zmask = 0;
   for (int i = 0; i < ncut; ++i) {
     const uint32_t qb = 1u << op->cutq[i];
@@ -183,10 +193,18 @@ __device__ __forceinline__ uint32_t swz_thread(const RegArgs& a, uint32_t t) {
 template <int R>
 __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArgs a) {
   constexpr int NE = 1 << R;
-  extern __shared__ float2 xs[];  // 2^k slots: transposes and warp-rank gates
+  extern __shared__ float2 xs[];  // 2^k slots (transposes, warp-rank gates), then the ops
   __shared__ float2 s_omega[8];   // w^e, w = e^{i pi / 4}
   const int t = threadIdx.x;
   const int lane = t & 31;
+  // the pass's ops, read by every thread: one copy in shared memory per block
+  OpRec* s_ops = (OpRec*)((char*)xs + a.xs_bytes);
+  {
+    static_assert(sizeof(OpRec) % 8 == 0, "ops are copied in 8-byte words");
+    const int nw = a.op_count * (int)(sizeof(OpRec) / 8);
+    const uint2* g = (const uint2*)a.ops;
+    for (int i = t; i < nw; i += 256) ((uint2*)s_ops)[i] = __ldg(g + i);
+  }
   if (t < 8) {
     // w^t: (+-1, 0), (0, +-1) for even t; (+-1/sqrt2, +-1/sqrt2) for odd t
     const int quad = t >> 1;
@@ -235,40 +253,49 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
     for (int j = 0; j < NE; ++j) v[j] = src[st | sreg(j)];
   }
   // shared-memory slots: storage index s = t + 256 j sits at s ^ swz(s); the
-  // compute-order element (t, j) is storage index P(t) | P(j)
-  const uint32_t sslot_t = (uint32_t)t ^ swz_thread(a, (uint32_t)t);
-  auto sslot_j = [&](int j) {
+  // compute-order element (t, j) is storage index P(t) | P(j).  Byte offsets: the
+  // storage slot of (t, j) is (sb_t ^ zb(j)) + 2048 j (the swizzle touches only the
+  // low 4 slot bits, below the j bits), the compute slot cb_t ^ cb(j).
+  const uint32_t sb_t = ((uint32_t)t ^ swz_thread(a, (uint32_t)t)) << 3;
+  uint32_t zb_r[R > 0 ? R : 1], cb_r[R > 0 ? R : 1];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    zb_r[r] = (uint32_t)a.swz[8 + r] << 3;
+    cb_r[r] = ((1u << a.c2s[8 + r]) ^ a.cswz[8 + r]) << 3;
+  }
+  auto sbyte = [&](int j) {
     uint32_t z = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if ((j >> r) & 1) z ^= a.swz[8 + r];
-    return ((uint32_t)j << 8) ^ z;
+      if ((j >> r) & 1) z ^= zb_r[r];
+    return (sb_t ^ z) + ((uint32_t)j << 11);
   };
-  uint32_t cslot_t = 0;
+  uint32_t cb_t = 0;
 #pragma unroll
   for (int r = 0; r < 8; ++r)
-    if ((t >> r) & 1) cslot_t |= 1u << a.c2s[r];
+    if ((t >> r) & 1) cb_t |= 1u << a.c2s[r];
   {
     uint32_t z = 0;
 #pragma unroll
     for (int r = 0; r < 8; ++r)
       if ((t >> r) & 1) z ^= a.cswz[r];
-    cslot_t ^= z;
+    cb_t = (cb_t ^ z) << 3;
   }
-  auto cslot_j = [&](int j) {
-    uint32_t o = 0;
+  auto cbyte = [&](int j) {
+    uint32_t o = cb_t;
 #pragma unroll
     for (int r = 0; r < R; ++r)
-      if ((j >> r) & 1) o ^= (1u << a.c2s[8 + r]) ^ a.cswz[8 + r];
+      if ((j >> r) & 1) o ^= cb_r[r];
     return o;
   };
-  __syncthreads();  // s_omega
+  char* xsb = (char*)xs;
+  __syncthreads();  // s_omega, s_ops
   if (a.transpose) {
 #pragma unroll
-    for (int j = 0; j < NE; ++j) xs[sslot_t ^ sslot_j(j)] = v[j];
+    for (int j = 0; j < NE; ++j) *(float2*)(xsb + sbyte(j)) = v[j];
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NE; ++j) v[j] = xs[cslot_t ^ cslot_j(j)];
+    for (int j = 0; j < NE; ++j) v[j] = *(const float2*)(xsb + cbyte(j));
     __syncthreads();
   }
   // compute-order global index bits for the diagonal ops
@@ -280,10 +307,10 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
 #pragma unroll
   for (int r = 0; r < R; ++r) regmask |= 1u << a.cpos[8 + r];
   for (int o = 0; o < a.op_count; ++o) {
-    const OpRec* op = a.ops + o;
-    if (__ldg(&op->type) == OP_GATE) {
-      const int lq = __ldg(&op->lq);
-      const int kind = __ldg(&op->kind);
+    const OpRec* op = s_ops + o;
+    if (op->type == OP_GATE) {
+      const int lq = op->lq;
+      const int kind = op->kind;
       if (lq >= 8) {
         reg_gate<R>(v, lq - 8, kind);
       } else if (lq < 5) {
@@ -309,24 +336,23 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
       // exponent of w at x = xt | r(j): the thread part (T and CZ terms within xt)
       // once per op, the register part from the op's table, and the CZ pairs between
       // a register qubit and a thread or non-local qubit as 4 popc(j & B)
-      const uint32_t tmask = __ldg(&op->tmask);
-      const int nsh = __ldg(&op->nsh);
+      const uint32_t tmask = op->tmask;
+      const int nsh = op->nsh;
       int s2 = 0;
-#pragma unroll
-      for (int s = 0; s < kMaxShift; ++s)
-        if (s < nsh) s2 += __popc(xt & (xt >> __ldg(&op->sh_d[s])) & __ldg(&op->sh_m[s]));
-      int et = __popc(xt & tmask) + 4 * s2;
+#pragma unroll 1
+      for (int s = 0; s < nsh; ++s) s2 += __popc(xt & (xt >> op->sh_d[s]) & op->sh_m[s]);
+      int et = __popc(xt & tmask) + 4 * s2 + (o == a.phase_op ? a.phase_e : 0);
       uint32_t B = 0;
 #pragma unroll
       for (int r = 0; r < R; ++r) {
-        const uint32_t pq = __ldg(&op->pq[r]);
+        const uint32_t pq = op->pq[r];
         if (pq != 0xFFu && ((xt >> pq) & 1u)) B |= 1u << r;
       }
       // cut slots of this copy-tree node: Z^l signs (lower half), P_l projectors
       // (upper half) split the same way
       bool proj = false, keep_t = true;
       uint32_t pm_r = 0, pv_r = 0;
-      if (__ldg(&op->ncut)) {
+      if (op->ncut) {
         Diag d;
         load_diag(op, ne.node_id, d);
         et += 4 * __popc(xt & d.zmask);
@@ -344,42 +370,87 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
           keep_t = (xt & d.pmask & ~regmask) == (d.pval & ~regmask);
         }
       }
+      // Exponents of 8 elements at a time, one 4-bit field per element (element
+      // 8w + i in field i of word w): the register-part table plus et in every
+      // field (each field stays below 15, so no carries), then the cross-CZ sign
+      // 4 popc(B & j) mod 8 as an XOR of 4 into the fields with odd parity of
+      // B & j.  kPar[r]: the fields i (of 0..7) whose bit r is set.
+      constexpr uint32_t kPar[3] = {0x40404040u, 0x44004400u, 0x44440000u};
+      uint32_t par0 = 0;
+#pragma unroll
+      for (int r = 0; r < 3 && r < R; ++r)
+        if ((B >> r) & 1u) par0 ^= kPar[r];
+      const uint32_t et8 = (uint32_t)(et & 7) * 0x11111111u;
       uint32_t ew[4];
 #pragma unroll
-      for (int w4 = 0; w4 < 4; ++w4) ew[w4] = (w4 * 8 < NE) ? __ldg(&op->ereg[w4]) : 0u;
+      for (int w4 = 0; w4 < 4; ++w4) {
+        if (w4 * 8 < NE) {
+          const uint32_t hi = (uint32_t)__popc(B & (uint32_t)(w4 << 3)) & 1u;
+          ew[w4] = (op->ereg[w4] + et8) ^ par0 ^ (hi ? 0x44444444u : 0u);
+        } else {
+          ew[w4] = 0u;
+        }
+      }
+      // projector: the elements j with (j & pm_r) == pv_r, as a bit mask over j
+      uint32_t kmask = 0xFFFFFFFFu;
+      if (proj) {
+        constexpr uint32_t kJ[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
 #pragma unroll
-      for (int j = 0; j < NE; ++j) {
-        const int e = (et + (int)((ew[j >> 3] >> (4 * (j & 7))) & 7u) + 4 * __popc(B & (uint32_t)j)) & 7;
-        v[j] = cmul(v[j], s_omega[e]);
-        if (proj && !(keep_t && (((uint32_t)j & pm_r) == pv_r))) v[j] = make_float2(0.f, 0.f);
+        for (int r = 0; r < R; ++r)
+          if ((pm_r >> r) & 1u) kmask &= ((pv_r >> r) & 1u) ? kJ[r] : ~kJ[r];
+        if (!keep_t) kmask = 0u;
+      }
+      // field i of a word, as the byte offset 8 e of w^e in s_omega
+      auto omega_at = [&](int j) {
+        const uint32_t w = ew[j >> 3];
+        const int i = j & 7;
+        const uint32_t off = (i == 0 ? (w << 3) : (w >> (4 * i - 3))) & 0x38u;
+        return *(const float2*)((const char*)s_omega + off);
+      };
+      if (proj) {
+#pragma unroll
+        for (int j = 0; j < NE; ++j) {
+          v[j] = cmul(v[j], omega_at(j));
+          if (!((kmask >> j) & 1u)) v[j] = make_float2(0.f, 0.f);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NE; ++j) v[j] = cmul(v[j], omega_at(j));
       }
     }
   }
   if (a.transpose) {
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NE; ++j) xs[cslot_t ^ cslot_j(j)] = v[j];
+    for (int j = 0; j < NE; ++j) *(float2*)(xsb + cbyte(j)) = v[j];
     __syncthreads();
 #pragma unroll
-    for (int j = 0; j < NE; ++j) v[j] = xs[sslot_t ^ sslot_j(j)];
+    for (int j = 0; j < NE; ++j) v[j] = *(const float2*)(xsb + sbyte(j));
+  }
+  if (a.phase_op < 0 && a.phase_e != 0) {
+    const float2 w = s_omega[a.phase_e & 7];
+#pragma unroll
+    for (int j = 0; j < NE; ++j) v[j] = cmul(v[j], w);
   }
 #pragma unroll
-  for (int j = 0; j < NE; ++j) dst[st | sreg(j)] = make_float2(v[j].x * a.scale, v[j].y * a.scale);
+  for (int j = 0; j < NE; ++j) dst[st | sreg(j)] = __fmul2_rn(v[j], make_float2(a.scale, a.scale));
 }
 
 template <int R>
 cudaError_t launch_r(const RegArgs& a, int64_t nslots, int use_smem, cudaStream_t s) {
-  const size_t smem = use_smem ? (sizeof(float2) << (8 + R)) : 0;
+  const uint32_t xs_bytes = use_smem ? (uint32_t)(sizeof(float2) << (8 + R)) : 0u;
+  const size_t smem = xs_bytes + (size_t)a.op_count * sizeof(OpRec);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(sweep_reg_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float2) << (8 + R)));
+                                         (int)((sizeof(float2) << (8 + R)) + kMaxPassOps * sizeof(OpRec)));
     if (e != cudaSuccess) return e;
     attr = true;
   }
   const uint64_t bps = 1ull << (a.n - a.k);
   const int64_t max_slots = (int64_t)((1ull << 30) / bps) > 0 ? (int64_t)((1ull << 30) / bps) : 1;
   RegArgs b = a;
+  b.xs_bytes = xs_bytes;
   for (int64_t s0 = 0; s0 < nslots; s0 += max_slots) {
     const int64_t ns = (nslots - s0) < max_slots ? (nslots - s0) : max_slots;
     b.slot_begin = s0;
@@ -394,7 +465,7 @@ cudaError_t launch_r(const RegArgs& a, int64_t nslots, int use_smem, cudaStream_
 }  // namespace
 
 bool sweep2_supported(const SweepLaunch& L) {
-  return L.k >= 8 && L.k <= 13 && L.low == 5 && L.n >= L.k && !L.general_gates;
+  return L.k >= 8 && L.k <= 13 && L.low == 5 && L.n >= L.k && !L.general_gates && L.op_count <= kMaxPassOps;
 }
 
 cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s) {
@@ -440,6 +511,8 @@ cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s) {
   if (nn != L.n - L.k) return cudaErrorInvalidValue;
   a.init_val = (float)ldexp(1.0, -(L.n / 2)) * ((L.n & 1) ? 0.70710678118654752f : 1.f);
   a.scale = L.scale;
+  a.phase_e = L.phase_e & 7;
+  a.phase_op = L.phase_op < L.op_count ? L.phase_op : -1;
   a.transpose = L.transpose;
   const int use_smem = L.warp_gates > 0 || L.transpose;
   switch (L.k - 8) {
