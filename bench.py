@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--sweep-fuse", type=int, default=0, help="fuse width k of the sweep measurement (0: library default)")
     ap.add_argument("--sweep-cols", type=int, default=10,
                     help="columns of the 6-row sweep grid (10: two 30-qubit halves)")
+    ap.add_argument("--no-q42", action="store_true", help="skip the 42-qubit (6x7, depth 22, c=14) measurement")
+    ap.add_argument("--q64", type=int, default=0, metavar="LEAVES",
+                    help="also time the 64-qubit circuit (8x8, depth 22, c=16) on LEAVES seeded copies and "
+                         "extrapolate to all 65536 with Eq. (2)")
+    ap.add_argument("--q-only", action="store_true", help="profiling case: only the 42/64-qubit measurements")
     ap.add_argument("--select", type=int, default=0,
                     help="profiling case: contract only the first S upper x S lower indices (S*S amplitudes)")
     return ap.parse_args()
@@ -244,6 +249,99 @@ def sweep_hbm(sim, torch, stream, reps=3, cols=10, fuse=0):
     return info
 
 
+def timed_selection_run(sim, torch, stream, plan, copies, su, sl, out):
+    """One evolve (range of all copies, or a list) + split-bf16 contraction with the
+    fused statistics, timed with CUDA events on the stream; returns (ms, phases, stats)."""
+    sim.sim_profile_read(reset=True)
+    sim.sim_profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    if isinstance(copies, int):
+        h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, copies, su, sl, stream=stream)
+    else:
+        h = sim.sim_evolve_halves_list(plan, sim.SIM_C64, copies, su, sl, stream=stream)
+    st = sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_BF16, False, out, stream=stream)
+    e1.record(stream)
+    sim.sim_status(stream)
+    sim.sim_profile_enable(False)
+    prof = sim.sim_profile_read(reset=True)
+    sim.sim_destroy_halves(h)
+    phases = {sim.PHASE_NAMES[i]: round(prof["ms"][i], 3) for i in range(sim.SIM_NUM_PHASES) if prof["launches"][i]}
+    return e0.elapsed_time(e1), phases, [float(x) for x in st], prof
+
+
+def run_q42(sim, torch, stream):
+    """6x7 grid, depth 22, cut between rows 2 and 3: c = 14, 16384 copies of two
+    21-qubit halves, all copies through the contraction, 2^14 x 2^14 selection."""
+    R, C, D, B = 6, 7, 22, 3
+    circ = sim.sim_build_circuit(R, C, D, 0, B)
+    plan, c, copies, nu, nl = sim.sim_cut(circ, B)
+    su, sl = sim.sim_select(nu, 1 << 14, nl, 1 << 14, 0)
+    out = torch.empty((sl.size, su.size), dtype=torch.complex64, device="cuda")
+    timed_selection_run(sim, torch, stream, plan, copies, su, sl, out)   # warm-up
+    ms, phases, st, _ = timed_selection_run(sim, torch, stream, plan, copies, su, sl, out)
+    res = {"workload": "42-qubit 6x7 grid random circuit, depth 22, seed 0, cut between rows 2 and 3: "
+                       "c=14, 16384 copies of two 21-qubit halves; 2^14 x 2^14 selected amplitudes",
+           "copies": copies, "amplitudes": int(su.size * sl.size), "ms": ms,
+           "amplitudes_per_s": su.size * sl.size / (ms / 1e3), "phases_ms": phases,
+           "stats": st, "note": "evolve + contraction with fused statistics, CUDA events on the stream; "
+                                "c=14, not the c=12 of the configuration text (no straight cut of 6x7 gives "
+                                "c=12 with equal halves)"}
+    del out
+    sim.sim_destroy_cut(plan)
+    sim.sim_destroy_circuit(circ)
+    sim.sim_release_cache()
+    return res
+
+
+def run_q64(sim, torch, stream, leaves, contraction_tflops):
+    """8x8 grid, depth 22, cut between rows 3 and 4: c = 16, 65536 copies of two
+    32-qubit halves.  A seeded list of copies (splitmix64(0)) is evolved with prefix
+    sharing; the measured time per fused pass extrapolates to all copies by Eq. (2):
+    Time = sum over levels of (passes of the level) x (nodes of the level) x t."""
+    import numpy as np
+    R, C, D, B = 8, 8, 22, 4
+    circ = sim.sim_build_circuit(R, C, D, 0, B)
+    plan, c, copies, nu, nl = sim.sim_cut(circ, B)
+    lst, _ = sim.sim_select(c, leaves, 1, 1, 0)
+    su, sl = sim.sim_select(nu, 1 << 14, nl, 1 << 14, 0)
+    out = torch.empty((sl.size, su.size), dtype=torch.complex64, device="cuda")
+    timed_selection_run(sim, torch, stream, plan, lst[:1], su, sl, out)   # warm-up: one copy
+    ms, phases, st, prof = timed_selection_run(sim, torch, stream, plan, lst, su, sl, out)
+    run_passes, full_passes, levels = 0, 0, []
+    for half in (0, 1):
+        for (layer, b0, b1, npass) in sim.sim_plan_levels(plan, half):
+            nodes = len(np.unique(lst & np.uint64((1 << int(b1)) - 1)))
+            run_passes += nodes * int(npass)
+            full_passes += (1 << int(b1)) * int(npass)
+            levels.append([half, int(layer), int(b1), int(npass), nodes])
+    sweep_ms = prof["ms"][sim.SIM_PHASE_SWEEP]
+    t_pass = sweep_ms / run_passes
+    gather_pack_ms = sum(prof["ms"][i] for i in (sim.SIM_PHASE_GATHER, sim.SIM_PHASE_PACK))
+    flops_full = 24.0 * su.size * sl.size * copies
+    est = {"sweep_s": full_passes * t_pass / 1e3,
+           "gather_pack_s": gather_pack_ms / leaves * copies / 1e3,
+           "contraction_s": flops_full / (contraction_tflops * 1e12) if contraction_tflops else None}
+    total = sum(v for v in est.values() if v)
+    res = {"workload": "64-qubit 8x8 grid random circuit, depth 22, seed 0, cut between rows 3 and 4: c=16, "
+                       "65536 copies of two 32-qubit halves (32 GB complex64 each); 2^14 x 2^14 selected amplitudes",
+           "leaves_run": leaves, "leaf_sample": "splitmix64(0), distinct copy indices (Floyd)",
+           "ms": ms, "phases_ms": phases, "stats_of_sample": st,
+           "fused_passes_run": run_passes, "ms_per_fused_pass": t_pass,
+           "levels": {"columns": ["half", "branch_layer", "copy_bits_after", "passes", "nodes_run"], "rows": levels},
+           "eq2_full_run": {"fused_passes": full_passes, **est, "total_s": total,
+                            "amplitudes_per_s": su.size * sl.size / total,
+                            "note": "Eq. (2) with n_i = fused passes per level, m = nodes per level (all copies), "
+                                    "t = measured ms per fused pass on 32-qubit states; contraction at the "
+                                    "30-qubit bench's measured tensor rate"}}
+    del out
+    sim.sim_destroy_cut(plan)
+    sim.sim_destroy_circuit(circ)
+    sim.sim_release_cache()
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -265,6 +363,13 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps(sweep_hbm(sim, torch, stream, reps=1, cols=args.sweep_cols, fuse=args.sweep_fuse)),
                   flush=True)
+        return
+    if args.q_only:
+        if rank == 0:
+            res = {} if args.no_q42 else {"q42": run_q42(sim, torch, stream)}
+            if args.q64:
+                res["q64"] = run_q64(sim, torch, stream, args.q64, None)
+            print(json.dumps(res), flush=True)
         return
     out = torch.empty((S, S), dtype=torch.complex64, device="cuda")
 
@@ -364,6 +469,10 @@ def run_ours(args):
 
     if not args.no_sweep:
         line["sweep_hbm"] = sweep_hbm(sim, torch, stream)
+    if rank == 0 and not args.no_q42 and args.select == 0:
+        line["q42"] = run_q42(sim, torch, stream)
+    if rank == 0 and args.q64 and args.select == 0:
+        line["q64"] = run_q64(sim, torch, stream, args.q64, achieved)
 
     # end to end through the C-ABI with a host output buffer
     if not args.no_e2e:

@@ -129,6 +129,15 @@ int sim_cut_list(sim_cut_plan plan, int32_t* cuts_out, int* n_equiv_out);
  * number of copy-tree levels, number of fused passes summed over levels, and the
  * number of plain passes the Section 2.4 scheme would need for one copy (one per
  * non-diagonal gate plus one per layer holding diagonal gates).  Host only. */
+/* Per copy-tree level of one half (0 upper, 1 lower): four int32 values
+ * {branch layer (-1 for the root), copy bits fixed before the level, copy bits
+ * fixed after it, fused passes of the level}.  A level is run once per distinct
+ * value of its fixed copy bits among the evolved copies (Section 2.3.2), so the
+ * work of any copy set follows from this table (Eq. (2) with n_i the passes of a
+ * level and m its node count).  Writes at most cap levels; *n_levels receives the
+ * number of levels.  Host only. */
+int sim_plan_levels(sim_cut_plan plan, int half, int32_t* out, int cap, int* n_levels);
+
 int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passes,
                       int* plain_passes);
 
@@ -147,8 +156,22 @@ int sim_evolve_halves(sim_cut_plan plan, int precision, uint64_t copy_begin,
                       const uint64_t* sel_l, uint64_t n_l, const sim_opts* opts,
                       void* stream, sim_halves* out);
 
+/* sim_evolve_halves for an explicit list of copies instead of a range: the copy
+ * tree is built over the listed copies only, so copies whose cut bits share a
+ * prefix share the evolution of that prefix (Section 2.3.2).  The paper evaluates
+ * the partitions independently (Supplementary B); a list lets a caller time a
+ * seeded sample of them and extrapolate with Eq. (2).
+ *   copies, n_copies  host array of n_copies distinct copy indices < 2^c, in the
+ *                     order of the leaf rows (sim_amplitudes sums over all of them)
+ * SIM_EINVAL for an empty list, an index >= 2^c or a repeated index; otherwise as
+ * sim_evolve_halves. */
+int sim_evolve_halves_list(sim_cut_plan plan, int precision, const uint64_t* copies,
+                           uint64_t n_copies, const uint64_t* sel_u, uint64_t n_u,
+                           const uint64_t* sel_l, uint64_t n_l, const sim_opts* opts,
+                           void* stream, sim_halves* out);
+
 /* Copy the selected entries of one leaf half-state (half 0 upper, 1 lower) of copy
- * `copy` (absolute copy index inside the evolved range) into out_dev, a device
+ * `copy` (an absolute copy index among the evolved copies) into out_dev, a device
  * buffer of n_sel elements of the halves' precision (complex64 or complex128). */
 int sim_halves_leaf(sim_halves h, int half, uint64_t copy, void* out_dev, void* stream);
 

@@ -32,6 +32,7 @@ EXPORTS = (
     "sim_select", "sim_sample", "sim_status", "sim_release_cache", "sim_destroy_circuit",
     "sim_destroy_cut", "sim_destroy_halves", "sim_last_error", "sim_version",
     "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc", "sim_amplitudes_stats",
+    "sim_evolve_halves_list", "sim_plan_levels",
 )
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -73,8 +74,11 @@ def lib():
         "sim_cut": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ip, u64p, ip, ip]),
         "sim_cut_list": (ctypes.c_int, [vp, i32p, ip]),
         "sim_plan_schedule": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ip]),
+        "sim_plan_levels": (ctypes.c_int, [vp, ctypes.c_int, i32p, ctypes.c_int, ip]),
         "sim_evolve_halves": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u64p, u64, u64p, u64,
                                              ctypes.POINTER(SimOpts), vp, ctypes.POINTER(vp)]),
+        "sim_evolve_halves_list": (ctypes.c_int, [vp, ctypes.c_int, u64p, u64, u64p, u64, u64p, u64,
+                                                  ctypes.POINTER(SimOpts), vp, ctypes.POINTER(vp)]),
         "sim_halves_leaf": (ctypes.c_int, [vp, ctypes.c_int, u64, vp, vp]),
         "sim_amplitudes": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
         "sim_stats": (ctypes.c_int, [vp, ctypes.c_int, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
@@ -186,6 +190,17 @@ def sim_plan_schedule(plan, half):
     return a.value, b.value, c.value
 
 
+def sim_plan_levels(plan, half):
+    """Copy-tree levels of one half: array of rows (branch layer, copy bits before,
+    copy bits after, fused passes)."""
+    n = ctypes.c_int()
+    _check(lib().sim_plan_levels(plan, half, None, 0, ctypes.byref(n)))
+    out = np.zeros(4 * n.value, dtype=np.int32)
+    _check(lib().sim_plan_levels(plan, half, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n.value,
+                                 ctypes.byref(n)))
+    return out.reshape(-1, 4)
+
+
 def sim_evolve_halves(plan, precision, copy_begin, copy_end, sel_u=None, sel_l=None, opts=None, stream=None):
     su, nu = _u64(sel_u)
     sl, nl = _u64(sel_l)
@@ -195,6 +210,21 @@ def sim_evolve_halves(plan, precision, copy_begin, copy_end, sel_u=None, sel_l=N
                                    su.ctypes.data_as(P) if su is not None else None, nu,
                                    sl.ctypes.data_as(P) if sl is not None else None, nl,
                                    _opts(opts), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sim_evolve_halves_list(plan, precision, copies, sel_u=None, sel_l=None, opts=None, stream=None):
+    """sim_evolve_halves over an explicit list of distinct copy indices (leaf rows in
+    list order)."""
+    cp, ncp = _u64(copies)
+    su, nu = _u64(sel_u)
+    sl, nl = _u64(sel_l)
+    P = ctypes.POINTER(ctypes.c_uint64)
+    h = ctypes.c_void_p()
+    _check(lib().sim_evolve_halves_list(plan, precision, cp.ctypes.data_as(P) if cp is not None else None, ncp,
+                                        su.ctypes.data_as(P) if su is not None else None, nu,
+                                        sl.ctypes.data_as(P) if sl is not None else None, nl,
+                                        _opts(opts), _stream(stream), ctypes.byref(h)))
     return h.value
 
 

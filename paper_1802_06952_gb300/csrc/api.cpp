@@ -26,10 +26,22 @@ struct sim_cut_s {
   CutPlan p;
 };
 
+// The copies of an evolved halves object, in leaf-row order: the range [kb, ke) or
+// an explicit list of distinct copy indices.
+struct CopySet {
+  uint64_t kb = 0, ke = 0;
+  std::vector<uint64_t> list;                 // empty: the range
+  std::unordered_map<uint64_t, int64_t> row;  // list: copy index -> row
+  uint64_t size() const { return list.empty() ? ke - kb : (uint64_t)list.size(); }
+  uint64_t at(uint64_t i) const { return list.empty() ? kb + i : list[i]; }
+  bool contains(uint64_t k) const { return list.empty() ? (k >= kb && k < ke) : row.count(k) > 0; }
+  int64_t row_of(uint64_t k) const { return list.empty() ? (int64_t)(k - kb) : row.at(k); }
+};
+
 struct sim_halves_s {
   CutPlan* plan = nullptr;
   int precision = SIM_C64;
-  uint64_t kb = 0, ke = 0;
+  CopySet cs;
   int64_t nsel[2] = {0, 0};
   bool full[2] = {true, true};
   void* d_sel[2] = {nullptr, nullptr};
@@ -297,21 +309,23 @@ struct TreeProgram {
 
 struct TreeBuilder {
   const HalfSchedule& S;
-  uint64_t kb, ke;
+  const CopySet& cs;
   bool direct;            // leaves written straight into leafsel rows (no selection)
   std::vector<std::vector<uint64_t>> needed;  // sorted node ids per level
   TreeProgram& prog;
 
+  // node ids of level j on the paths to the copies: the low bits_total bits of each
   std::vector<uint64_t> needed_ids(int j) const {
     const int bits = S.levels[j].bits_total;
     std::vector<uint64_t> ids;
     const uint64_t count = bits >= 63 ? ~0ull : (1ull << bits);
-    if (ke - kb >= count) {
+    const uint64_t K = cs.size();
+    if (cs.list.empty() && K >= count) {
       ids.resize(count);
       for (uint64_t i = 0; i < count; ++i) ids[i] = i;
     } else {
-      ids.reserve(ke - kb);
-      for (uint64_t k = kb; k < ke; ++k) ids.push_back(k & (count - 1));
+      ids.reserve(K);
+      for (uint64_t i = 0; i < K; ++i) ids.push_back(cs.at(i) & (count - 1));
       std::sort(ids.begin(), ids.end());
       ids.erase(std::unique(ids.begin(), ids.end()), ids.end());
     }
@@ -344,7 +358,7 @@ struct TreeBuilder {
           const uint64_t pmask = L.bits_before >= 63 ? ~0ull : ((1ull << L.bits_before) - 1);
           e.parent_slot = parent_slot.at(ids[i] & pmask);
         }
-        e.dst_row = (leaf && direct) ? (int64_t)(ids[i] - kb) : (int64_t)(i - c0);
+        e.dst_row = (leaf && direct) ? cs.row_of(ids[i]) : (int64_t)(i - c0);
         prog.table.push_back(e);
         my_slot[ids[i]] = (int64_t)(i - c0);
       }
@@ -368,7 +382,7 @@ struct TreeBuilder {
             NodeEntry e;
             e.node_id = ids[i];
             e.parent_slot = 0;
-            e.dst_row = (int64_t)(ids[i] - kb);
+            e.dst_row = cs.row_of(ids[i]);
             prog.table.push_back(e);
           }
           LaunchRec r;
@@ -397,7 +411,7 @@ struct TreeBuilder {
   }
 };
 
-int evolve_c64_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t* d_sel, int64_t nsel, bool full,
+int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel, int64_t nsel, bool full,
                     void* leafsel, cudaStream_t st, const sim_opts* opts) {
   const HalfSchedule& S = P.sched[h];
   const int n = S.n;
@@ -410,12 +424,12 @@ int evolve_c64_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t*
   const size_t budget = (size_t)(fr * 0.6);
   for (int j = 0; j < J; ++j) {
     const int64_t need_nodes = (int64_t)std::min<uint64_t>(
-        ke - kb, S.levels[j].bits_total >= 63 ? ~0ull : (1ull << S.levels[j].bits_total));
+        cs.size(), S.levels[j].bits_total >= 63 ? ~0ull : (1ull << S.levels[j].bits_total));
     int64_t cap = (int64_t)(budget / std::max(1, J) / state_bytes);
     if (cap < 1) cap = 1;
     prog.level_cap.push_back(std::min<int64_t>(cap, std::max<int64_t>(need_nodes, 1)));
   }
-  TreeBuilder tb{S, kb, ke, full, {}, prog};
+  TreeBuilder tb{S, cs, full, {}, prog};
   tb.build();
   // buffers
   std::vector<DevBuf> lvl(J);
@@ -474,13 +488,13 @@ int evolve_c64_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t*
 // complex128 plain path of one half: every copy evolved on its own, one pass per
 // non-diagonal gate and one combined diagonal pass per layer (Sections 2.3.1, 2.4)
 // ---------------------------------------------------------------------------
-int evolve_plain_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_t* d_sel, int64_t nsel, bool full,
+int evolve_plain_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel, int64_t nsel, bool full,
                       void* leafsel, cudaStream_t st) {
   const int n = h ? P.n_l : P.n_u;
   const size_t state_bytes = sizeof(double) * 2 * ((size_t)1 << n);
   size_t fr = 0, tot = 0;
   CK(cudaMemGetInfo(&fr, &tot));
-  const uint64_t K = ke - kb;
+  const uint64_t K = cs.size();
   uint64_t cap = (uint64_t)(fr * 0.5 / state_bytes);
   if (cap < 1) cap = 1;
   const uint64_t batch = std::min(K, cap);
@@ -491,18 +505,19 @@ int evolve_plain_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_
   std::vector<uint64_t> hid(batch);
   std::vector<NodeEntry> htab(batch);
   PhaseScope ps(SIM_PHASE_PLAIN, st);
-  for (uint64_t k0 = kb; k0 < ke; k0 += batch) {
-    const uint64_t nb = std::min(batch, ke - k0);
+  // copies in row order, `batch` at a time (row r = position in the copy set)
+  for (uint64_t k0 = 0; k0 < K; k0 += batch) {
+    const uint64_t nb = std::min(batch, K - k0);
     for (uint64_t i = 0; i < nb; ++i) {
-      hid[i] = k0 + i;
-      htab[i].node_id = k0 + i;
+      hid[i] = cs.at(k0 + i);
+      htab[i].node_id = hid[i];
       htab[i].parent_slot = 0;
-      htab[i].dst_row = (int64_t)(k0 + i - kb);
+      htab[i].dst_row = (int64_t)(k0 + i);
     }
     CK(cudaMemcpyAsync(ids.p, hid.data(), sizeof(uint64_t) * nb, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(table.p, htab.data(), sizeof(NodeEntry) * nb, cudaMemcpyHostToDevice, st));
     note_bytes((sizeof(uint64_t) + sizeof(NodeEntry)) * nb, 0);
-    void* psi = full ? (void*)((char*)leafsel + (k0 - kb) * state_bytes) : work.p;
+    void* psi = full ? (void*)((char*)leafsel + k0 * state_bytes) : work.p;
     CK(launch_plain_init_zero(psi, n, (int64_t)nb, st));
     for (size_t t = 0; t < P.plain[h].size(); ++t) {
       const PlainLayer& L = P.plain[h][t];
@@ -517,7 +532,7 @@ int evolve_plain_half(CutPlan& P, int h, uint64_t kb, uint64_t ke, const uint64_
       }
     }
     if (!full) CK(launch_gather(work.p, n, table.as<NodeEntry>(), (int64_t)nb, d_sel, nsel, leafsel, 1, st));
-    if (k0 + batch < ke) CK(cudaStreamSynchronize(st));  // host arrays are reused
+    if (k0 + batch < K) CK(cudaStreamSynchronize(st));  // host arrays are reused
   }
   CK(cudaStreamSynchronize(st));
   return SIM_OK;
@@ -553,7 +568,7 @@ int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cu
   int rc = device_info(&di);
   if (rc) return rc;
   const int64_t M = h->nsel[1], N = h->nsel[0];
-  const int64_t K = (int64_t)(h->ke - h->kb);
+  const int64_t K = (int64_t)h->cs.size();
   const int nq = h->plan->circ.n;
   if (contraction == SIM_FP64_PLAIN) {
     {
@@ -636,8 +651,7 @@ namespace sim {
 bool halves_view(const sim_halves_s* h, HalvesView* v) {
   if (!h || !v) return false;
   v->precision = h->precision;
-  v->kb = h->kb;
-  v->ke = h->ke;
+  v->K = h->cs.size();
   for (int i = 0; i < 2; ++i) {
     v->nsel[i] = h->nsel[i];
     v->leafsel[i] = h->leafsel[i];
@@ -761,6 +775,21 @@ int sim_cut_list(sim_cut_plan plan, int32_t* cuts_out, int* n_equiv_out) {
   return SIM_OK;
 }
 
+int sim_plan_levels(sim_cut_plan plan, int half, int32_t* out, int cap, int* n_levels) {
+  if (!plan || half < 0 || half > 1 || cap < 0 || (cap > 0 && !out)) return fail(SIM_EINVAL, "bad arguments");
+  const HalfSchedule& S = plan->p.sched[half];
+  const int J = (int)S.levels.size();
+  for (int j = 0; j < J && j < cap; ++j) {
+    const Level& L = S.levels[j];
+    out[4 * j + 0] = L.branch_layer;
+    out[4 * j + 1] = L.bits_before;
+    out[4 * j + 2] = L.bits_total;
+    out[4 * j + 3] = (int32_t)L.passes.size();
+  }
+  if (n_levels) *n_levels = J;
+  return SIM_OK;
+}
+
 int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passes, int* plain_passes) {
   if (!plan || half < 0 || half > 1) return fail(SIM_EINVAL, "bad plan or half");
   const HalfSchedule& S = plan->p.sched[half];
@@ -772,16 +801,13 @@ int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passe
   return SIM_OK;
 }
 
-int sim_evolve_halves(sim_cut_plan plan, int precision, uint64_t copy_begin, uint64_t copy_end, const uint64_t* sel_u,
-                      uint64_t n_u, const uint64_t* sel_l, uint64_t n_l, const sim_opts* opts, void* stream,
-                      sim_halves* out) {
-  API_BEGIN
-  if (!plan || !out) return fail(SIM_EINVAL, "plan and out must not be NULL");
-  *out = nullptr;
+namespace {
+
+// sim_evolve_halves and sim_evolve_halves_list: evolve the copies of `cs` (already
+// validated against 2^c) for both halves and gather their leaves.
+int evolve_halves_impl(sim_cut_plan plan, int precision, CopySet&& cs, const uint64_t* sel_u, uint64_t n_u,
+                       const uint64_t* sel_l, uint64_t n_l, const sim_opts* opts, void* stream, sim_halves* out) {
   CutPlan& P = plan->p;
-  if (precision != SIM_C64 && precision != SIM_C128_PLAIN) return fail(SIM_EINVAL, "unknown precision");
-  const uint64_t copies = 1ull << P.c;
-  if (copy_begin >= copy_end || copy_end > copies) return fail(SIM_EINVAL, "copy range must satisfy begin < end <= 2^c");
   if (opts && opts->fuse_qubits && opts->fuse_qubits != P.fuse_qubits) {
     CutPlan np;
     std::string err = build_cut_plan(P.circ, P.circ.cut_row ? (P.n_u / P.circ.C) : 0, opts->fuse_qubits, np);
@@ -807,11 +833,10 @@ int sim_evolve_halves(sim_cut_plan plan, int precision, uint64_t copy_begin, uin
   auto* h = new sim_halves_s();
   h->plan = &P;
   h->precision = precision;
-  h->kb = copy_begin;
-  h->ke = copy_end;
+  h->cs = std::move(cs);
   h->stream = st;
   CK(cudaGetDevice(&h->device));
-  const uint64_t K = copy_end - copy_begin;
+  const uint64_t K = h->cs.size();
   const size_t esz = precision == SIM_C64 ? 8 : 16;
   auto cleanup = [&]() { sim_destroy_halves(h); };
   for (int hh = 0; hh < 2; ++hh) {
@@ -837,10 +862,10 @@ int sim_evolve_halves(sim_cut_plan plan, int precision, uint64_t copy_begin, uin
   }
   for (int hh = 0; hh < 2; ++hh) {
     int r = precision == SIM_C64
-                ? evolve_c64_half(P, hh, copy_begin, copy_end, (const uint64_t*)h->d_sel[hh], h->nsel[hh],
-                                  h->full[hh], h->leafsel[hh], st, opts)
-                : evolve_plain_half(P, hh, copy_begin, copy_end, (const uint64_t*)h->d_sel[hh], h->nsel[hh],
-                                    h->full[hh], h->leafsel[hh], st);
+                ? evolve_c64_half(P, hh, h->cs, (const uint64_t*)h->d_sel[hh], h->nsel[hh], h->full[hh],
+                                  h->leafsel[hh], st, opts)
+                : evolve_plain_half(P, hh, h->cs, (const uint64_t*)h->d_sel[hh], h->nsel[hh], h->full[hh],
+                                    h->leafsel[hh], st);
     if (r) {
       std::string keep = g_err;
       cleanup();
@@ -849,17 +874,54 @@ int sim_evolve_halves(sim_cut_plan plan, int precision, uint64_t copy_begin, uin
   }
   *out = h;
   return SIM_OK;
+}
+
+}  // namespace
+
+int sim_evolve_halves(sim_cut_plan plan, int precision, uint64_t copy_begin, uint64_t copy_end, const uint64_t* sel_u,
+                      uint64_t n_u, const uint64_t* sel_l, uint64_t n_l, const sim_opts* opts, void* stream,
+                      sim_halves* out) {
+  API_BEGIN
+  if (!plan || !out) return fail(SIM_EINVAL, "plan and out must not be NULL");
+  *out = nullptr;
+  if (precision != SIM_C64 && precision != SIM_C128_PLAIN) return fail(SIM_EINVAL, "unknown precision");
+  const uint64_t copies = 1ull << plan->p.c;
+  if (copy_begin >= copy_end || copy_end > copies) return fail(SIM_EINVAL, "copy range must satisfy begin < end <= 2^c");
+  CopySet cs;
+  cs.kb = copy_begin;
+  cs.ke = copy_end;
+  return evolve_halves_impl(plan, precision, std::move(cs), sel_u, n_u, sel_l, n_l, opts, stream, out);
+  API_END
+}
+
+int sim_evolve_halves_list(sim_cut_plan plan, int precision, const uint64_t* copies, uint64_t n_copies,
+                           const uint64_t* sel_u, uint64_t n_u, const uint64_t* sel_l, uint64_t n_l,
+                           const sim_opts* opts, void* stream, sim_halves* out) {
+  API_BEGIN
+  if (!plan || !out || !copies) return fail(SIM_EINVAL, "plan, copies and out must not be NULL");
+  *out = nullptr;
+  if (precision != SIM_C64 && precision != SIM_C128_PLAIN) return fail(SIM_EINVAL, "unknown precision");
+  if (n_copies == 0) return fail(SIM_EINVAL, "empty copy list");
+  const uint64_t total = 1ull << plan->p.c;
+  CopySet cs;
+  cs.list.assign(copies, copies + n_copies);
+  cs.row.reserve((size_t)n_copies);
+  for (uint64_t i = 0; i < n_copies; ++i) {
+    if (cs.list[i] >= total) return fail(SIM_EINVAL, "copy index out of range (must be < 2^c)");
+    if (!cs.row.emplace(cs.list[i], (int64_t)i).second) return fail(SIM_EINVAL, "copy indices must be distinct");
+  }
+  return evolve_halves_impl(plan, precision, std::move(cs), sel_u, n_u, sel_l, n_l, opts, stream, out);
   API_END
 }
 
 int sim_halves_leaf(sim_halves h, int half, uint64_t copy, void* out_dev, void* stream) {
   API_BEGIN
   if (!h || half < 0 || half > 1 || !out_dev) return fail(SIM_EINVAL, "bad arguments");
-  if (copy < h->kb || copy >= h->ke) return fail(SIM_EINVAL, "copy outside the evolved range");
+  if (!h->cs.contains(copy)) return fail(SIM_EINVAL, "copy not among the evolved copies");
   const size_t esz = h->precision == SIM_C64 ? 8 : 16;
   const size_t bytes = esz * (size_t)h->nsel[half];
-  CK(cudaMemcpyAsync(out_dev, (const char*)h->leafsel[half] + (copy - h->kb) * bytes, bytes, cudaMemcpyDeviceToDevice,
-                     (cudaStream_t)stream));
+  CK(cudaMemcpyAsync(out_dev, (const char*)h->leafsel[half] + (size_t)h->cs.row_of(copy) * bytes, bytes,
+                     cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return SIM_OK;
   API_END
 }

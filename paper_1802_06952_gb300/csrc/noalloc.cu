@@ -71,7 +71,7 @@ extern "C" int sim_amplitudes_noalloc(sim_halves h, int contraction, int accumul
     return set_error(SIM_EINVAL, "sim_amplitudes_noalloc writes device memory only (out_dev is not device memory)");
   }
   const int64_t M = v.nsel[1], N = v.nsel[0];
-  const int64_t K = (int64_t)(v.ke - v.kb);
+  const int64_t K = (int64_t)v.K;
   const int64_t kpad = ((2 * K + 63) / 64) * 64;
   const int64_t N2 = 2 * N;
   // scratch layout: [status int][4 fp16 scale floats][A hi][A lo][B hi][B lo]

@@ -148,7 +148,7 @@ struct CutPlan {
 // points kept in other files; returns false for a NULL handle.
 struct HalvesView {
   int precision;
-  uint64_t kb, ke;
+  uint64_t K;  // copies held (leaf rows)
   int64_t nsel[2];
   const void* leafsel[2];
 };

@@ -111,6 +111,43 @@ def test_bad_shapes_and_cuts():
         sim.sim_destroy_circuit(c)
 
 
+@pytest.mark.parametrize("R,C,d,b", [(4, 4, 10, 2), (6, 5, 16, 3), (6, 7, 22, 3), (8, 8, 22, 4)])
+def test_plan_levels_cover_the_copy_bits(R, C, d, b):
+    """Levels: root first, copy bits fixed in order up to c, passes adding up to the
+    schedule's total; the branch layers are the layers holding cuts."""
+    circ = sim.sim_build_circuit(R, C, d, 0, b)
+    plan, c, copies, nu, nl = sim.sim_cut(circ, b)
+    try:
+        cut_layers = sorted({t for (t, u, l) in sim.sim_cut_list(plan, c)[0]})
+        for half in (0, 1):
+            lv = sim.sim_plan_levels(plan, half)
+            nlev, fused, plain = sim.sim_plan_schedule(plan, half)
+            assert lv.shape == (nlev, 4) and lv[:, 3].sum() == fused
+            assert lv[0, 0] == -1 and lv[0, 1] == 0 and lv[-1, 2] == c
+            assert all(lv[j, 1] == lv[j - 1, 2] for j in range(1, nlev))
+            assert list(lv[1:, 0]) == cut_layers[: nlev - 1]
+    finally:
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(circ)
+
+
+def test_bad_copy_lists_rejected_on_the_host():
+    """sim_evolve_halves_list validates its list before any device work."""
+    c = sim.sim_build_circuit(4, 4, 10, 0)
+    plan, cc, copies, nu, nl = sim.sim_cut(c, 2)
+    try:
+        for bad in ([], [0, 3, 3], [copies], [1, 2, copies + 5]):
+            with pytest.raises(sim.SimError) as e:
+                sim.sim_evolve_halves_list(plan, sim.SIM_C64, np.array(bad, dtype=np.uint64))
+            assert e.value.code == sim.SIM_EINVAL and sim.sim_last_error()
+        with pytest.raises(sim.SimError) as e:
+            sim.sim_evolve_halves(plan, sim.SIM_C64, 3, 3)
+        assert e.value.code == sim.SIM_EINVAL
+    finally:
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(c)
+
+
 @pytest.mark.parametrize("nqu,nu,nql,nl,seed", [(15, 300, 15, 77, 0), (21, 1 << 10, 21, 1 << 10, 5),
                                                 (4, 16, 4, 3, 1), (32, 5, 32, 5, 123)])
 def test_select_equals_oracle(nqu, nu, nql, nl, seed):
