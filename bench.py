@@ -56,6 +56,8 @@ def parse():
                     help="also time the 64-qubit circuit (8x8, depth 22, c=16) on LEAVES seeded copies and "
                          "extrapolate to all 65536 with Eq. (2)")
     ap.add_argument("--q-only", action="store_true", help="profiling case: only the 42/64-qubit measurements")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-circuit batch measurement")
+    ap.add_argument("--batch-only", action="store_true", help="profiling case: only the batch measurement")
     ap.add_argument("--select", type=int, default=0,
                     help="profiling case: contract only the first S upper x S lower indices (S*S amplitudes)")
     return ap.parse_args()
@@ -342,6 +344,72 @@ def run_q64(sim, torch, stream, leaves, contraction_tflops):
     return res
 
 
+def batch_descs(n=64):
+    """The batch workload: n circuits, seeds 0..n-1; grid R x 4 with R = 5, 6, 7, 8
+    in turn (20-32 qubits), cut at row R // 2, depth uniform in 12..20 (numpy
+    default_rng(0)); the cut layers 7, 8, 15, 16 give c = 4, 6 or 8."""
+    import numpy as np
+    depths = np.random.default_rng(0).integers(12, 21, size=n)
+    return [(5 + i % 4, 4, int(depths[i]), i, (5 + i % 4) // 2) for i in range(n)]
+
+
+def run_batch(sim, torch, stream, reps=3):
+    """64 circuits evaluated in full, each into the shared output buffer; fixed
+    choices vs the autotuner, each as CUDA-graph replays (after the uncaptured and
+    the captured run)."""
+    import numpy as np
+    descs = batch_descs()
+    total_amps = sum(1 << (r * c) for (r, c, d, s, b) in descs)
+    res = {"workload": "64 random grid circuits R x 4, R = 5..8 (20-32 qubits), depth uniform 12-20, seeds 0-63, "
+                       "cut at row R/2 (c = 4, 6, 8): every circuit's full amplitude vector, one after another "
+                       "into one reused output buffer, statistics fused, 4096 amplitudes per circuit gathered",
+           "circuits": len(descs), "amplitudes_per_run": total_amps}
+    rng = np.random.default_rng(5)
+    subset = np.stack([rng.choice(1 << (r * c), 4096, replace=False) for (r, c, d, s, b) in descs]).astype(np.uint64)
+    for label, tune in (("fixed", False), ("autotuned", True)):
+        t0 = time.perf_counter()
+        b = sim.sim_batch_create(descs, subset, autotune=tune, use_graph=True, stream=stream)
+        t_create = time.perf_counter() - t0
+        try:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            eager = []
+            for r in range(2):      # uncaptured run, captured run
+                torch.cuda.synchronize()
+                e0.record(stream)
+                sim.sim_batch_run(b, stream=stream)
+                e1.record(stream)
+                sim.sim_status(stream)
+                eager.append(e0.elapsed_time(e1))
+            sim.sim_profile_read(reset=True)
+            sim.sim_profile_enable(True)
+            times = []
+            for r in range(reps):   # graph replays
+                e0.record(stream)
+                sim.sim_batch_run(b, stream=stream)
+                e1.record(stream)
+                sim.sim_status(stream)
+                times.append(e0.elapsed_time(e1))
+            sim.sim_profile_enable(False)
+            prof = sim.sim_profile_read(reset=True)
+            st, _ = sim.sim_batch_results(b, len(descs), 4096)
+            choices = {}
+            for i, (R, C, d, s, cut) in enumerate(descs):
+                info, ms = sim.sim_batch_info(b, i)
+                if ms > 0 or not tune:
+                    choices.setdefault("%dx%d c=%d" % (R, C, info["c"]),
+                                       {k: info[k] for k in ("fuse", "single_cta", "group")})
+            ms = statistics.median(times)
+            res[label] = {"ms_per_run": ms, "amplitudes_per_s": total_amps / (ms / 1e3),
+                          "uncaptured_run_ms": eager[0], "create_s": t_create,
+                          "launches_per_run": int(sum(prof["launches"])) // reps,
+                          "max_abs_norm_error": float(np.max(np.abs(st[:, 0] - 1.0))),
+                          "choices": choices}
+        finally:
+            sim.sim_destroy_batch(b)
+            sim.sim_release_cache()
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -363,6 +431,10 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps(sweep_hbm(sim, torch, stream, reps=1, cols=args.sweep_cols, fuse=args.sweep_fuse)),
                   flush=True)
+        return
+    if args.batch_only:
+        if rank == 0:
+            print(json.dumps(run_batch(sim, torch, stream)), flush=True)
         return
     if args.q_only:
         if rank == 0:
@@ -469,6 +541,8 @@ def run_ours(args):
 
     if not args.no_sweep:
         line["sweep_hbm"] = sweep_hbm(sim, torch, stream)
+    if rank == 0 and not args.no_batch and args.select == 0:
+        line["batch"] = run_batch(sim, torch, stream)
     if rank == 0 and not args.no_q42 and args.select == 0:
         line["q42"] = run_q42(sim, torch, stream)
     if rank == 0 and args.q64 and args.select == 0:

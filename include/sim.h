@@ -273,6 +273,63 @@ int sim_profile_enable(int on);
 int sim_profile_read(double* ms_out, uint64_t* instances_out, uint64_t* launches_out,
                      uint64_t* bytes_out, int reset);
 
+/* ---- Batches of circuits ------------------------------------------------------
+ * Many circuits of different sizes and cuts, each evaluated in full (all copies,
+ * all 2^n amplitudes) into one output buffer that the circuits reuse in turn.  The
+ * paper evaluates one circuit at a time; a batch keeps the GPU busy across many
+ * small ones: everything is planned and allocated at creation, so a run is a pure
+ * sequence of kernel launches that can be captured once into a CUDA graph. */
+typedef struct sim_batch_s* sim_batch;
+
+/* Batch options (NULL: defaults; zero fields mean the default).
+ *   contraction  SIM_SPLIT_BF16 (default) or SIM_SPLIT_FP16
+ *   autotune     0: fixed choices (fused-pass width 12, CTA-pair contraction with
+ *                raster groups of 32); 1: for each circuit shape (rows, cols, cut
+ *                row, cut CZs c), time fuse widths 10..13 and three contraction tile
+ *                variants on its first circuit and keep the fastest
+ *   use_graph    1: the second sim_batch_run captures the batch into a CUDA graph
+ *                (the first one runs uncaptured and initialises every kernel);
+ *                later runs launch the graph */
+typedef struct {
+  int contraction;
+  int autotune;
+  int use_graph;
+  int reserved[5];
+} sim_batch_opts;
+
+/* Build, cut and schedule every circuit (host), autotune if asked (device work on
+ * stream, which is synchronised), allocate the buffers for the largest circuit and
+ * upload the op and node tables.
+ *   descs, n_circuits  circuit descriptions (sim_build_circuit); cut_row 0 means
+ *                      the middle row
+ *   subset_idx         host array [n_circuits][subset_n] of flat amplitude indices
+ *                      x = x_u + 2^{n_u} x_l (< 2^n of that circuit), or NULL when
+ *                      subset_n is 0; each run gathers those amplitudes
+ * SIM_EINVAL on a bad description or index; SIM_ENOMEM if the buffers do not fit;
+ * SIM_EUNSUPPORTED for circuits above 34 qubits (full vectors). */
+int sim_batch_create(const sim_circuit_desc* descs, int n_circuits, const uint64_t* subset_idx,
+                     uint64_t subset_n, const sim_batch_opts* opts, void* stream, sim_batch* out);
+
+/* Enqueue one evaluation of the whole batch on stream: per circuit the sweeps of
+ * both halves, the split-pack, the tensor-core contraction into the shared output
+ * buffer with the statistics fused into it, and the subset gather.  No host
+ * synchronisation and no allocation; the batch's buffers are reused, so runs must
+ * not overlap. */
+int sim_batch_run(sim_batch b, void* stream);
+
+/* After a run has finished (the caller synchronises its stream), per circuit i:
+ * stats_out[4i .. 4i+3] = {sum |A|^2, mean 2^n |A|^2, mean ln 2^n |A|^2, KS
+ * distance to Eq. 7} over all 2^n amplitudes, and subset_out[i * subset_n + j] =
+ * A_i(subset_idx[i][j]) as complex64 (host memory).  Either may be NULL. */
+int sim_batch_results(sim_batch b, double* stats_out, void* subset_out);
+
+/* Circuit i of the batch: {qubits, cut CZs c, fuse width, contraction kernel
+ * (0 CTA pair, 1 single CTA), raster group} and the autotuner's time in ms of
+ * the chosen sweep + contraction of that shape (0 when not tuned on this circuit). */
+int sim_batch_info(sim_batch b, int i, int32_t info_out[5], double* tuned_ms);
+
+void sim_destroy_batch(sim_batch b);
+
 void sim_destroy_circuit(sim_circuit circ);
 void sim_destroy_cut(sim_cut_plan plan);
 void sim_destroy_halves(sim_halves h);

@@ -32,7 +32,8 @@ EXPORTS = (
     "sim_select", "sim_sample", "sim_status", "sim_release_cache", "sim_destroy_circuit",
     "sim_destroy_cut", "sim_destroy_halves", "sim_last_error", "sim_version",
     "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc", "sim_amplitudes_stats",
-    "sim_evolve_halves_list", "sim_plan_levels",
+    "sim_evolve_halves_list", "sim_plan_levels", "sim_batch_create", "sim_batch_run", "sim_batch_results",
+    "sim_batch_info", "sim_destroy_batch",
 )
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -46,6 +47,11 @@ class SimError(RuntimeError):
 class _Desc(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int), ("cols", ctypes.c_int), ("depth", ctypes.c_int),
                 ("seed", ctypes.c_uint64), ("cut_row", ctypes.c_int), ("gate_list", ctypes.c_char_p)]
+
+
+class BatchOpts(ctypes.Structure):
+    _fields_ = [("contraction", ctypes.c_int), ("autotune", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class SimOpts(ctypes.Structure):
@@ -80,6 +86,12 @@ def lib():
         "sim_evolve_halves_list": (ctypes.c_int, [vp, ctypes.c_int, u64p, u64, u64p, u64, u64p, u64,
                                                   ctypes.POINTER(SimOpts), vp, ctypes.POINTER(vp)]),
         "sim_halves_leaf": (ctypes.c_int, [vp, ctypes.c_int, u64, vp, vp]),
+        "sim_batch_create": (ctypes.c_int, [ctypes.POINTER(_Desc), ctypes.c_int, u64p, u64, ctypes.POINTER(BatchOpts),
+                                            vp, ctypes.POINTER(vp)]),
+        "sim_batch_run": (ctypes.c_int, [vp, vp]),
+        "sim_batch_results": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), vp]),
+        "sim_batch_info": (ctypes.c_int, [vp, ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_double)]),
+        "sim_destroy_batch": (None, [vp]),
         "sim_amplitudes": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
         "sim_stats": (ctypes.c_int, [vp, ctypes.c_int, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      u64p, vp]),
@@ -226,6 +238,50 @@ def sim_evolve_halves_list(plan, precision, copies, sel_u=None, sel_l=None, opts
                                         sl.ctypes.data_as(P) if sl is not None else None, nl,
                                         _opts(opts), _stream(stream), ctypes.byref(h)))
     return h.value
+
+
+def sim_batch_create(descs, subset_idx=None, contraction=0, autotune=False, use_graph=False, stream=None):
+    """descs: list of (rows, cols, depth, seed, cut_row); subset_idx: uint64 array
+    [n_circuits, S] of flat amplitude indices (or None)."""
+    n = len(descs)
+    arr = (_Desc * n)(*[_Desc(r, c, d, s, b, None) for (r, c, d, s, b) in descs])
+    S = 0
+    ptr = None
+    if subset_idx is not None:
+        subset_idx = np.ascontiguousarray(subset_idx, dtype=np.uint64)
+        assert subset_idx.shape[0] == n
+        S = subset_idx.shape[1]
+        ptr = subset_idx.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+    o = BatchOpts(contraction, int(autotune), int(use_graph), (ctypes.c_int * 5)())
+    h = ctypes.c_void_p()
+    _check(lib().sim_batch_create(arr, n, ptr, S, ctypes.byref(o), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def sim_batch_run(batch, stream=None):
+    _check(lib().sim_batch_run(batch, _stream(stream)))
+
+
+def sim_batch_results(batch, n_circuits, subset_n):
+    """(stats [n, 4], subset amplitudes [n, subset_n] complex64); call after the
+    run's stream has been synchronised."""
+    st = np.zeros((n_circuits, 4), dtype=np.float64)
+    sub = np.zeros((n_circuits, subset_n), dtype=np.complex64)
+    _check(lib().sim_batch_results(batch, st.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   sub.ctypes.data_as(ctypes.c_void_p) if subset_n else None))
+    return st, sub
+
+
+def sim_batch_info(batch, i):
+    """({n, c, fuse, gemm kernel (0 pair, 1 single), raster group}, tuned ms)."""
+    info = np.zeros(5, dtype=np.int32)
+    ms = ctypes.c_double()
+    _check(lib().sim_batch_info(batch, i, info.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(ms)))
+    return dict(zip(("n", "c", "fuse", "single_cta", "group"), (int(x) for x in info))), ms.value
+
+
+def sim_destroy_batch(batch):
+    lib().sim_destroy_batch(batch)
 
 
 def sim_halves_leaf(halves, half, copy, out, stream=None):

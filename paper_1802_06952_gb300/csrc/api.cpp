@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/sim.h"
+#include "runtime.h"
 #include "sim_internal.h"
 
 using namespace sim;
@@ -24,18 +25,6 @@ struct sim_circuit_s {
 
 struct sim_cut_s {
   CutPlan p;
-};
-
-// The copies of an evolved halves object, in leaf-row order: the range [kb, ke) or
-// an explicit list of distinct copy indices.
-struct CopySet {
-  uint64_t kb = 0, ke = 0;
-  std::vector<uint64_t> list;                 // empty: the range
-  std::unordered_map<uint64_t, int64_t> row;  // list: copy index -> row
-  uint64_t size() const { return list.empty() ? ke - kb : (uint64_t)list.size(); }
-  uint64_t at(uint64_t i) const { return list.empty() ? kb + i : list[i]; }
-  bool contains(uint64_t k) const { return list.empty() ? (k >= kb && k < ke) : row.count(k) > 0; }
-  int64_t row_of(uint64_t k) const { return list.empty() ? (int64_t)(k - kb) : row.at(k); }
 };
 
 struct sim_halves_s {
@@ -179,6 +168,7 @@ struct Profiler {
   uint64_t inst[SIM_NUM_PHASES] = {};
   uint64_t launches[SIM_NUM_PHASES] = {};
   uint64_t h2d = 0, d2h = 0;
+  uint64_t all_launches[SIM_NUM_PHASES] = {};  // counted whether or not the profiler is on
 
   cudaEvent_t get() {
     if (!spare.empty()) {
@@ -295,18 +285,6 @@ int upload_plan_ops(CutPlan& P, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // complex64 copy-tree evolution of one half
 // ---------------------------------------------------------------------------
-struct LaunchRec {
-  int level, pass;      // pass < 0: gather
-  int64_t table_off, nslots;
-  int src_buf, dst_buf; // buffer ids: level index, or -1 = leafsel
-};
-
-struct TreeProgram {
-  std::vector<NodeEntry> table;
-  std::vector<LaunchRec> launches;
-  std::vector<int64_t> level_cap;  // nodes per chunk buffer of each level
-};
-
 struct TreeBuilder {
   const HalfSchedule& S;
   const CopySet& cs;
@@ -411,17 +389,10 @@ struct TreeBuilder {
   }
 };
 
-int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel, int64_t nsel, bool full,
-                    void* leafsel, cudaStream_t st, const sim_opts* opts) {
-  const HalfSchedule& S = P.sched[h];
-  const int n = S.n;
-  const size_t state_bytes = sizeof(float) * 2 * ((size_t)1 << n);
+TreeProgram plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_t budget) {
+  const size_t state_bytes = sizeof(float) * 2 * ((size_t)1 << S.n);
   const int J = (int)S.levels.size();
   TreeProgram prog;
-  // chunk capacity per level from the free device memory
-  size_t fr = 0, tot = 0;
-  CK(cudaMemGetInfo(&fr, &tot));
-  const size_t budget = (size_t)(fr * 0.6);
   for (int j = 0; j < J; ++j) {
     const int64_t need_nodes = (int64_t)std::min<uint64_t>(
         cs.size(), S.levels[j].bits_total >= 63 ? ~0ull : (1ull << S.levels[j].bits_total));
@@ -431,23 +402,19 @@ int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel,
   }
   TreeBuilder tb{S, cs, full, {}, prog};
   tb.build();
-  // buffers
-  std::vector<DevBuf> lvl(J);
-  for (int j = 0; j < J; ++j) {
-    const bool leaf = (j == J - 1);
-    if (leaf && full) continue;
-    CK(lvl[j].alloc(state_bytes * (size_t)prog.level_cap[j]));
-  }
-  DevBuf table;
-  CK(table.alloc(sizeof(NodeEntry) * (prog.table.size() + 1)));
-  CK(cudaMemcpyAsync(table.p, prog.table.data(), sizeof(NodeEntry) * prog.table.size(), cudaMemcpyHostToDevice, st));
-  note_bytes(sizeof(NodeEntry) * prog.table.size(), 0);
-  const int threads = (opts && opts->sweep_threads > 0) ? opts->sweep_threads : 256;
+  return prog;
+}
+
+int enqueue_tree(const CutPlan& P, int h, const TreeProgram& prog, void* const* lvl, const NodeEntry* table,
+                 const uint64_t* d_sel, int64_t nsel, void* leafsel, cudaStream_t st, int kernel_choice,
+                 int threads) {
+  const HalfSchedule& S = P.sched[h];
+  const int n = S.n;
   for (const LaunchRec& r : prog.launches) {
-    void* dstp = r.dst_buf < 0 ? leafsel : lvl[r.dst_buf].p;
+    void* dstp = r.dst_buf < 0 ? leafsel : lvl[r.dst_buf];
     PhaseScope ps(r.pass < 0 ? SIM_PHASE_GATHER : SIM_PHASE_SWEEP, st);
     if (r.pass < 0) {
-      CK(launch_gather(lvl[r.src_buf].p, n, table.as<NodeEntry>() + r.table_off, r.nslots, d_sel, nsel, leafsel, 0, st));
+      CK(launch_gather(lvl[r.src_buf], n, table + r.table_off, r.nslots, d_sel, nsel, leafsel, 0, st));
       continue;
     }
     const PassDesc& pd = S.levels[r.level].passes[r.pass];
@@ -459,9 +426,9 @@ int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel,
     sl.ops = P.d_ops[h] + pd.op_begin;
     sl.op_count = pd.op_count;
     sl.src = pd.src;
-    sl.nodes = table.as<NodeEntry>() + r.table_off;
+    sl.nodes = table + r.table_off;
     sl.nslots = r.nslots;
-    sl.src_base = pd.src == SRC_PARENT ? lvl[r.src_buf].p : dstp;
+    sl.src_base = pd.src == SRC_PARENT ? lvl[r.src_buf] : dstp;
     sl.dst_base = dstp;
     sl.threads = threads;
     memcpy(sl.order, pd.order, sizeof sl.order);
@@ -473,15 +440,39 @@ int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel,
     memcpy(sl.sorder, pd.sorder, sizeof sl.sorder);
     memcpy(sl.swz, pd.swz, sizeof sl.swz);
     sl.transpose = pd.transpose;
-    const int kernel_choice = opts ? opts->sweep_kernel : 0;
     if (kernel_choice != 1 && sweep2_supported(sl))
       CK(launch_sweep2_c64(sl, st));
     else
       CK(launch_sweep_c64(sl, st));
   }
-  // the pool may hand these buffers to the next call on this stream only after
-  // the launches above have been enqueued, which keeps reuse stream-ordered
   return SIM_OK;
+}
+
+int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel, int64_t nsel, bool full,
+                    void* leafsel, cudaStream_t st, const sim_opts* opts) {
+  const HalfSchedule& S = P.sched[h];
+  const size_t state_bytes = sizeof(float) * 2 * ((size_t)1 << S.n);
+  const int J = (int)S.levels.size();
+  // chunk capacity per level from the free device memory
+  size_t fr = 0, tot = 0;
+  CK(cudaMemGetInfo(&fr, &tot));
+  const TreeProgram prog = plan_tree(S, cs, full, (size_t)(fr * 0.6));
+  std::vector<DevBuf> lvl(J);
+  std::vector<void*> lp(J, nullptr);
+  for (int j = 0; j < J; ++j) {
+    const bool leaf = (j == J - 1);
+    if (leaf && full) continue;
+    CK(lvl[j].alloc(state_bytes * (size_t)prog.level_cap[j]));
+    lp[j] = lvl[j].p;
+  }
+  DevBuf table;
+  CK(table.alloc(sizeof(NodeEntry) * (prog.table.size() + 1)));
+  CK(cudaMemcpyAsync(table.p, prog.table.data(), sizeof(NodeEntry) * prog.table.size(), cudaMemcpyHostToDevice, st));
+  note_bytes(sizeof(NodeEntry) * prog.table.size(), 0);
+  // the pool may hand these buffers to the next call on this stream only after
+  // the launches are enqueued, which keeps reuse stream-ordered
+  return enqueue_tree(P, h, prog, lp.data(), table.as<NodeEntry>(), d_sel, nsel, leafsel, st,
+                      opts ? opts->sweep_kernel : 0, (opts && opts->sweep_threads > 0) ? opts->sweep_threads : 256);
 }
 
 // ---------------------------------------------------------------------------
@@ -648,6 +639,31 @@ void finish_stats(const double a[3], const std::vector<unsigned long long>& hh, 
 }  // namespace
 
 namespace sim {
+TreeProgram rt_plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_t budget) {
+  return plan_tree(S, cs, full, budget);
+}
+int rt_enqueue_tree(const CutPlan& P, int half, const TreeProgram& prog, void* const* lvl, const NodeEntry* table,
+                    const uint64_t* d_sel, int64_t nsel, void* leafsel, cudaStream_t st, int kernel_choice,
+                    int threads) {
+  return enqueue_tree(P, half, prog, lvl, table, d_sel, nsel, leafsel, st, kernel_choice, threads);
+}
+cudaError_t rt_alloc(void** p, size_t n) { return pool().alloc(p, n); }
+void rt_free(void* p) { pool().free(p); }
+int rt_device(int** d_status, int* num_sms) {
+  DeviceInfo* di = nullptr;
+  const int rc = device_info(&di);
+  if (rc) return rc;
+  if (d_status) *d_status = di->d_status;
+  if (num_sms) *num_sms = di->num_sms;
+  return SIM_OK;
+}
+int rt_upload_plan(CutPlan& P, cudaStream_t st) { return upload_plan_ops(P, st); }
+void rt_free_plan(CutPlan& P) { free_plan_ops(P); }
+void rt_finish_stats(const double acc[3], const std::vector<unsigned long long>& hist, uint64_t count, int n_qubits,
+                     double stats_out[4], uint64_t* hist_out) {
+  finish_stats(acc, hist, count, n_qubits, stats_out, hist_out);
+}
+
 bool halves_view(const sim_halves_s* h, HalvesView* v) {
   if (!h || !v) return false;
   v->precision = h->precision;
@@ -664,7 +680,21 @@ int set_error(int code, const std::string& msg) { return fail(code, msg); }
 void note_launches(int phase, int count) {
   Profiler& P = prof();
   std::lock_guard<std::mutex> lk(P.mu);
-  if (P.on && phase >= 0 && phase < SIM_NUM_PHASES) P.launches[phase] += (uint64_t)count;
+  if (phase < 0 || phase >= SIM_NUM_PHASES) return;
+  P.all_launches[phase] += (uint64_t)count;
+  if (P.on) P.launches[phase] += (uint64_t)count;
+}
+bool rt_profile_swap(bool on) {
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  const bool old = P.on;
+  P.on = on;
+  return old;
+}
+void rt_launch_totals(uint64_t out[SIM_NUM_PHASES]) {
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> lk(P.mu);
+  for (int i = 0; i < SIM_NUM_PHASES; ++i) out[i] = P.all_launches[i];
 }
 void note_bytes(uint64_t h2d, uint64_t d2h) {
   Profiler& P = prof();

@@ -525,7 +525,8 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kpad, in
 }  // namespace
 
 cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s) {
-  if (tc_gemm_pair_enabled() && tc_gemm_pair_supported(a)) return launch_tc_gemm_pair(a, s);
+  const bool want_pair = a.variant == 2 || (a.variant == 0 && tc_gemm_pair_enabled());
+  if (want_pair && tc_gemm_pair_supported(a)) return launch_tc_gemm_pair(a, s);
   if (a.M <= 0 || a.N2 <= 0) return cudaSuccess;
   if (a.kpad <= 0 || a.kpad % BK != 0 || a.M > (1ll << 31) - BM || a.N2 > (1ll << 31) - BN)
     return cudaErrorInvalidValue;

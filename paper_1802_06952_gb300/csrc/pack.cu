@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "../../include/sim.h"
 #include "sim_internal.h"
 
@@ -162,6 +164,22 @@ cudaError_t launch_absmax_c64(const void* x, int64_t count, float* out_dev, cuda
   if (e != cudaSuccess) return e;
   scale_from_max_kernel<<<1, 1, 0, s>>>(out_dev);
   note_launches(SIM_PHASE_PACK, 2);
+  return cudaGetLastError();
+}
+
+namespace {
+__global__ void gather_flat_kernel(const float2* __restrict__ src, const uint64_t* __restrict__ idx, int64_t n,
+                                   float2* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = src[idx[i]];
+}
+}  // namespace
+
+cudaError_t launch_gather_flat_c64(const void* src, const uint64_t* idx, int64_t n, void* dst, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+  gather_flat_kernel<<<(unsigned)blocks, 256, 0, s>>>((const float2*)src, idx, n, (float2*)dst);
+  note_launches(SIM_PHASE_GATHER, 1);
   return cudaGetLastError();
 }
 

@@ -232,6 +232,8 @@ cudaError_t launch_pack_b(const void* leaves, int64_t K, int64_t nsel, int64_t k
 // out_dev[0] = max |re|, |im| over a complex64 array; out_dev[1] = the power-of-two
 // fp16 pre-scale derived from it
 cudaError_t launch_absmax_c64(const void* x, int64_t count, float* out_dev, cudaStream_t s);
+// dst[i] = src[idx[i]] for n complex64 values (a flat-index gather of amplitudes)
+cudaError_t launch_gather_flat_c64(const void* src, const uint64_t* idx, int64_t n, void* dst, cudaStream_t s);
 
 // tcgen05 contraction: C[M][2N] fp32 (= complex64 [M][N]) (+)= sum over 3 split
 // segments of A_seg[M][kpad] * B_seg[2N][kpad]^T.
@@ -250,6 +252,10 @@ struct TcGemmArgs {
   float w_scale = 1.f;            // 2^n
   double* st_acc = nullptr;       // [sum |A|^2, sum ln 2^n|A|^2 over |A| > 0, count]
   unsigned long long* st_hist = nullptr;  // SIM_KS_BINS counts of u = 1 - exp(-2^n |A|^2)
+  // 0: the CTA-pair kernel where it applies (SIM_TC_PAIR=0 in the environment
+  // selects the single-CTA one); 1: single-CTA kernel; 2: CTA-pair kernel where it
+  // applies (16-byte output rows), the single-CTA kernel otherwise
+  int variant = 0;
 };
 cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s);
 // CTA-pair variant of the same contraction (tcgen05 cta_group::2, M = 256 per pair)

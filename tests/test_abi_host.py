@@ -131,6 +131,19 @@ def test_plan_levels_cover_the_copy_bits(R, C, d, b):
         sim.sim_destroy_circuit(circ)
 
 
+def test_bad_batches_rejected_on_the_host():
+    """sim_batch_create validates circuits and subset indices before any device work."""
+    with pytest.raises(sim.SimError) as e:
+        sim.sim_batch_create([(5, 4, 12, 0, 2), (0, 4, 12, 1, 2)])
+    assert e.value.code == sim.SIM_EINVAL
+    with pytest.raises(sim.SimError) as e:
+        sim.sim_batch_create([(5, 4, 12, 0, 2)], subset_idx=np.array([[1, 2, 1 << 20]], dtype=np.uint64))
+    assert e.value.code == sim.SIM_EINVAL and "subset" in sim.sim_last_error()
+    with pytest.raises(sim.SimError) as e:
+        sim.sim_batch_create([(5, 4, 12, 0, 5)])
+    assert e.value.code == sim.SIM_EINVAL
+
+
 def test_bad_copy_lists_rejected_on_the_host():
     """sim_evolve_halves_list validates its list before any device work."""
     c = sim.sim_build_circuit(4, 4, 10, 0)
