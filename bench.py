@@ -57,6 +57,7 @@ def parse():
                          "extrapolate to all 65536 with Eq. (2)")
     ap.add_argument("--q-only", action="store_true", help="profiling case: only the 42/64-qubit measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-circuit batch measurement")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GPU path on the 30-qubit circuit")
     ap.add_argument("--batch-only", action="store_true", help="profiling case: only the batch measurement")
     ap.add_argument("--select", type=int, default=0,
                     help="profiling case: contract only the first S upper x S lower indices (S*S amplitudes)")
@@ -344,6 +345,36 @@ def run_q64(sim, torch, stream, leaves, contraction_tflops):
     return res
 
 
+def run_plain_fp64(sim, torch, stream):
+    """The same 30-qubit workload (seed 0) through the plain FP64 GPU path: every copy
+    evolved on its own in complex128, one pass per gate (Sections 2.3.1, 2.4), and
+    the FP64 contraction: the reference the split path must beat at <= 1e-5."""
+    circ = sim.sim_build_circuit(R, C, DEPTH, SEEDS[0], CUT_ROW)
+    plan, c, copies, nu, nl = sim.sim_cut(circ, CUT_ROW)
+    out = torch.empty((1 << nl, 1 << nu), dtype=torch.complex128, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sim.sim_profile_read(reset=True)
+    sim.sim_profile_enable(True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    h = sim.sim_evolve_halves(plan, sim.SIM_C128_PLAIN, 0, copies, stream=stream)
+    sim.sim_amplitudes(h, sim.SIM_FP64_PLAIN, False, out, stream=stream)
+    e1.record(stream)
+    sim.sim_status(stream)
+    sim.sim_profile_enable(False)
+    prof = sim.sim_profile_read(reset=True)
+    ms = e0.elapsed_time(e1)
+    sim.sim_destroy_halves(h)
+    sim.sim_destroy_cut(plan)
+    sim.sim_destroy_circuit(circ)
+    del out
+    sim.sim_release_cache()
+    return {"workload": "the bench's 30-qubit circuit, seed 0, through the plain FP64 GPU path",
+            "ms": ms, "amplitudes_per_s": (1 << (nu + nl)) / (ms / 1e3),
+            "phases_ms": {sim.PHASE_NAMES[i]: round(prof["ms"][i], 2) for i in range(sim.SIM_NUM_PHASES)
+                          if prof["launches"][i]}}
+
+
 def batch_descs(n=64):
     """The batch workload: n circuits, seeds 0..n-1; grid R x 4 with R = 5, 6, 7, 8
     in turn (20-32 qubits), cut at row R // 2, depth uniform in 12..20 (numpy
@@ -541,6 +572,9 @@ def run_ours(args):
 
     if not args.no_sweep:
         line["sweep_hbm"] = sweep_hbm(sim, torch, stream)
+    if rank == 0 and args.select == 0 and not args.no_plain:
+        line["plain_fp64"] = run_plain_fp64(sim, torch, stream)
+        line["plain_fp64"]["speedup_of_split_path"] = line["plain_fp64"]["ms"] / (total_ms / args.steps)
     if rank == 0 and not args.no_batch and args.select == 0:
         line["batch"] = run_batch(sim, torch, stream)
     if rank == 0 and not args.no_q42 and args.select == 0:
