@@ -440,6 +440,7 @@ int enqueue_tree(const CutPlan& P, int h, const TreeProgram& prog, void* const* 
     memcpy(sl.sorder, pd.sorder, sizeof sl.sorder);
     memcpy(sl.swz, pd.swz, sizeof sl.swz);
     sl.transpose = pd.transpose;
+    sl.vec4 = pd.vec4;
     if (kernel_choice != 1 && sweep2_supported(sl))
       CK(launch_sweep2_c64(sl, st));
     else

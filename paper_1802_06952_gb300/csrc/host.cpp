@@ -350,6 +350,30 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
         if (gates_on[a] != gates_on[b2]) return gates_on[a] > gates_on[b2];
         return a < b2;
       });
+      if (nreg >= 2) {
+        // 256-bit runs: register ranks 8, 9 = qubits 0, 1; lanes 0..2 = qubits 2..4,
+        // so that 8 lanes read 256 contiguous bytes; the busiest other qubits take the
+        // remaining register ranks, the next two lanes 3 and 4, the rest the warp
+        // ranks; loads and stores use this order directly
+        std::vector<int> rest;
+        for (int q : all)
+          if (q > 4) rest.push_back(q);
+        std::vector<int> regs2(rest.begin(), rest.begin() + (nreg - 2));
+        std::vector<int> lanes2 = {2, 3, 4};
+        lanes2.insert(lanes2.end(), rest.begin() + (nreg - 2), rest.begin() + nreg);
+        std::vector<int> warps2(rest.begin() + nreg, rest.end());
+        std::sort(warps2.begin(), warps2.end());
+        r = 0;
+        for (int q : lanes2) p.order[r++] = (uint8_t)q;
+        for (int q : warps2) p.order[r++] = (uint8_t)q;
+        p.order[r++] = 0;
+        p.order[r++] = 1;
+        for (int q : regs2) p.order[r++] = (uint8_t)q;
+        for (int t2 = 0; t2 < k; ++t2) p.sorder[t2] = p.order[t2];
+        memset(p.swz, 0, sizeof p.swz);
+        p.transpose = 0;
+        p.vec4 = 1;
+      } else {
       std::vector<int> lanes(all.begin(), all.begin() + 5);
       std::vector<int> regs(all.begin() + 5, all.begin() + 5 + nreg);
       std::vector<int> warps(all.begin() + 5 + nreg, all.end());
@@ -392,6 +416,7 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
             covered |= 1u << b;
             break;
           }
+      }
       }
     } else {
       for (int q = 0; q < low; ++q) p.order[r++] = (uint8_t)q;

@@ -100,6 +100,11 @@ struct PassDesc {
   // both orders read and write shared memory without bank conflicts
   uint8_t sorder[16];
   uint8_t swz[16];
+  // register-blocked sweep with k >= 10: register ranks 8 and 9 hold qubits 0 and 1,
+  // so each thread's elements come in runs of 4 consecutive amplitudes (32 bytes)
+  // loaded and stored with one 256-bit access each; any qubits can then be lanes,
+  // and the compute order is also the load order (no transposes)
+  int vec4;
   int transpose;        // compute order differs from storage order
 };
 
@@ -193,9 +198,10 @@ struct SweepLaunch {
   int general_gates;
   float scale;
   int phase_e, phase_op;  // PassDesc::phase_e, phase_op
-  uint8_t sorder[16];     // PassDesc::sorder, swz, transpose
+  uint8_t sorder[16];     // PassDesc::sorder, swz, transpose, vec4
   uint8_t swz[16];
   int transpose;
+  int vec4;
 };
 // staged-block sweep (any k, any threads)
 cudaError_t launch_sweep_c64(const SweepLaunch& L, cudaStream_t s);

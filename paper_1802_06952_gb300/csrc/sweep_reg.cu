@@ -11,6 +11,11 @@
 // When the two differ, the block transposes once after the load and once before
 // the store through shared memory, in a layout whose low 4 slot bits are XORed
 // with a per-pass mask of the high bits so that both orders are bank-conflict free.
+// For k >= 10 the planner instead puts qubits 0 and 1 on register bits 0 and 1
+// (vec4): each thread's elements then form runs of 4 consecutive amplitudes, one
+// 32-byte sector each, loaded and stored with 256-bit accesses, which keeps every
+// access sector-coalesced for any choice of lane qubits; the compute order is the
+// load order and no transpose is needed.
 // In compute order each thread keeps its 2^R amplitudes in registers:
 //   gate on a register rank  register pairs, no data exchange
 //   gate on a lane rank      partner value by warp shuffle
@@ -54,8 +59,22 @@ struct RegArgs {
   int phase_e;           // w^phase_e: their phase
   int phase_op;          // diagonal op that takes the phase (-1: the store)
   int transpose;
+  int vec4;              // runs of 4 consecutive amplitudes on register bits 0, 1
   uint32_t xs_bytes;     // shared-memory slots before the copy of the ops
 };
+
+// 4 consecutive complex64 amplitudes (32 bytes, 32-byte aligned) in one access; the
+// data is streamed once, so it does not allocate in L1
+__device__ __forceinline__ void load_run4(const float2* p, float2& a, float2& b, float2& c, float2& d) {
+  asm volatile("ld.global.L1::no_allocate.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=f"(a.x), "=f"(a.y), "=f"(b.x), "=f"(b.y), "=f"(c.x), "=f"(c.y), "=f"(d.x), "=f"(d.y)
+               : "l"(p));
+}
+__device__ __forceinline__ void store_run4(float2* p, float2 a, float2 b, float2 c, float2 d) {
+  asm volatile("st.global.L1::no_allocate.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a.x),
+               "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y), "f"(d.x), "f"(d.y)
+               : "memory");
+}
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -248,6 +267,9 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
   } else if (a.src == SRC_ZERO) {
 #pragma unroll
     for (int j = 0; j < NE; ++j) v[j] = make_float2((st | sreg(j)) == 0 ? 1.f : 0.f, 0.f);
+  } else if (R >= 2 && a.vec4) {
+#pragma unroll
+    for (int j = 0; j < NE; j += 4) load_run4(src + (st | sreg(j)), v[j], v[j + 1], v[j + 2], v[j + 3]);
   } else {
 #pragma unroll
     for (int j = 0; j < NE; ++j) v[j] = src[st | sreg(j)];
@@ -432,8 +454,16 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
 #pragma unroll
     for (int j = 0; j < NE; ++j) v[j] = cmul(v[j], w);
   }
+  const float2 sc2 = make_float2(a.scale, a.scale);
+  if (R >= 2 && a.vec4) {
 #pragma unroll
-  for (int j = 0; j < NE; ++j) dst[st | sreg(j)] = __fmul2_rn(v[j], make_float2(a.scale, a.scale));
+    for (int j = 0; j < NE; j += 4)
+      store_run4(dst + (st | sreg(j)), __fmul2_rn(v[j], sc2), __fmul2_rn(v[j + 1], sc2), __fmul2_rn(v[j + 2], sc2),
+                 __fmul2_rn(v[j + 3], sc2));
+  } else {
+#pragma unroll
+    for (int j = 0; j < NE; ++j) dst[st | sreg(j)] = __fmul2_rn(v[j], sc2);
+  }
 }
 
 template <int R>
@@ -485,10 +515,11 @@ cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s) {
   uint32_t seen_c = 0, seen_s = 0;
   int srank[32];
   for (int q = 0; q < 32; ++q) srank[q] = -1;
+  if (L.vec4 && (L.k < 10 || L.transpose || L.order[8] != 0 || L.order[9] != 1)) return cudaErrorInvalidValue;
   for (int r = 0; r < L.k; ++r) {
     const int qc = L.order[r], qs = L.sorder[r];
     if (qc >= L.n || qs >= L.n || (seen_c & (1u << qc)) || (seen_s & (1u << qs))) return cudaErrorInvalidValue;
-    if (r < 5 && qs != r) return cudaErrorInvalidValue;
+    if (!L.vec4 && r < 5 && qs != r) return cudaErrorInvalidValue;
     if ((r < 4 && L.swz[r] != 0) || L.swz[r] > 15) return cudaErrorInvalidValue;
     seen_c |= 1u << qc;
     seen_s |= 1u << qs;
@@ -514,6 +545,7 @@ cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s) {
   a.phase_e = L.phase_e & 7;
   a.phase_op = L.phase_op < L.op_count ? L.phase_op : -1;
   a.transpose = L.transpose;
+  a.vec4 = L.vec4;
   const int use_smem = L.warp_gates > 0 || L.transpose;
   switch (L.k - 8) {
     case 0: return launch_r<0>(a, L.nslots, use_smem, s);
