@@ -86,7 +86,8 @@ typedef struct {
 } sim_circuit_desc;
 
 /* Tuning knobs; pass NULL for defaults.  Zero fields mean "choose automatically".
- *   fuse_qubits    local qubits staged per thread block in a fused sweep (4..13)
+ *   fuse_qubits    local qubits staged per thread block in a fused sweep (4..13;
+ *                  default 13)
  *   sweep_threads  threads per block of the staged sweep (64..256, multiple of 32)
  *   gemm_group_m   m-blocks per raster group of the persistent contraction
  *   sweep_kernel   1: staged shared-memory sweep; 0 or 2: register-blocked sweep
@@ -283,7 +284,7 @@ typedef struct sim_batch_s* sim_batch;
 
 /* Batch options (NULL: defaults; zero fields mean the default).
  *   contraction  SIM_SPLIT_BF16 (default) or SIM_SPLIT_FP16
- *   autotune     0: fixed choices (fused-pass width 12, CTA-pair contraction with
+ *   autotune     0: fixed choices (fused-pass width 13, CTA-pair contraction with
  *                raster groups of 32); 1: for each circuit shape (rows, cols, cut
  *                row, cut CZs c), time fuse widths 10..13 and three contraction tile
  *                variants on its first circuit and keep the fastest

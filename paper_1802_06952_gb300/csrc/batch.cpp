@@ -38,7 +38,7 @@ constexpr int kMaxLevels = 16;
 
 // contraction variants the autotuner chooses from: {TcGemmArgs::variant, raster group}
 constexpr int kGemmVariants[3][2] = {{2, 32}, {2, 8}, {1, 16}};
-constexpr int kFixedFuse = 12;
+constexpr int kFixedFuse = 13;
 constexpr int kFixedGemm = 0;
 
 struct Item {

@@ -301,7 +301,7 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
     int cnt = low;
     size_t j = i;
     for (; j < seq.size(); ++j) {
-      if ((int)(j - i) >= kMaxPassOps) break;
+      if ((int)(j - i) >= kMaxPassOps - 24) break;  // room for the exchanges of the register-blocked sweep
       if (seq[j].type != OP_GATE) continue;
       uint32_t bit = 1u << seq[j].q;
       if (local & bit) continue;
@@ -427,17 +427,79 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
       for (int t2 = 0; t2 < nreg; ++t2) p.order[r++] = (uint8_t)hi[t2];
       for (int t2 = 0; t2 < k; ++t2) p.sorder[t2] = p.order[t2];
     }
-    int rank_of[32];
-    for (int t2 = 0; t2 < 32; ++t2) rank_of[t2] = -1;
-    for (int t2 = 0; t2 < k; ++t2) rank_of[p.order[t2]] = t2;
+    // Ops of the pass with the rank map at each op.  Register-blocked passes with
+    // 256-bit runs (vec4) exchange warp ranks 5+m with register ranks 10+m
+    // (m < nsw) when a gate hits one of those warp ranks, which turns the
+    // exchanged warp qubits into register qubits (one shared-memory round trip,
+    // the cost of one warp-rank gate, for every later gate on them).
+    const int R = (k >= 8 && low == 5) ? k - 8 : 0;
+    // (measured: a gain with three register ranks to exchange, k = 13; a loss with
+    // one or two, where fewer gates move per exchange)
+    const int nsw = (p.vec4 && R >= 5) ? 3 : 0;
+    int ord[16];
+    int rank_of[32], rank0[32];
+    for (int t2 = 0; t2 < 32; ++t2) rank_of[t2] = rank0[t2] = -1;
+    for (int t2 = 0; t2 < 16; ++t2) ord[t2] = t2 < k ? p.order[t2] : -1;
+    for (int t2 = 0; t2 < k; ++t2) rank_of[p.order[t2]] = rank0[p.order[t2]] = t2;
     p.warp_gates = 0;
     p.general_gates = 0;
     int n_xy = 0, n_h = 0;
     p.phase_op = -1;
+    auto fill_diag_tables = [&](OpRec& o) {
+      uint32_t regmask = 0;
+      for (int t2 = 0; t2 < R; ++t2) regmask |= 1u << ord[8 + t2];
+      o.regmask = regmask;
+      memset(o.rq, 0xFF, sizeof o.rq);
+      for (int t2 = 0; t2 < R; ++t2) o.rq[t2] = (uint8_t)ord[8 + t2];
+      memset(o.ereg, 0, sizeof o.ereg);
+      for (int jj = 0; jj < (1 << R); ++jj) {
+        uint32_t xr = 0;
+        for (int t2 = 0; t2 < R; ++t2)
+          if ((jj >> t2) & 1) xr |= 1u << ord[8 + t2];
+        int s2 = 0;
+        for (int sc = 0; sc < o.nsh; ++sc) s2 += __builtin_popcount(xr & (xr >> o.sh_d[sc]) & o.sh_m[sc]);
+        const int e = (__builtin_popcount(xr & o.tmask) + 4 * s2) & 7;
+        o.ereg[jj / 8] |= (uint32_t)e << (4 * (jj % 8));
+      }
+      for (int t2 = 0; t2 < 8; ++t2) o.pq[t2] = 0xFF;
+      for (int t2 = 0; t2 < R; ++t2) {
+        const int q = ord[8 + t2];
+        for (int sc = 0; sc < o.nsh; ++sc) {
+          const int d = (int)o.sh_d[sc];
+          int partner = -1;
+          if ((o.sh_m[sc] >> q) & 1u) partner = q + d;                      // pair (q, q + d)
+          if (q - d >= 0 && ((o.sh_m[sc] >> (q - d)) & 1u)) partner = q - d;  // pair (q - d, q)
+          if (partner >= 0 && !((regmask >> partner) & 1u)) o.pq[t2] = (uint8_t)partner;
+        }
+      }
+    };
     for (size_t t = i; t < j; ++t) {
       OpRec o = seq[t];
       if (o.type == OP_GATE) {
+        const int cur = rank_of[o.q];
+        // exchange only when the rest of the pass has clearly more gates on the
+        // qubits coming in (the warp ranks) than on those going out (which would
+        // bring them back): each exchange costs about one warp-rank gate
+        int in_cnt = 0, out_cnt = 0;
+        if (nsw > 0 && cur >= 5 && cur < 5 + nsw)
+          for (size_t u = t; u < j; ++u) {
+            if (seq[u].type != OP_GATE) continue;
+            const int ru = rank_of[seq[u].q];
+            if (ru >= 5 && ru < 5 + nsw) ++in_cnt;
+            if (ru >= 10 && ru < 10 + nsw) ++out_cnt;
+          }
+        if (nsw > 0 && cur >= 5 && cur < 5 + nsw && in_cnt >= out_cnt + 2) {
+          OpRec sw;
+          memset(&sw, 0, sizeof sw);
+          sw.type = OP_SWAP;
+          for (int m = 0; m < nsw; ++m) std::swap(ord[5 + m], ord[10 + m]);
+          for (int t2 = 0; t2 < k; ++t2) rank_of[ord[t2]] = t2;
+          for (int t2 = 0; t2 < 8; ++t2) sw.tq[t2] = (uint8_t)ord[t2];
+          ops.push_back(sw);
+          ++p.warp_gates;  // needs the shared-memory slots
+        }
         o.lq = rank_of[o.q];
+        o.lq0 = rank0[o.q];
         if (k >= 8 && o.lq >= 5 && o.lq < 8) ++p.warp_gates;
         if (o.kind == 1 || o.kind == 2)
           ++n_xy;
@@ -446,44 +508,18 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
         else
           ++p.general_gates;
       } else {
-        p.phase_op = (int)(t - i);
+        if (R > 0) fill_diag_tables(o);
+        p.phase_op = (int)(ops.size() - (size_t)p.op_begin);
       }
       ops.push_back(o);
     }
+    p.op_count = (int)(ops.size() - (size_t)p.op_begin);
+    // stores use the map after the last exchange
+    if (p.vec4)
+      for (int t2 = 0; t2 < k; ++t2) p.sorder[t2] = (uint8_t)ord[t2];
     p.scale = (float)std::ldexp(n_xy + n_h == 0 ? 1.0 : ((n_xy + n_h) & 1 ? 0.70710678118654752440 : 1.0),
                                 -((n_xy + n_h) / 2));
     p.phase_e = n_xy & 7;
-    // register-part tables of the diagonal ops for the register-blocked sweep
-    if (k >= 8 && low == 5) {
-      const int R = k - 8;
-      uint32_t regmask = 0;
-      for (int t2 = 0; t2 < R; ++t2) regmask |= 1u << p.order[8 + t2];
-      for (size_t oi = (size_t)p.op_begin; oi < ops.size(); ++oi) {
-        OpRec& o = ops[oi];
-        if (o.type != OP_DIAG) continue;
-        memset(o.ereg, 0, sizeof o.ereg);
-        for (int jj = 0; jj < (1 << R); ++jj) {
-          uint32_t xr = 0;
-          for (int t2 = 0; t2 < R; ++t2)
-            if ((jj >> t2) & 1) xr |= 1u << p.order[8 + t2];
-          int s2 = 0;
-          for (int sc = 0; sc < o.nsh; ++sc) s2 += __builtin_popcount(xr & (xr >> o.sh_d[sc]) & o.sh_m[sc]);
-          const int e = (__builtin_popcount(xr & o.tmask) + 4 * s2) & 7;
-          o.ereg[jj / 8] |= (uint32_t)e << (4 * (jj % 8));
-        }
-        for (int t2 = 0; t2 < 8; ++t2) o.pq[t2] = 0xFF;
-        for (int t2 = 0; t2 < R; ++t2) {
-          const int q = p.order[8 + t2];
-          for (int sc = 0; sc < o.nsh; ++sc) {
-            const int d = (int)o.sh_d[sc];
-            int partner = -1;
-            if ((o.sh_m[sc] >> q) & 1u) partner = q + d;                      // pair (q, q + d)
-            if (q - d >= 0 && ((o.sh_m[sc] >> (q - d)) & 1u)) partner = q - d;  // pair (q - d, q)
-            if (partner >= 0 && !((regmask >> partner) & 1u)) o.pq[t2] = (uint8_t)partner;
-          }
-        }
-      }
-    }
     passes.push_back(p);
     first = false;
     i = j;
@@ -500,7 +536,7 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
   plan.n_u = b * c.C;
   plan.n_l = c.n - plan.n_u;
   if (plan.n_u > 32 || plan.n_l > 32) return "each half must have at most 32 qubits";
-  plan.fuse_qubits = fuse_qubits > 0 ? fuse_qubits : 12;
+  plan.fuse_qubits = fuse_qubits > 0 ? fuse_qubits : 13;
   if (plan.fuse_qubits < 4 || plan.fuse_qubits > 13) return "fuse_qubits must be in 4..13";
   const int nu = plan.n_u;
   // E_int: CZs with one endpoint in each half, numbered by (layer, upper qubit)

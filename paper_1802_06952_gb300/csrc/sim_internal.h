@@ -30,7 +30,10 @@ struct Circuit {
 // ---------------------------------------------------------------------------
 // Device op records of the fused complex64 sweeps and the plain complex128 path
 // ---------------------------------------------------------------------------
-enum OpType : int { OP_GATE = 0, OP_DIAG = 1 };
+// OP_SWAP (register-blocked sweep only): exchange the data of warp ranks 5+m with
+// register ranks 10+m (m < min(3, R-2)) so that the qubits at those warp ranks
+// become register qubits; the staged sweep ignores it (its layout never moves).
+enum OpType : int { OP_GATE = 0, OP_DIAG = 1, OP_SWAP = 2 };
 constexpr int kMaxShift = 6;   // CZ shift classes per diagonal op
 constexpr int kMaxCutSlots = 16;
 
@@ -63,6 +66,15 @@ struct OpRec {
   //   pq[r]: the non-register CZ partner qubit of register rank r (0xFF: none)
   uint32_t ereg[4];
   uint8_t pq[8];
+  // register-blocked sweep, per op with the rank -> qubit map at that op:
+  //   GATE: lq is the current rank of q, lq0 its rank in the pass's initial order
+  //         (the staged sweep's layout)
+  //   DIAG: rq[r] the qubit at register rank 8 + r, regmask their mask
+  //   SWAP: tq[r] the qubit at thread rank r (r < 8) after the exchange
+  int32_t lq0;
+  uint32_t regmask;
+  uint8_t rq[8];
+  uint8_t tq[8];
 };
 
 // At most this many ops per fused pass (the register-blocked sweep copies a pass's

@@ -148,8 +148,10 @@ __global__ void __launch_bounds__(256) sweep_c64_kernel(SweepArgs a) {
   __syncthreads();
   for (int o = 0; o < a.op_count; ++o) {
     const OpRec* op = a.ops + o;
-    if (__ldg(&op->type) == OP_GATE) {
-      const int lq = __ldg(&op->lq);
+    const int type = __ldg(&op->type);
+    if (type == OP_SWAP) continue;  // layout exchanges of the register-blocked sweep
+    if (type == OP_GATE) {
+      const int lq = __ldg(&op->lq0);
       const float2 m00 = make_float2(__ldg(&op->m[0]), __ldg(&op->m[1]));
       const float2 m01 = make_float2(__ldg(&op->m[2]), __ldg(&op->m[3]));
       const float2 m10 = make_float2(__ldg(&op->m[4]), __ldg(&op->m[5]));

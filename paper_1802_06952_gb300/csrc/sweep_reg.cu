@@ -248,16 +248,27 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
   uint32_t base = 0;
   for (uint32_t i = 0; i < nb_log; ++i)
     if ((g >> i) & 1u) base |= 1u << a.nonlocal[i];
-  // storage-order address of this thread's elements: st | sreg(j)
-  uint32_t st = base;
+  // storage-order address of this thread's elements: st | sreg(j) (stores, and
+  // loads outside vec4); vec4 loads use the pass's initial compute order: lt | lreg(j)
+  uint32_t st = base, lt = base;
 #pragma unroll
   for (int r = 0; r < 8; ++r)
-    if ((t >> r) & 1) st |= 1u << a.spos[r];
+    if ((t >> r) & 1) {
+      st |= 1u << a.spos[r];
+      lt |= 1u << a.cpos[r];
+    }
   auto sreg = [&](int j) {
     uint32_t o = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r)
       if ((j >> r) & 1) o |= 1u << a.spos[8 + r];
+    return o;
+  };
+  auto lreg = [&](int j) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+      if ((j >> r) & 1) o |= 1u << a.cpos[8 + r];
     return o;
   };
   float2 v[NE];
@@ -269,7 +280,7 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
     for (int j = 0; j < NE; ++j) v[j] = make_float2((st | sreg(j)) == 0 ? 1.f : 0.f, 0.f);
   } else if (R >= 2 && a.vec4) {
 #pragma unroll
-    for (int j = 0; j < NE; j += 4) load_run4(src + (st | sreg(j)), v[j], v[j + 1], v[j + 2], v[j + 3]);
+    for (int j = 0; j < NE; j += 4) load_run4(src + (lt | lreg(j)), v[j], v[j + 1], v[j + 2], v[j + 3]);
   } else {
 #pragma unroll
     for (int j = 0; j < NE; ++j) v[j] = src[st | sreg(j)];
@@ -325,11 +336,33 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
 #pragma unroll
   for (int r = 0; r < 8; ++r)
     if ((t >> r) & 1) xt |= 1u << a.cpos[r];
-  uint32_t regmask = 0;
-#pragma unroll
-  for (int r = 0; r < R; ++r) regmask |= 1u << a.cpos[8 + r];
   for (int o = 0; o < a.op_count; ++o) {
     const OpRec* op = s_ops + o;
+    if (op->type == OP_SWAP) {
+      // exchange warp ranks 5+m with register ranks 10+m (m < NSW): the element at
+      // (t, j) afterwards is the one at t with warp bits from j's bits 2.., and j
+      // with those bits from t's warp bits (reads conflict-free: for fixed j a
+      // warp reads 32 consecutive slots)
+      constexpr int NSW = R - 2 < 3 ? (R - 2 > 0 ? R - 2 : 0) : 3;
+      if constexpr (NSW > 0) {
+        constexpr int MS = (1 << NSW) - 1;
+#pragma unroll
+        for (int j = 0; j < NE; ++j) xs[j * 256 + t] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NE; ++j) {
+          const int old_t = (t & ~(MS << 5)) | (((j >> 2) & MS) << 5);
+          const int old_j = (j & ~(MS << 2)) | (((t >> 5) & MS) << 2);
+          v[j] = xs[old_j * 256 + old_t];
+        }
+        __syncthreads();
+        xt = base;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          if ((t >> r) & 1) xt |= 1u << op->tq[r];
+      }
+      continue;
+    }
     if (op->type == OP_GATE) {
       const int lq = op->lq;
       const int kind = op->kind;
@@ -380,7 +413,7 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
         et += 4 * __popc(xt & d.zmask);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-          const uint32_t qb = 1u << a.cpos[8 + r];
+          const uint32_t qb = 1u << op->rq[r];
           if (d.zmask & qb) B ^= 1u << r;
           if (d.pmask & qb) {
             pm_r |= 1u << r;
@@ -389,7 +422,7 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
         }
         if (d.pmask) {
           proj = true;
-          keep_t = (xt & d.pmask & ~regmask) == (d.pval & ~regmask);
+          keep_t = (xt & d.pmask & ~op->regmask) == (d.pval & ~op->regmask);
         }
       }
       // Exponents of 8 elements at a time, one 4-bit field per element (element
@@ -515,7 +548,11 @@ cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s) {
   uint32_t seen_c = 0, seen_s = 0;
   int srank[32];
   for (int q = 0; q < 32; ++q) srank[q] = -1;
-  if (L.vec4 && (L.k < 10 || L.transpose || L.order[8] != 0 || L.order[9] != 1)) return cudaErrorInvalidValue;
+  // vec4: runs of 4 amplitudes on register bits 0, 1 in both the load (initial)
+  // and the store (final) order
+  if (L.vec4 && (L.k < 10 || L.transpose || L.order[8] != 0 || L.order[9] != 1 || L.sorder[8] != 0 ||
+                 L.sorder[9] != 1))
+    return cudaErrorInvalidValue;
   for (int r = 0; r < L.k; ++r) {
     const int qc = L.order[r], qs = L.sorder[r];
     if (qc >= L.n || qs >= L.n || (seen_c & (1u << qc)) || (seen_s & (1u << qs))) return cudaErrorInvalidValue;
@@ -529,7 +566,7 @@ cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s) {
     a.swz[r] = L.swz[r];
   }
   if (seen_c != seen_s) return cudaErrorInvalidValue;
-  if (!L.transpose)
+  if (!L.transpose && !L.vec4)
     for (int r = 0; r < L.k; ++r)
       if (L.order[r] != L.sorder[r]) return cudaErrorInvalidValue;
   for (int r = 0; r < L.k; ++r) {

@@ -67,7 +67,7 @@ def test_batch_fixed_choices(reference, contraction):
         check(st, sub, reference)
         for i, (R, C, d, seed, cut) in enumerate(DESCS):
             info, ms = sim.sim_batch_info(b, i)
-            assert info["n"] == R * C and info["c"] == cs[i] and info["fuse"] == 12 and ms == 0
+            assert info["n"] == R * C and info["c"] == cs[i] and info["fuse"] == 13 and ms == 0
     finally:
         sim.sim_destroy_batch(b)
 
