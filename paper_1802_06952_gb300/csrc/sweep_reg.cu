@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
       // (t, j) afterwards is the one at t with warp bits from j's bits 2.., and j
       // with those bits from t's warp bits (reads conflict-free: for fixed j a
       // warp reads 32 consecutive slots)
-      constexpr int NSW = R - 2 < 3 ? (R - 2 > 0 ? R - 2 : 0) : 3;
+      constexpr int NSW = R >= 5 ? 3 : 0;  // the planner exchanges only at k = 13
       if constexpr (NSW > 0) {
         constexpr int MS = (1 << NSW) - 1;
 #pragma unroll
