@@ -10,8 +10,9 @@ Contents
               (Supplementary A, Eqs. 3-8; Section 2.1, Eq. 1)
   oracle.c    plain FP64 state-vector evolution (Supplementary A, Eq. 4) and the
               cut-and-sum reconstruction (Supplementary A, Eq. 8)
-  this file   ctypes binding, the amplitude selection draw, and the FP64
-              statistics of Section 3 (Eq. 7)
+  this file   ctypes binding, the amplitude selection draw, the FP64
+              statistics of Section 3 (Eq. 7), and Born-rule sampling of
+              measurement outcomes with the cross-entropy statistics
 
 Parity status: every function here is pinned by tests under ``tests/`` that do
 not call the oracle to make their expected values (brute-force Kronecker
@@ -217,3 +218,75 @@ def ks_from_hist(hist):
     edges = np.arange(1, KS_BINS + 1) / KS_BINS
     emp = np.cumsum(hist) / tot
     return float(np.max(np.abs(emp - edges)))
+
+
+# ---------------------------------------------------------------------------
+# Measurement outcomes (Section 3: "measurement outcomes of the full vector space
+# can be extracted"): Born-rule samples of a block of amplitudes, and the
+# cross-entropy statistics of the samples against the distribution of Eq. 7.
+# ---------------------------------------------------------------------------
+EULER_GAMMA = 0.57721566490153286061
+
+
+def splitmix64_at(seed, counters):
+    """Outputs c of the splitmix64 stream seeded with `seed` (c = 0 is the first
+    output): state_c = seed + (c + 1) * 0x9E3779B97F4A7C15 mod 2^64, then the
+    published finaliser (shifts 30, 27, 31; multipliers 0xBF58476D1CE4E5B9,
+    0x94D049BB133111EB), vectorised over the counters."""
+    c = np.asarray(counters, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = np.uint64(seed & 0xFFFFFFFFFFFFFFFF) + (c + np.uint64(1)) * np.uint64(0x9E3779B97F4A7C15)
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def born_proposals(seed, count, c_begin, c_end):
+    """Proposal c of the rejection sampler: index i_c = r_{2c} mod count and
+    uniform u_c = (r_{2c+1} >> 11) * 2^-53 in [0, 1), from the counter-based
+    splitmix64 stream r seeded with `seed`."""
+    c = np.arange(c_begin, c_end, dtype=np.uint64)
+    r_i = splitmix64_at(seed, np.uint64(2) * c)
+    r_u = splitmix64_at(seed, np.uint64(2) * c + np.uint64(1))
+    i = r_i % np.uint64(count)
+    u = (r_u >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return i, u
+
+
+def born_sample(amps, seed, n_samples, max_proposals, batch=1 << 20):
+    """Born-rule samples over a block of amplitudes by rejection sampling: with
+    p = |A|^2 in FP64 and p_max its largest value over the block, proposal c (see
+    born_proposals) is accepted when u_c * p_max < p_{i_c}.  Accepted i follow
+    p / sum(p) over the block (the Born rule restricted to the block).
+    Returns (indices, proposal ordinals, p_max) of the first n_samples accepted
+    proposals among the first max_proposals."""
+    a = np.asarray(amps).astype(np.complex128).ravel()
+    p = a.real * a.real + a.imag * a.imag
+    pmax = float(p.max())
+    idx, ords = [], []
+    got = 0
+    c0 = 0
+    while got < n_samples and c0 < max_proposals:
+        c1 = min(max_proposals, c0 + batch)
+        i, u = born_proposals(seed, p.size, c0, c1)
+        acc = np.nonzero(u * pmax < p[i.astype(np.int64)])[0]
+        take = acc[: n_samples - got]
+        idx.append(i[take])
+        ords.append(take.astype(np.uint64) + np.uint64(c0))
+        got += take.size
+        c0 = c1
+    idx = np.concatenate(idx) if idx else np.zeros(0, np.uint64)
+    ords = np.concatenate(ords) if ords else np.zeros(0, np.uint64)
+    return idx, ords, pmax
+
+
+def cross_entropy(p_samples, n_qubits):
+    """Cross-entropy statistics of samples x_s with probabilities p(x_s), w = 2^n p:
+    linear  mean(w) - 1
+    log     mean(ln w) + gamma
+    Under Eq. 7 (alpha = 1, w exponentially distributed) a sample drawn by the
+    Born rule has w with density w e^{-w}, so E[w] = 2 and E[ln w] = 1 - gamma
+    (both statistics 1); a uniform sample has E[w] = 1 and E[ln w] = -gamma (both
+    0)."""
+    w = np.asarray(p_samples, dtype=np.float64) * math.ldexp(1.0, n_qubits)
+    return float(w.mean() - 1.0), float(np.log(w).mean() + EULER_GAMMA)
