@@ -274,6 +274,31 @@ int sim_profile_enable(int on);
 int sim_profile_read(double* ms_out, uint64_t* instances_out, uint64_t* launches_out,
                      uint64_t* bytes_out, int reset);
 
+/* Born-rule samples of measurement outcomes (Section 3: measurement outcomes of the
+ * full vector space) from a block of amplitudes, by rejection sampling with a
+ * measured bound, and their cross-entropy statistics against Eq. 7.
+ *   amps_dev       device array of count complex64 amplitudes (for example the
+ *                  output of sim_amplitudes; with no selection its flat index is
+ *                  the bitstring x = x_u + 2^{n_u} x_l)
+ *   n_qubits       n of w = 2^n |A|^2
+ *   seed           proposal c draws i_c = r_{2c} mod count and u_c =
+ *                  (r_{2c+1} >> 11) 2^-53 from the counter-based splitmix64 stream r
+ *                  of the seed (output c: state seed + (c+1) 0x9E3779B97F4A7C15,
+ *                  then the published finaliser); it is accepted when
+ *                  u_c p_max < p_{i_c}, p = |A|^2 in FP64, p_max the block's maximum
+ *   n_samples      samples wanted; max_proposals caps the proposals drawn
+ *   idx_out        host array of n_samples: the accepted indices, in proposal order
+ *   ordinal_out    host array of n_samples (or NULL): the proposal number c of each
+ *   xeb_out        {mean w - 1, mean ln w + Euler's gamma, 2^n p_max}: both
+ *                  statistics are 1 for Born samples of Eq. 7 (alpha = 1) and 0 for
+ *                  uniform samples
+ *   n_out          samples produced (fewer than n_samples if max_proposals ran out)
+ * The accepted indices follow p / sum(p) over the block.  Returns after the work
+ * has finished.  SIM_EINVAL for empty or NULL arguments. */
+int sim_born_sample(const void* amps_dev, uint64_t count, int n_qubits, uint64_t seed, uint64_t n_samples,
+                    uint64_t max_proposals, uint64_t* idx_out, uint64_t* ordinal_out, double xeb_out[3],
+                    uint64_t* n_out, void* stream);
+
 /* ---- Batches of circuits ------------------------------------------------------
  * Many circuits of different sizes and cuts, each evaluated in full (all copies,
  * all 2^n amplitudes) into one output buffer that the circuits reuse in turn.  The

@@ -33,7 +33,7 @@ EXPORTS = (
     "sim_destroy_cut", "sim_destroy_halves", "sim_last_error", "sim_version",
     "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc", "sim_amplitudes_stats",
     "sim_evolve_halves_list", "sim_plan_levels", "sim_batch_create", "sim_batch_run", "sim_batch_results",
-    "sim_batch_info", "sim_destroy_batch",
+    "sim_batch_info", "sim_destroy_batch", "sim_born_sample",
 )
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -92,6 +92,8 @@ def lib():
         "sim_batch_results": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_double), vp]),
         "sim_batch_info": (ctypes.c_int, [vp, ctypes.c_int, i32p, ctypes.POINTER(ctypes.c_double)]),
         "sim_destroy_batch": (None, [vp]),
+        "sim_born_sample": (ctypes.c_int, [vp, u64, ctypes.c_int, u64, u64, u64, u64p, u64p,
+                                           ctypes.POINTER(ctypes.c_double), u64p, vp]),
         "sim_amplitudes": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, vp, vp]),
         "sim_stats": (ctypes.c_int, [vp, ctypes.c_int, u64, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                      u64p, vp]),
@@ -278,6 +280,22 @@ def sim_batch_info(batch, i):
     ms = ctypes.c_double()
     _check(lib().sim_batch_info(batch, i, info.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), ctypes.byref(ms)))
     return dict(zip(("n", "c", "fuse", "single_cta", "group"), (int(x) for x in info))), ms.value
+
+
+def sim_born_sample(amps, n_qubits, seed, n_samples, max_proposals, stream=None):
+    """Born-rule samples of a device block of complex64 amplitudes (torch tensor or
+    pointer with amps.numel()): returns (indices, proposal ordinals, xeb) where xeb =
+    [linear, log, 2^n p_max]."""
+    count = amps.numel()
+    idx = np.zeros(n_samples, dtype=np.uint64)
+    ords = np.zeros(n_samples, dtype=np.uint64)
+    xeb = (ctypes.c_double * 3)()
+    n = ctypes.c_uint64()
+    P = ctypes.POINTER(ctypes.c_uint64)
+    _check(lib().sim_born_sample(_ptr(amps), count, n_qubits, seed, n_samples, max_proposals,
+                                 idx.ctypes.data_as(P), ords.ctypes.data_as(P), xeb, ctypes.byref(n),
+                                 _stream(stream)))
+    return idx[: n.value], ords[: n.value], np.array(xeb[:], dtype=np.float64)
 
 
 def sim_destroy_batch(batch):
