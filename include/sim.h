@@ -77,12 +77,18 @@ typedef struct sim_halves_s* sim_halves;
  *   cut_row      b, the row the CZ patterns 7 and 8 straddle (0 => rows / 2)
  *   gate_list    optional canonical gate-list text ("circuit R C depth seed" then
  *                one "t NAME q [q2]" line per gate, NAME in H X2 Y2 T CZ); when not
- *                NULL it replaces the generator. */
+ *                NULL it replaces the generator.
+ *   rule_t_in_pool  0: a qubit's first gate after H is T and later ones are X^1/2
+ *                or Y^1/2 (top bit of the next splitmix64 output); 1: later ones are
+ *                uniform over {X^1/2, Y^1/2, T} ((output >> 32) mod 3), a variant
+ *                nearer the T share the paper reports (Sec. 3, Fig. 4); its exact
+ *                rule is not printed in the paper. */
 typedef struct {
   int rows, cols, depth;
   uint64_t seed;
   int cut_row;
   const char* gate_list;
+  int rule_t_in_pool;
 } sim_circuit_desc;
 
 /* Tuning knobs; pass NULL for defaults.  Zero fields mean "choose automatically".

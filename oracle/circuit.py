@@ -69,11 +69,15 @@ def pattern_couplers(R, C, b, p):
     return out
 
 
-def generate(R, C, depth, seed, b=None):
+def generate(R, C, depth, seed, b=None, t_in_pool=False):
     """Gate list [(t, name, q) or (t, 'CZ', q1, q2)] of a random grid circuit.
 
     ``b`` is the cut row used to place patterns 5-8; by default b = R // 2.
-    Gates within a layer are ordered by their first qubit.
+    Gates within a layer are ordered by their first qubit.  A qubit gets a gate
+    in layer t >= 2 when it was in a CZ at t - 1 and is not at t: its first such
+    gate is T; later ones are X2 / Y2 by the top bit of the next splitmix64
+    output, or with ``t_in_pool`` uniform over X2, Y2, T by (output >> 32) mod 3
+    (a variant nearer the paper's T share; the paper does not print its rule).
     """
     if b is None:
         b = R // 2
@@ -100,7 +104,11 @@ def generate(R, C, depth, seed, b=None):
                             had_first[q] = True
                             layer.append((t, "T", q))
                         else:
-                            name = "Y2" if (rng.next() >> 63) & 1 else "X2"
+                            r = rng.next()
+                            if t_in_pool:
+                                name = ("X2", "Y2", "T")[(r >> 32) % 3]
+                            else:
+                                name = "Y2" if (r >> 63) & 1 else "X2"
                             layer.append((t, name, q))
             prev_in_cz = in_cz
         layer.sort(key=lambda g: g[2])
@@ -208,9 +216,9 @@ class CutPlan:
         return dict(sorted(per.items()))
 
 
-def grid_cut(R, C, depth, seed, b=None):
+def grid_cut(R, C, depth, seed, b=None, t_in_pool=False):
     """Generate a grid circuit and cut it between rows b-1 and b (default R // 2)."""
     if b is None:
         b = R // 2
-    gates = generate(R, C, depth, seed, b)
+    gates = generate(R, C, depth, seed, b, t_in_pool)
     return gates, CutPlan(R * C, b * C, gates)

@@ -46,7 +46,8 @@ class SimError(RuntimeError):
 
 class _Desc(ctypes.Structure):
     _fields_ = [("rows", ctypes.c_int), ("cols", ctypes.c_int), ("depth", ctypes.c_int),
-                ("seed", ctypes.c_uint64), ("cut_row", ctypes.c_int), ("gate_list", ctypes.c_char_p)]
+                ("seed", ctypes.c_uint64), ("cut_row", ctypes.c_int), ("gate_list", ctypes.c_char_p),
+                ("rule_t_in_pool", ctypes.c_int)]
 
 
 class BatchOpts(ctypes.Structure):
@@ -159,8 +160,8 @@ def _opts(opts):
 # ---------------------------------------------------------------------------
 # C-ABI names
 # ---------------------------------------------------------------------------
-def sim_build_circuit(rows=0, cols=0, depth=0, seed=0, cut_row=0, gate_list=None):
-    d = _Desc(rows, cols, depth, seed, cut_row, gate_list.encode() if gate_list else None)
+def sim_build_circuit(rows=0, cols=0, depth=0, seed=0, cut_row=0, gate_list=None, t_in_pool=False):
+    d = _Desc(rows, cols, depth, seed, cut_row, gate_list.encode() if gate_list else None, int(t_in_pool))
     h = ctypes.c_void_p()
     _check(lib().sim_build_circuit(ctypes.byref(d), ctypes.byref(h)))
     return h.value
@@ -246,7 +247,7 @@ def sim_batch_create(descs, subset_idx=None, contraction=0, autotune=False, use_
     """descs: list of (rows, cols, depth, seed, cut_row); subset_idx: uint64 array
     [n_circuits, S] of flat amplitude indices (or None)."""
     n = len(descs)
-    arr = (_Desc * n)(*[_Desc(r, c, d, s, b, None) for (r, c, d, s, b) in descs])
+    arr = (_Desc * n)(*[_Desc(r, c, d, s, b, None, 0) for (r, c, d, s, b) in descs])
     S = 0
     ptr = None
     if subset_idx is not None:

@@ -738,7 +738,7 @@ int sim_build_circuit(const sim_circuit_desc* desc, sim_circuit* out) {
   if (desc->gate_list)
     err = parse_circuit(desc->gate_list, c->c);
   else
-    err = generate_circuit(desc->rows, desc->cols, desc->depth, desc->seed, desc->cut_row, c->c);
+    err = generate_circuit(desc->rows, desc->cols, desc->depth, desc->seed, desc->cut_row, c->c, desc->rule_t_in_pool);
   if (!err.empty()) {
     delete c;
     return fail(SIM_EINVAL, err);

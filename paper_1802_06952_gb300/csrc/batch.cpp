@@ -333,7 +333,8 @@ int sim_batch_create(const sim_circuit_desc* descs, int n_circuits, const uint64
       Item& it = B->items[(size_t)i];
       const sim_circuit_desc& d = descs[i];
       std::string err = d.gate_list ? parse_circuit(d.gate_list, it.circ)
-                                    : generate_circuit(d.rows, d.cols, d.depth, d.seed, d.cut_row, it.circ);
+                                    : generate_circuit(d.rows, d.cols, d.depth, d.seed, d.cut_row, it.circ,
+                                                       d.rule_t_in_pool);
       if (!err.empty()) return set_error(SIM_EINVAL, "circuit " + std::to_string(i) + ": " + err);
       it.cut_row = d.cut_row > 0 ? d.cut_row : it.circ.R / 2;
       err = build_cut_plan(it.circ, it.cut_row, kFixedFuse, it.plan);

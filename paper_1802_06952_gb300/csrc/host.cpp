@@ -55,7 +55,7 @@ static void couplers(int R, int C, int b, int p, std::vector<std::pair<int, int>
 // the CZs of pattern ((t-1) mod 8) + 1; for t >= 2 a qubit that was in a CZ at t-1
 // and is not in one at t gets T if this is its first gate after H, else X^1/2 or
 // Y^1/2 from one splitmix64 draw (top bit 1 -> Y^1/2), in (layer, qubit) order.
-std::string generate_circuit(int R, int C, int depth, uint64_t seed, int cut_row, Circuit& out) {
+std::string generate_circuit(int R, int C, int depth, uint64_t seed, int cut_row, Circuit& out, int t_in_pool) {
   if (R < 1 || C < 1 || R * C > 64 || depth < 1) return "grid must have 1..64 qubits and depth >= 1";
   const int n = R * C;
   const int b = cut_row > 0 ? cut_row : R / 2;
@@ -83,7 +83,13 @@ std::string generate_circuit(int R, int C, int depth, uint64_t seed, int cut_row
               layer.push_back({t, G_T, q, -1});
             } else {
               uint64_t r = splitmix64_next(rng);
-              layer.push_back({t, (r >> 63) ? G_Y2 : G_X2, q, -1});
+              if (t_in_pool) {
+                // the T-in-pool variant: uniform over {X^1/2, Y^1/2, T}
+                const uint64_t k3 = (r >> 32) % 3;
+                layer.push_back({t, k3 == 0 ? G_X2 : (k3 == 1 ? G_Y2 : G_T), q, -1});
+              } else {
+                layer.push_back({t, (r >> 63) ? G_Y2 : G_X2, q, -1});
+              }
             }
           }
         }

@@ -178,7 +178,7 @@ void note_launches(int phase, int count);
 void note_bytes(uint64_t h2d, uint64_t d2h);
 
 // Host logic (host.cpp)
-std::string generate_circuit(int R, int C, int depth, uint64_t seed, int cut_row, Circuit& out);
+std::string generate_circuit(int R, int C, int depth, uint64_t seed, int cut_row, Circuit& out, int t_in_pool = 0);
 std::string parse_circuit(const char* text, Circuit& out);
 std::string circuit_text(const Circuit& c);
 std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan);

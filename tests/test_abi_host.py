@@ -44,6 +44,33 @@ def test_generator_text_equals_oracle(R, C, d, seed):
         sim.sim_destroy_circuit(c)
 
 
+@pytest.mark.parametrize("R,C,d,seed", [(6, 5, 16, 0), (6, 7, 22, 4), (8, 8, 22, 0)])
+def test_t_in_pool_generator_equals_oracle(R, C, d, seed):
+    """The T-in-pool gate rule: byte-equal gate lists from both generators; the same
+    placement as the default rule (only gate names differ), and about a third of the
+    gates after each qubit's first are T."""
+    c = sim.sim_build_circuit(R, C, d, seed, 0, None, True)
+    try:
+        txt = sim.sim_circuit_text(c)
+        gates = oc.generate(R, C, d, seed, R // 2, t_in_pool=True)
+        assert txt == oc.to_text(R, C, d, seed, gates)
+    finally:
+        sim.sim_destroy_circuit(c)
+    plain = oc.generate(R, C, d, seed, R // 2)
+    assert [g[:1] + g[2:] for g in gates] == [g[:1] + g[2:] for g in plain]
+    n = R * C
+    firsts, later = set(), []
+    for g in gates:
+        if g[1] in ("X2", "Y2", "T") and g[0] >= 2:
+            if g[2] in firsts:
+                later.append(g[1])
+            else:
+                firsts.add(g[2])
+                assert g[1] == "T"
+    share = later.count("T") / len(later)
+    assert abs(share - 1 / 3) < 4 * (2 / 9 / len(later)) ** 0.5 + 0.01
+
+
 @pytest.mark.parametrize("R,C,d,seed", [(4, 4, 10, 0), (6, 5, 16, 1), (6, 7, 22, 0), (8, 8, 22, 0), (8, 7, 23, 0)])
 def test_cut_list_equals_oracle(R, C, d, seed):
     gates, plan = oc.grid_cut(R, C, d, seed, R // 2)

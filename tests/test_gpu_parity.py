@@ -421,3 +421,24 @@ def test_gpu_argument_errors():
         sim.sim_status()
     finally:
         r.close()
+
+
+def test_t_in_pool_rule_circuit():
+    """A circuit of the T-in-pool gate rule (T also after a qubit's first gate, folded
+    into that layer's combined diagonal): full 20-qubit vector vs the oracle."""
+    R, C, d, seed, b = 4, 5, 18, 3, 2
+    gates, plan = oc.grid_cut(R, C, d, seed, b, t_in_pool=True)
+    assert sum(1 for g in gates if g[1] == "T") > R * C
+    ref = oracle.statevector(R * C, gates).reshape(1 << plan.n_l, 1 << plan.n_u)
+    circ = sim.sim_build_circuit(R, C, d, seed, b, None, True)
+    cp, c, copies, nu, nl = sim.sim_cut(circ, b)
+    try:
+        for prec, kind, tol in ((sim.SIM_C64, sim.SIM_SPLIT_BF16, TOL_SPLIT),
+                                (sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN, TOL_PLAIN)):
+            h = sim.sim_evolve_halves(cp, prec, 0, copies)
+            got = amplitudes(h, kind, 1 << nl, 1 << nu).cpu().numpy()
+            sim.sim_destroy_halves(h)
+            assert rel_err(got, ref) <= tol
+    finally:
+        sim.sim_destroy_cut(cp)
+        sim.sim_destroy_circuit(circ)
