@@ -33,7 +33,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
 
-CODES = {"H": 0, "X2": 1, "Y2": 2, "T": 3, "CZ": 4, "P0": 5, "P1": 6, "Z": 7}
+CODES = {"H": 0, "X2": 1, "Y2": 2, "T": 3, "CZ": 4, "P0": 5, "P1": 6, "Z": 7, "CX": 8, "X": 9}
 
 
 def build(force=False):
@@ -76,16 +76,18 @@ def num_threads():
 
 
 def _encode(gates):
-    """Gate tuples -> int32 [ngates, 3] {code, q1, q2}; cut slots -> codes -1 / -2."""
+    """Gate tuples -> int32 [ngates, 3] {code, q1, q2}; cut slots -> codes -1 / -2 / -3."""
     rows = []
     for g in gates:
         name = g[1]
-        if name == "CZ":
-            rows.append((CODES["CZ"], g[2], g[3]))
+        if name in ("CZ", "CX"):
+            rows.append((CODES[name], g[2], g[3]))
         elif name == "CUTP":
             rows.append((-1, g[3], g[2]))
         elif name == "CUTZ":
             rows.append((-2, g[3], g[2]))
+        elif name == "CUTX":
+            rows.append((-3, g[3], g[2]))
         else:
             rows.append((CODES[name], g[2], 0))
     a = np.asarray(rows if rows else np.zeros((0, 3)), dtype=np.int32).reshape(-1, 3)

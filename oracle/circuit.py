@@ -133,7 +133,7 @@ def parse_text(text):
     gates = []
     for f in rows[1:]:
         t, name = int(f[0]), f[1]
-        if name == "CZ":
+        if name in ("CZ", "CX"):
             gates.append((t, name, int(f[2]), int(f[3])))
         else:
             gates.append((t, name, int(f[2])))
@@ -145,6 +145,8 @@ class CutPlan:
     (0 .. n_u-1) and a lower half (n_u .. n-1).  Every CZ with one endpoint in each
     half (the set E_int of its layer) is replaced by P_l on the upper endpoint and
     Q_l in {I, Z} on the lower endpoint, l being one bit l_m of the copy index.
+    A controlled X across the cut (Supplementary A, Eq. 1 with U = X) is replaced
+    by P_l on its control and X^l on its target, whichever half each is in.
     Bits are numbered by (layer, upper qubit) ascending; copy k = sum_m l_m 2^m.
     """
 
@@ -155,7 +157,7 @@ class CutPlan:
         self.lower = []         # gates on lower qubits (re-indexed); ('CUTZ', m, k-n_u)
         cz_cross = []
         for g in gates:
-            if g[1] == "CZ":
+            if g[1] in ("CZ", "CX"):
                 a, c2 = min(g[2], g[3]), max(g[2], g[3])
                 if a < n_u <= c2:
                     cz_cross.append((g[0], a, c2))
@@ -174,6 +176,20 @@ class CutPlan:
                     m = index[(t, a, c2)]
                     self.upper.append((t, "CUTP", m, a))
                     self.lower.append((t, "CUTZ", m, c2 - n_u))
+            elif g[1] == "CX":
+                qc, qt = g[2], g[3]
+                if qc < n_u and qt < n_u:
+                    self.upper.append(g)
+                elif qc >= n_u and qt >= n_u:
+                    self.lower.append((t, "CX", qc - n_u, qt - n_u))
+                else:
+                    m = index[(t, min(qc, qt), max(qc, qt))]
+                    if qc < n_u:
+                        self.upper.append((t, "CUTP", m, qc))
+                        self.lower.append((t, "CUTX", m, qt - n_u))
+                    else:
+                        self.upper.append((t, "CUTX", m, qt))
+                        self.lower.append((t, "CUTP", m, qc - n_u))
             else:
                 q = g[2]
                 if q < n_u:
@@ -205,6 +221,10 @@ class CutPlan:
                 bit = (k >> g[2]) & 1
                 if bit:
                     out.append((g[0], "Z", g[3]))
+            elif g[1] == "CUTX":
+                bit = (k >> g[2]) & 1
+                if bit:
+                    out.append((g[0], "X", g[3]))
             else:
                 out.append(g)
         return out

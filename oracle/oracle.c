@@ -22,8 +22,10 @@
  *   T   = diag(1, (1+i)/sqrt2)
  *   CZ  = diag(1, 1, 1, -1)                                    (Eq. 1 left side)
  *   P0  = diag(1, 0), P1 = diag(0, 1), Z = diag(1, -1)         (Eq. 1 right side)
+ *   CX  = controlled X, control q1, target q2; X = [[0, 1], [1, 0]]
+ *         (Supplementary A, Eq. 1 with U = X: CX = P0 (x) I + P1 (x) X)
  *
- * Gate encoding (three int32 per gate): {code, q1, q2}; q2 is used by CZ only.
+ * Gate encoding (three int32 per gate): {code, q1, q2}; q2 is used by CZ and CX.
  */
 #include <complex.h>
 #include <math.h>
@@ -31,7 +33,7 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { OR_H = 0, OR_X2 = 1, OR_Y2 = 2, OR_T = 3, OR_CZ = 4, OR_P0 = 5, OR_P1 = 6, OR_Z = 7 };
+enum { OR_H = 0, OR_X2 = 1, OR_Y2 = 2, OR_T = 3, OR_CZ = 4, OR_P0 = 5, OR_P1 = 6, OR_Z = 7, OR_CX = 8, OR_X = 9 };
 
 typedef double complex cplx;
 
@@ -61,6 +63,9 @@ static void gate_matrix(int code, cplx m[4]) {
     case OR_Z:
       m[0] = 1; m[1] = 0; m[2] = 0; m[3] = -1;
       break;
+    case OR_X:
+      m[0] = 0; m[1] = 1; m[2] = 1; m[3] = 0;
+      break;
     default:
       m[0] = 1; m[1] = 0; m[2] = 0; m[3] = 1;
   }
@@ -88,6 +93,20 @@ static void apply_cz(cplx* psi, int n, int q1, int q2) {
     if ((i & m) == m) psi[i] = -psi[i];
 }
 
+/* CX with control qc and target qt: amplitudes with bit qc set exchange the target
+ * bit (Eq. 4 for the two-qubit gate). */
+static void apply_cx(cplx* psi, int n, int qc, int qt) {
+  const int64_t dim = (int64_t)1 << n;
+  const int64_t c = (int64_t)1 << qc, t = (int64_t)1 << qt;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < dim; ++i) {
+    if (!(i & c) || (i & t)) continue;
+    const cplx a = psi[i];
+    psi[i] = psi[i | t];
+    psi[i | t] = a;
+  }
+}
+
 void or_evolve(int n, const int32_t* ops, int nops, double* psi_d, int init_zero) {
   cplx* psi = (cplx*)psi_d;
   const int64_t dim = (int64_t)1 << n;
@@ -99,6 +118,8 @@ void or_evolve(int n, const int32_t* ops, int nops, double* psi_d, int init_zero
     int code = ops[3 * g], q1 = ops[3 * g + 1], q2 = ops[3 * g + 2];
     if (code == OR_CZ) {
       apply_cz(psi, n, q1, q2);
+    } else if (code == OR_CX) {
+      apply_cx(psi, n, q1, q2);
     } else {
       cplx m[4];
       gate_matrix(code, m);
@@ -110,9 +131,10 @@ void or_evolve(int n, const int32_t* ops, int nops, double* psi_d, int init_zero
 /*
  * Reconstruction over copies k in [k_begin, k_end):
  *   out[i_l * n_sel_u + i_u] (+)= sum_k U_k[sel_u[i_u]] * L_k[sel_l[i_l]]
- * The half gate lists carry cut slots: code -1 means "P_{l_m} on q1" (upper,
- * m = q2) and code -2 means "Z^{l_m} on q1" (lower, m = q2), with
- * l_m = bit m of k (Supplementary A, Eqs. 7-8).  If accumulate is 0 the output is
+ * The half gate lists carry cut slots: code -1 means "P_{l_m} on q1" (the control
+ * side, m = q2), code -2 means "Z^{l_m} on q1" and code -3 "X^{l_m} on q1" (the
+ * target side of a cut CZ or CX), with l_m = bit m of k (Supplementary A,
+ * Eqs. 1, 7-8).  If accumulate is 0 the output is
  * cleared first.  The sum over k is taken in ascending k for every output.
  */
 static int resolve(const int32_t* tmpl, int ntmpl, uint64_t k, int32_t* out) {
@@ -124,6 +146,8 @@ static int resolve(const int32_t* tmpl, int ntmpl, uint64_t k, int32_t* out) {
       out[3 * n] = bitv ? OR_P1 : OR_P0; out[3 * n + 1] = q1; out[3 * n + 2] = 0; ++n;
     } else if (code == -2) {
       if ((k >> q2) & 1u) { out[3 * n] = OR_Z; out[3 * n + 1] = q1; out[3 * n + 2] = 0; ++n; }
+    } else if (code == -3) {
+      if ((k >> q2) & 1u) { out[3 * n] = OR_X; out[3 * n + 1] = q1; out[3 * n + 2] = 0; ++n; }
     } else {
       out[3 * n] = code; out[3 * n + 1] = q1; out[3 * n + 2] = q2; ++n;
     }
