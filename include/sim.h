@@ -76,8 +76,8 @@ typedef struct sim_halves_s* sim_halves;
  *   seed         splitmix64 seed of the X^1/2 / Y^1/2 draws
  *   cut_row      b, the row the CZ patterns 7 and 8 straddle (0 => rows / 2)
  *   gate_list    optional canonical gate-list text ("circuit R C depth seed" then
- *                one "t NAME q [q2]" line per gate, NAME in H X2 Y2 T CZ); when not
- *                NULL it replaces the generator.
+ *                one "t NAME q [q2]" line per gate, NAME in H X2 Y2 T CZ CX; CX is
+ *                "t CX control target"); when not NULL it replaces the generator.
  *   rule_t_in_pool  0: a qubit's first gate after H is T and later ones are X^1/2
  *                or Y^1/2 (top bit of the next splitmix64 output); 1: later ones are
  *                uniform over {X^1/2, Y^1/2, T} ((output >> 32) mod 3), a variant
@@ -122,8 +122,11 @@ int sim_circuit_text(sim_circuit circ, char* buf, size_t cap, size_t* len_out);
 /* Cut the circuit between rows cut_row-1 and cut_row (Section 2.1; Supplementary A,
  * Eqs. 6-8): find E_int, number the cut CZs, split the gates into two half-circuits,
  * build the copy tree (one level per layer holding cuts) and the fused pass
- * schedule.  Outputs (any may be NULL): c, 2^c, qubits per half.  Host only.
- * SIM_EUNSUPPORTED if a non-CZ gate crosses the cut or a half exceeds 32 qubits. */
+ * schedule.  A controlled X (explicit gate lists, "t CX control target") across the
+ * cut is cut the same way with U = X (Supplementary A, Eq. 1): P_l on the control,
+ * X^l on the target.  Outputs (any may be NULL): c, 2^c, qubits per half.  Host only.
+ * SIM_EUNSUPPORTED if a controlled X lies inside one half, a half exceeds 32 qubits
+ * or c exceeds 40. */
 int sim_cut(sim_circuit circ, int cut_row, sim_cut_plan* out, int* c_out,
             uint64_t* copies_out, int* n_upper_out, int* n_lower_out);
 

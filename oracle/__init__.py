@@ -115,7 +115,7 @@ def apply_gates(psi, n, gates):
 
 
 def half_state(plan, half, k):
-    """Half-state of copy k: half 0 = upper (P_l slots), half 1 = lower (Z^l slots)."""
+    """Half-state of copy k: half 0 = upper, half 1 = lower, each with its cut slots."""
     n_h = plan.n_u if half == 0 else plan.n_l
     tmpl = _encode(plan.upper if half == 0 else plan.lower)
     psi = np.zeros(1 << n_h, dtype=np.complex128)

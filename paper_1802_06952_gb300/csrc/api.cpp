@@ -779,7 +779,8 @@ int sim_cut(sim_circuit circ, int cut_row, sim_cut_plan* out, int* c_out, uint64
   std::string err = build_cut_plan(circ->c, cut_row, 0, p->p);
   if (!err.empty()) {
     delete p;
-    return fail(err.find("at most") != std::string::npos || err.find("more than") != std::string::npos
+    return fail(err.find("at most") != std::string::npos || err.find("more than") != std::string::npos ||
+                        err.find("not supported") != std::string::npos
                     ? SIM_EUNSUPPORTED
                     : SIM_EINVAL,
                 err);

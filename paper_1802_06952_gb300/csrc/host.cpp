@@ -24,7 +24,7 @@ uint64_t splitmix64_next(uint64_t& state) {
   return z ^ (z >> 31);
 }
 
-static const char* kGateName[] = {"H", "X2", "Y2", "T", "CZ"};
+static const char* kGateName[] = {"H", "X2", "Y2", "T", "CZ", "CX", "X"};
 
 // CZ couplers of pattern p (1..8) on an R x C grid whose cut lies above row b.
 // Patterns 1-4: horizontal (r,c)-(r,c+1) with (r%2, c%2) = (0,0), (1,1), (0,1), (1,0).
@@ -108,8 +108,8 @@ std::string circuit_text(const Circuit& c) {
   snprintf(buf, sizeof buf, "circuit %d %d %d %llu\n", c.R, c.C, c.depth, (unsigned long long)c.seed);
   s += buf;
   for (const Gate& g : c.gates) {
-    if (g.code == G_CZ)
-      snprintf(buf, sizeof buf, "%d CZ %d %d\n", g.t, g.q1, g.q2);
+    if (g.code == G_CZ || g.code == G_CX)
+      snprintf(buf, sizeof buf, "%d %s %d %d\n", g.t, kGateName[g.code], g.q1, g.q2);
     else
       snprintf(buf, sizeof buf, "%d %s %d\n", g.t, kGateName[g.code], g.q1);
     s += buf;
@@ -144,20 +144,21 @@ std::string parse_circuit(const char* text, Circuit& out) {
     std::string nm;
     if (!(ls >> t >> nm >> q1)) return "malformed gate line: " + line;
     int code = -1;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 6; ++i)
       if (nm == kGateName[i]) code = i;
     if (code < 0) return "unknown gate name: " + nm;
-    if (code == G_CZ && !(ls >> q2)) return "CZ needs two qubits: " + line;
+    const bool two = code == G_CZ || code == G_CX;
+    if (two && !(ls >> q2)) return nm + " needs two qubits: " + line;
     if (t < 0 || t >= out.depth) return "gate layer out of range: " + line;
     if (t < last_t) return "gates must be ordered by layer";
     last_t = (int)t;
-    if (q1 < 0 || q1 >= out.n || (code == G_CZ && (q2 < 0 || q2 >= out.n || q2 == q1)))
+    if (q1 < 0 || q1 >= out.n || (two && (q2 < 0 || q2 >= out.n || q2 == q1)))
       return "qubit out of range: " + line;
-    if (used_at[q1] == t || (code == G_CZ && used_at[q2] == t)) return "qubit used twice in one layer: " + line;
+    if (used_at[q1] == t || (two && used_at[q2] == t)) return "qubit used twice in one layer: " + line;
     used_at[q1] = (int)t;
-    if (code == G_CZ) used_at[q2] = (int)t;
-    Gate g{(int)t, code, (int)q1, (int)(code == G_CZ ? q2 : -1)};
-    if (code == G_CZ && g.q2 < g.q1) std::swap(g.q1, g.q2);
+    if (two) used_at[q2] = (int)t;
+    Gate g{(int)t, code, (int)q1, (int)(two ? q2 : -1)};
+    if (code == G_CZ && g.q2 < g.q1) std::swap(g.q1, g.q2);  // a CX keeps (control, target)
     out.gates.push_back(g);
   }
   if (!have_head) return "empty gate list";
@@ -191,12 +192,22 @@ void select_indices(int nq, uint64_t count, uint64_t& state, std::vector<uint64_
 // ---------------------------------------------------------------------------
 namespace {
 
+// A diagonal cut slot on half-local qubit q for copy bit m: P_l (z = false: the
+// upper end of a cut CZ, or the control of a cut controlled X in either half) or
+// Z^l (z = true: the lower end of a cut CZ).
+struct CutSlot {
+  int q, m;
+  bool z;
+};
+
 struct HalfGateLists {
-  // per layer: non-diagonal gates (qubit, code), T qubits, CZ pairs, cut slots (q, m)
+  // per layer: non-diagonal gates (qubit, code), T qubits, CZ pairs, diagonal cut
+  // slots, and X^l slots (q, m) on the target of a cut controlled X
   std::vector<std::vector<std::pair<int, int>>> nondiag;
   std::vector<uint32_t> tmask;
   std::vector<std::vector<std::pair<int, int>>> cz;
-  std::vector<std::vector<std::pair<int, int>>> cuts;
+  std::vector<std::vector<CutSlot>> cuts;
+  std::vector<std::vector<std::pair<int, int>>> xcuts;
 };
 
 void gate_matrix(int code, double m[8]) {
@@ -218,6 +229,11 @@ void gate_matrix(int code, double m[8]) {
       memcpy(m, v, sizeof v);
       break;
     }
+    case G_X: {  // [[0, 1], [1, 0]]
+      double v[8] = {0, 0, 1, 0, 1, 0, 0, 0};
+      memcpy(m, v, sizeof v);
+      break;
+    }
     default: {
       double v[8] = {1, 0, 0, 0, 0, 0, 1, 0};
       memcpy(m, v, sizeof v);
@@ -225,13 +241,14 @@ void gate_matrix(int code, double m[8]) {
   }
 }
 
-OpRec make_gate(int code, int q) {
+OpRec make_gate(int code, int q, int cond = -1) {
   OpRec o;
   memset(&o, 0, sizeof o);
   o.type = OP_GATE;
   o.q = q;
   o.lq = -1;
-  o.kind = code == G_X2 ? 1 : code == G_Y2 ? 2 : code == G_H ? 3 : 0;
+  o.cond = cond;
+  o.kind = code == G_X2 ? 1 : code == G_Y2 ? 2 : code == G_H ? 3 : code == G_X ? 4 : 0;
   gate_matrix(code, o.md);
   for (int i = 0; i < 8; ++i) o.m[i] = (float)o.md[i];
   return o;
@@ -239,8 +256,8 @@ OpRec make_gate(int code, int q) {
 
 // One or more DIAG ops for a layer: T mask, CZ pairs grouped by distance
 // (x & (x >> d) & mask counts pairs (a, a + d) with both bits set), cut slots.
-void make_diags(int half, uint32_t tmask, const std::vector<std::pair<int, int>>& cz,
-                const std::vector<std::pair<int, int>>& cuts, std::vector<OpRec>& out) {
+void make_diags(uint32_t tmask, const std::vector<std::pair<int, int>>& cz, const std::vector<CutSlot>& cuts,
+                std::vector<OpRec>& out) {
   std::map<int, uint32_t> by_d;
   for (auto& p : cz) {
     int a = std::min(p.first, p.second), b = std::max(p.first, p.second);
@@ -253,7 +270,6 @@ void make_diags(int half, uint32_t tmask, const std::vector<std::pair<int, int>>
     OpRec o;
     memset(&o, 0, sizeof o);
     o.type = OP_DIAG;
-    o.half = half;
     o.lq = -1;
     o.q = -1;
     if (first) o.tmask = tmask;
@@ -265,8 +281,9 @@ void make_diags(int half, uint32_t tmask, const std::vector<std::pair<int, int>>
       ++ci;
     }
     while (si < cuts.size() && o.ncut < kMaxCutSlots) {
-      o.cutq[o.ncut] = (uint8_t)cuts[si].first;
-      o.cutm[o.ncut] = (uint8_t)cuts[si].second;
+      o.cutq[o.ncut] = (uint8_t)cuts[si].q;
+      o.cutm[o.ncut] = (uint8_t)cuts[si].m;
+      if (cuts[si].z) o.cutz |= 1u << o.ncut;
       ++o.ncut;
       ++si;
     }
@@ -511,7 +528,7 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
           ++n_xy;
         else if (o.kind == 3)
           ++n_h;
-        else
+        else if (o.kind != 4)
           ++p.general_gates;
       } else {
         if (R > 0) fill_diag_tables(o);
@@ -545,9 +562,16 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
   plan.fuse_qubits = fuse_qubits > 0 ? fuse_qubits : 13;
   if (plan.fuse_qubits < 4 || plan.fuse_qubits > 13) return "fuse_qubits must be in 4..13";
   const int nu = plan.n_u;
-  // E_int: CZs with one endpoint in each half, numbered by (layer, upper qubit)
-  for (const Gate& g : c.gates)
-    if (g.code == G_CZ && g.q1 < nu && g.q2 >= nu) plan.cuts.push_back({g.t, g.q1, g.q2});
+  // E_int: CZs (and controlled X gates) with one endpoint in each half, numbered by
+  // (layer, upper qubit)
+  for (const Gate& g : c.gates) {
+    if (g.code == G_CZ && g.q1 < nu && g.q2 >= nu) plan.cuts.push_back({g.t, g.q1, g.q2, 0});
+    if (g.code == G_CX) {
+      const int a = std::min(g.q1, g.q2), b2 = std::max(g.q1, g.q2);
+      if (!(a < nu && b2 >= nu)) return "a controlled X inside one half is not supported (only across the cut)";
+      plan.cuts.push_back({g.t, a, b2, g.q1 < nu ? 1 : 2});
+    }
+  }
   std::sort(plan.cuts.begin(), plan.cuts.end(), [](const CutCZ& a, const CutCZ& b2) {
     return a.t != b2.t ? a.t < b2.t : a.h < b2.h;
   });
@@ -562,6 +586,7 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
     hl[h].tmask.assign(c.depth, 0);
     hl[h].cz.assign(c.depth, {});
     hl[h].cuts.assign(c.depth, {});
+    hl[h].xcuts.assign(c.depth, {});
   }
   for (const Gate& g : c.gates) {
     if (g.code == G_CZ) {
@@ -571,9 +596,15 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
         hl[1].cz[g.t].emplace_back(g.q1 - nu, g.q2 - nu);
       } else {
         int m = cut_index[{g.t, g.q1}];
-        hl[0].cuts[g.t].emplace_back(g.q1, m);
-        hl[1].cuts[g.t].emplace_back(g.q2 - nu, m);
+        hl[0].cuts[g.t].push_back({g.q1, m, false});
+        hl[1].cuts[g.t].push_back({g.q2 - nu, m, true});
       }
+    } else if (g.code == G_CX) {
+      const int a = std::min(g.q1, g.q2);
+      const int m = cut_index[{g.t, a}];
+      const int hc = g.q1 < nu ? 0 : 1;  // half of the control
+      hl[hc].cuts[g.t].push_back({hc ? g.q1 - nu : g.q1, m, false});
+      hl[1 - hc].xcuts[g.t].emplace_back(hc ? g.q2 : g.q2 - nu, m);
     } else {
       int h = g.q1 < nu ? 0 : 1;
       int q = h ? g.q1 - nu : g.q1;
@@ -596,7 +627,7 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
     // holding any diagonal gate (T, CZ, or cut slot)
     int plain = 0;
     for (int t = 0; t < c.depth; ++t) {
-      plain += (int)hl[h].nondiag[t].size();
+      plain += (int)hl[h].nondiag[t].size() + (int)hl[h].xcuts[t].size();
       if (hl[h].tmask[t] || !hl[h].cz[t].empty() || !hl[h].cuts[t].empty()) ++plain;
     }
     S.plain_passes = plain;
@@ -625,15 +656,16 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
       for (int t = t_begin; t <= t_end; ++t) {
         const bool own_cut_layer = (j > 0 && t == t_begin);
         if (own_cut_layer) {
-          // this level applies only the cut slots of its branch layer here
-          make_diags(h, 0, {}, hl[h].cuts[t], seq);
+          // this level applies only the cut slots of its branch layer here (the X^l
+          // slots act on qubits no other gate of the layer touches)
+          for (auto& p : hl[h].xcuts[t]) seq.push_back(make_gate(G_X, p.first, p.second));
+          make_diags(0, {}, hl[h].cuts[t], seq);
           continue;
         }
         if (!(j == 0 && t == 0 && uniform))
           for (auto& p : hl[h].nondiag[t]) seq.push_back(make_gate(p.second, p.first));
         const bool next_branch = (j + 1 < nlev && t == t_end);
-        make_diags(h, hl[h].tmask[t], hl[h].cz[t],
-                   next_branch ? std::vector<std::pair<int, int>>() : hl[h].cuts[t], seq);
+        make_diags(hl[h].tmask[t], hl[h].cz[t], next_branch ? std::vector<CutSlot>() : hl[h].cuts[t], seq);
       }
       int first_src = j == 0 ? (uniform ? SRC_UNIFORM : SRC_ZERO) : SRC_PARENT;
       split_passes(n, plan.fuse_qubits, seq, first_src, L.passes, S.ops);
@@ -645,7 +677,8 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
     plan.plain[h].assign(c.depth, PlainLayer());
     for (int t = 0; t < c.depth; ++t) {
       for (auto& p : hl[h].nondiag[t]) plan.plain[h][t].gates.push_back(make_gate(p.second, p.first));
-      make_diags(h, hl[h].tmask[t], hl[h].cz[t], hl[h].cuts[t], plan.plain[h][t].diags);
+      for (auto& p : hl[h].xcuts[t]) plan.plain[h][t].gates.push_back(make_gate(G_X, p.first, p.second));
+      make_diags(hl[h].tmask[t], hl[h].cz[t], hl[h].cuts[t], plan.plain[h][t].diags);
     }
   }
   return "";

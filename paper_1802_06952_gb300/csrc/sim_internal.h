@@ -14,7 +14,10 @@ namespace sim {
 // ---------------------------------------------------------------------------
 // Circuit IR (Supplementary A, Eq. 3: layers of single-qubit gates and CZ edges)
 // ---------------------------------------------------------------------------
-enum GateCode : int { G_H = 0, G_X2 = 1, G_Y2 = 2, G_T = 3, G_CZ = 4 };
+// G_CX: controlled X, q1 control, q2 target (only across the cut, where it becomes
+// P_l on the control and X^l on the target: Supplementary A, Eq. 1 with U = X);
+// G_X: the X of such a slot (not a gate of the circuit text)
+enum GateCode : int { G_H = 0, G_X2 = 1, G_Y2 = 2, G_T = 3, G_CZ = 4, G_CX = 5, G_X = 6 };
 
 struct Gate {
   int t, code, q1, q2;
@@ -41,18 +44,20 @@ constexpr int kMaxCutSlots = 16;
 // path) or on qubit `q` (plain path).  A DIAG is the combined diagonal of one
 // layer (Section 2.4, Eqs. 4 and 6) plus the copy-dependent cut slots:
 //   phase(x) = w^{popc(x & tmask)} * (-1)^{sum_s popc(x & (x >> sh_d[s]) & sh_m[s])}
-//   upper half:  * [bit cutq[i] of x == bit cutm[i] of the copy id]   (P_l)
-//   lower half:  * (-1)^{bit cutq[i] of x * bit cutm[i] of the copy id} (Z^l)
-// with w = e^{i pi / 4}.
+//   slot i with bit i of cutz clear:  * [bit cutq[i] of x == bit cutm[i] of the copy id]   (P_l)
+//   slot i with bit i of cutz set:    * (-1)^{bit cutq[i] of x * bit cutm[i] of the copy id} (Z^l)
+// with w = e^{i pi / 4}.  P_l sits on the upper end of a cut CZ and on the control
+// of a cut controlled X (in either half), Z^l on the lower end of a cut CZ.
 struct OpRec {
   int32_t type;
   int32_t lq;
   int32_t q;
   int32_t nsh;
   int32_t ncut;
-  int32_t half;
+  uint32_t cutz;
   uint32_t tmask;
-  int32_t kind;          // GATE: 0 general 2x2, 1 X^1/2, 2 Y^1/2, 3 H (closed-form updates)
+  int32_t kind;          // GATE: 0 general 2x2, 1 X^1/2, 2 Y^1/2, 3 H, 4 X (closed-form updates)
+  int32_t cond;          // GATE: -1, or copy bit m: applied only where l_m = 1 (X^l slot)
   uint32_t sh_d[kMaxShift];
   uint32_t sh_m[kMaxShift];
   uint8_t cutq[kMaxCutSlots];
@@ -144,6 +149,7 @@ struct PlainLayer {
 
 struct CutCZ {
   int t, h, k;  // layer, upper qubit, lower qubit (global indices)
+  int kind = 0;  // 0 CZ; 1 CX with the control in the upper half; 2 control in the lower half
 };
 
 struct CutPlan {

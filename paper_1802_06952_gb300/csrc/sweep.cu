@@ -41,7 +41,7 @@ struct DiagState {
 };
 
 // Resolve a DIAG op for one copy-tree node: the cut slots become a projector
-// (upper half: bits cutq must equal the copy bits cutm) or a Z mask (lower half).
+// (P_l slots: bits cutq must equal the copy bits cutm) or a Z mask (Z^l slots).
 __device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, DiagState& d) {
   d.tmask = __ldg(&op->tmask);
   d.nsh = __ldg(&op->nsh);
@@ -50,12 +50,12 @@ __device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, Dia
     d.sh_m[s] = __ldg(&op->sh_m[s]);
   }
   const int ncut = __ldg(&op->ncut);
-  const int half = __ldg(&op->half);
+  const uint32_t cutz = __ldg(&op->cutz);
   d.pmask = d.pval = d.zmask = 0;
   for (int i = 0; i < ncut; ++i) {
     const uint32_t qb = 1u << op->cutq[i];
     const uint32_t l = (uint32_t)((node_id >> op->cutm[i]) & 1ull);
-    if (half == 0) {
+    if (!((cutz >> i) & 1u)) {
       d.pmask |= qb;
       if (l) d.pval |= qb;
     } else if (l) {
@@ -151,6 +151,9 @@ __global__ void __launch_bounds__(256) sweep_c64_kernel(SweepArgs a) {
     const int type = __ldg(&op->type);
     if (type == OP_SWAP) continue;  // layout exchanges of the register-blocked sweep
     if (type == OP_GATE) {
+      // an X^l slot of a cut controlled X: only in the copies with l_m = 1
+      const int cond = __ldg(&op->cond);
+      if (cond >= 0 && !((ne.node_id >> cond) & 1ull)) continue;
       const int lq = __ldg(&op->lq0);
       const float2 m00 = make_float2(__ldg(&op->m[0]), __ldg(&op->m[1]));
       const float2 m01 = make_float2(__ldg(&op->m[2]), __ldg(&op->m[3]));
@@ -196,7 +199,9 @@ __global__ void plain_init_zero_kernel(double2* psi, int n, uint64_t total) {
     psi[i] = make_double2((i & mask) == 0 ? 1.0 : 0.0, 0.0);
 }
 
-__global__ void plain_gate_kernel(double2* psi, int n, int q, const OpRec* op, uint64_t npairs_total) {
+__global__ void plain_gate_kernel(double2* psi, int n, int q, const OpRec* op, const uint64_t* copy_ids,
+                                  uint64_t npairs_total) {
+  const int cond = op->cond;  // X^l slot of a cut controlled X: copies with l_m = 1 only
   const double2 m00 = make_double2(op->md[0], op->md[1]);
   const double2 m01 = make_double2(op->md[2], op->md[3]);
   const double2 m10 = make_double2(op->md[4], op->md[5]);
@@ -206,6 +211,7 @@ __global__ void plain_gate_kernel(double2* psi, int n, int q, const OpRec* op, u
   for (uint64_t t = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; t < npairs_total;
        t += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t s = t / half, p = t % half;
+    if (cond >= 0 && !((copy_ids[s] >> cond) & 1ull)) continue;
     double2* v = psi + (s << n);
     const uint64_t i0 = ((p & ~lo_mask) << 1) | (p & lo_mask);
     const uint64_t i1 = i0 | (1ull << q);
@@ -313,7 +319,7 @@ cudaError_t launch_plain_init_zero(void* psi, int n, int64_t nstates, cudaStream
 
 cudaError_t launch_plain_gate(const PlainLaunch& L, cudaStream_t s) {
   const uint64_t total = (uint64_t)L.nstates << (L.n - 1);
-  plain_gate_kernel<<<grid_for(total, 256), 256, 0, s>>>((double2*)L.psi, L.n, L.q, L.op, total);
+  plain_gate_kernel<<<grid_for(total, 256), 256, 0, s>>>((double2*)L.psi, L.n, L.q, L.op, L.copy_ids, total);
   note_launches(SIM_PHASE_PLAIN, 1);
   return cudaGetLastError();
 }

@@ -1,0 +1,28 @@
+"""Explicit test circuits shared by several test files (plain gate lists)."""
+import numpy as np
+
+from oracle import circuit as oc
+
+
+def cx_cut_circuit(seed):
+    """4x4 grid: H layer, CZ patterns, random single-qubit gates, and controlled X
+    gates across the cut (rows 1 | 2) in both directions."""
+    R, C, b, depth = 4, 4, 2, 10
+    base = oc.generate(R, C, depth, seed, b)
+    rng = np.random.default_rng(seed)
+    gates = list(base)
+    busy = {}
+    for g in base:
+        for q in g[2:]:
+            busy.setdefault(g[0], set()).add(q)
+    extra = []
+    for t in range(2, depth):
+        free = [q for q in range(R * C) if q not in busy.get(t, set())]
+        up = [q for q in free if q < b * C]
+        lo = [q for q in free if q >= b * C]
+        if up and lo:
+            qa, qb = int(rng.choice(up)), int(rng.choice(lo))
+            extra.append((t, "CX", qa, qb) if t % 2 else (t, "CX", qb, qa))
+            busy.setdefault(t, set()).update((qa, qb))
+    gates = sorted(gates + extra, key=lambda g: (g[0], g[2]))
+    return R, C, b, depth, gates

@@ -158,6 +158,31 @@ def test_plan_levels_cover_the_copy_bits(R, C, d, b):
         sim.sim_destroy_circuit(circ)
 
 
+def test_controlled_x_cuts_on_the_host():
+    """Controlled X gates across the cut count as cuts (P_l on the control, X^l on the
+    target); the cut list equals the oracle's; one inside a half is unsupported."""
+    from circuits import cx_cut_circuit
+    R, C, b, depth, gates = cx_cut_circuit(1)
+    txt = oc.to_text(R, C, depth, 0, gates)
+    c = sim.sim_build_circuit(gate_list=txt)
+    try:
+        assert sim.sim_circuit_text(c) == txt
+        plan, cc, copies, nu, nl = sim.sim_cut(c, b)
+        ref = oc.CutPlan(R * C, b * C, gates)
+        assert cc == ref.c and sim.sim_cut_list(plan, cc)[0] == [tuple(x) for x in ref.cuts]
+        sim.sim_destroy_cut(plan)
+    finally:
+        sim.sim_destroy_circuit(c)
+    bad = oc.to_text(4, 4, 3, 0, [(0, "H", 0), (1, "CX", 0, 1)])
+    c = sim.sim_build_circuit(gate_list=bad)
+    try:
+        with pytest.raises(sim.SimError) as e:
+            sim.sim_cut(c, 2)
+        assert e.value.code == sim.SIM_EUNSUPPORTED
+    finally:
+        sim.sim_destroy_circuit(c)
+
+
 def test_bad_batches_rejected_on_the_host():
     """sim_batch_create validates circuits and subset indices before any device work."""
     with pytest.raises(sim.SimError) as e:

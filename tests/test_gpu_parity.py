@@ -442,3 +442,47 @@ def test_t_in_pool_rule_circuit():
     finally:
         sim.sim_destroy_cut(cp)
         sim.sim_destroy_circuit(circ)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_controlled_x_cuts(seed):
+    """Controlled X gates across the cut (Supplementary A, Eq. 1 with U = X: P_l on
+    the control, X^l on the target, in either half): the full 16-qubit vector of the
+    split path, the plain FP64 path, both sweep kernels and a copy list, against the
+    oracle's uncut state vector."""
+    from circuits import cx_cut_circuit
+    R, C, b, depth, gates = cx_cut_circuit(seed)
+    n, n_u = R * C, b * C
+    ref = oracle.statevector(n, gates).reshape(1 << (n - n_u), 1 << n_u)
+    circ = sim.sim_build_circuit(gate_list=oc.to_text(R, C, depth, 0, gates))
+    cp, c, copies, nu, nl = sim.sim_cut(circ, b)
+    try:
+        runs = [(sim.SIM_C64, sim.SIM_SPLIT_BF16, TOL_SPLIT, {"sweep_kernel": 2}),
+                (sim.SIM_C64, sim.SIM_SPLIT_FP16, TOL_SPLIT, {"sweep_kernel": 1, "fuse_qubits": 5}),
+                (sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN, TOL_PLAIN, None)]
+        for prec, kind, tol, opts in runs:
+            h = sim.sim_evolve_halves(cp, prec, 0, copies, None, None, opts)
+            got = amplitudes(h, kind, 1 << nl, 1 << nu).cpu().numpy()
+            sim.sim_destroy_halves(h)
+            assert rel_err(got, ref) <= tol, (prec, kind)
+        # a copy list: the oracle's partial sum over those copies.  A sum of a few
+        # outer products has no averaging, so the split contraction is held to its
+        # per-product bound: each real component keeps a residual of 2^-16 of itself
+        # after hi + lo (bf16) and lo * lo is dropped, so a complex product is off by
+        # at most 3 * 2^-16 |U_k[x_u]| |L_k[x_l]|, plus the complex64 leaves' rounding.
+        gplan = oc.CutPlan(n, n_u, gates)
+        lst = np.array([copies - 1, 0, copies // 2 + 1], dtype=np.uint64)
+        part = sum(oracle.cut_amplitudes(gplan, None, None, int(k), int(k) + 1) for k in lst)
+        mag = sum(np.abs(oracle.half_state(gplan, 1, int(k)))[:, None] *
+                  np.abs(oracle.half_state(gplan, 0, int(k)))[None, :] for k in lst)
+        h = sim.sim_evolve_halves_list(cp, sim.SIM_C64, lst)
+        got = amplitudes(h, sim.SIM_SPLIT_BF16, 1 << nl, 1 << nu).cpu().numpy()
+        sim.sim_destroy_halves(h)
+        assert np.all(np.abs(got - part) <= 3 * 2.0 ** -16 * mag + 1e-6 * mag.max())
+        h = sim.sim_evolve_halves_list(cp, sim.SIM_C128_PLAIN, lst)
+        got = amplitudes(h, sim.SIM_FP64_PLAIN, 1 << nl, 1 << nu).cpu().numpy()
+        sim.sim_destroy_halves(h)
+        assert rel_err(got, part) <= TOL_PLAIN
+    finally:
+        sim.sim_destroy_cut(cp)
+        sim.sim_destroy_circuit(circ)

@@ -5,6 +5,7 @@ import numpy as np
 
 import oracle
 from oracle import circuit as oc
+from circuits import cx_cut_circuit
 
 I2 = np.eye(2)
 X = np.array([[0, 1], [1, 0]], dtype=complex)
@@ -52,30 +53,6 @@ def test_cx_against_kronecker_products():
     psi0 = np.zeros(1 << n, dtype=complex)
     psi0[0] = 1
     assert np.max(np.abs(oracle.statevector(n, gates) - u @ psi0)) < 1e-13
-
-
-def cx_cut_circuit(seed):
-    """4x4 grid: H layer, CZ patterns, random single-qubit gates, and controlled X
-    gates across the cut (rows 1 | 2) in both directions."""
-    R, C, b, depth = 4, 4, 2, 10
-    base = oc.generate(R, C, depth, seed, b)
-    rng = np.random.default_rng(seed)
-    gates = list(base)
-    busy = {}
-    for g in base:
-        for q in g[2:]:
-            busy.setdefault(g[0], set()).add(q)
-    extra = []
-    for t in range(2, depth):
-        free = [q for q in range(R * C) if q not in busy.get(t, set())]
-        up = [q for q in free if q < b * C]
-        lo = [q for q in free if q >= b * C]
-        if up and lo:
-            qa, qb = int(rng.choice(up)), int(rng.choice(lo))
-            extra.append((t, "CX", qa, qb) if t % 2 else (t, "CX", qb, qa))
-            busy.setdefault(t, set()).update((qa, qb))
-    gates = sorted(gates + extra, key=lambda g: (g[0], g[2]))
-    return R, C, b, depth, gates
 
 
 def test_cut_equals_uncut_with_controlled_x_cuts():
