@@ -528,7 +528,7 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
           ++n_xy;
         else if (o.kind == 3)
           ++n_h;
-        else if (o.kind != 4)
+        else
           ++p.general_gates;
       } else {
         if (R > 0) fill_diag_tables(o);
@@ -656,10 +656,18 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
       for (int t = t_begin; t <= t_end; ++t) {
         const bool own_cut_layer = (j > 0 && t == t_begin);
         if (own_cut_layer) {
-          // this level applies only the cut slots of its branch layer here (the X^l
-          // slots act on qubits no other gate of the layer touches)
-          for (auto& p : hl[h].xcuts[t]) seq.push_back(make_gate(G_X, p.first, p.second));
-          make_diags(0, {}, hl[h].cuts[t], seq);
+          // this level applies only the cut slots of its branch layer here.  An X^l
+          // slot becomes H Z^l H (H Z H = X, H H = I): the fused passes need no
+          // copy-dependent gate, only the diagonal slot Z^l between two H gates,
+          // whose common factor 1/2 is the same in every copy.  The X^l slots act on
+          // qubits no other gate of the layer touches.
+          std::vector<CutSlot> slots = hl[h].cuts[t];
+          for (auto& p : hl[h].xcuts[t]) {
+            seq.push_back(make_gate(G_H, p.first));
+            slots.push_back({p.first, p.second, true});
+          }
+          make_diags(0, {}, slots, seq);
+          for (auto& p : hl[h].xcuts[t]) seq.push_back(make_gate(G_H, p.first));
           continue;
         }
         if (!(j == 0 && t == 0 && uniform))

@@ -57,7 +57,8 @@ struct OpRec {
   uint32_t cutz;
   uint32_t tmask;
   int32_t kind;          // GATE: 0 general 2x2, 1 X^1/2, 2 Y^1/2, 3 H, 4 X (closed-form updates)
-  int32_t cond;          // GATE: -1, or copy bit m: applied only where l_m = 1 (X^l slot)
+  int32_t cond;          // GATE: -1, or copy bit m: applied only where l_m = 1 (the X^l slot
+                         // of the plain path; fused passes take H Z^l H instead)
   uint32_t sh_d[kMaxShift];
   uint32_t sh_m[kMaxShift];
   uint8_t cutq[kMaxCutSlots];

@@ -87,15 +87,10 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 //   [[1, -i], [-i, 1]] (X^1/2):  a0 - i a1, a1 - i a0
 //   [[1, -1], [1, 1]]  (Y^1/2):  a0 - a1,   a0 + a1
 //   [[1, 1], [1, -1]]  (H):      a0 + a1,   a0 - a1
-//   [[0, 1], [1, 0]]   (X):      a1,        a0
-// Y and H are the same on both components (packed fp32x2 additions).
+// The last two are the same on both components (packed fp32x2 additions).
 template <int KIND>
 __device__ __forceinline__ void pair_update(float2& a0, float2& a1) {
-  if (KIND == 4) {
-    const float2 b0 = a1;
-    a1 = a0;
-    a0 = b0;
-  } else if (KIND == 1) {
+  if (KIND == 1) {
     const float2 b0 = make_float2(a0.x + a1.y, a0.y - a1.x);
     a1 = make_float2(a1.x + a0.y, a1.y - a0.x);
     a0 = b0;
@@ -124,10 +119,8 @@ __device__ __forceinline__ void reg_gate_b(float2 (&v)[1 << R], int kind) {
       reg_pairs<R, B, 1>(v);
     else if (kind == 2)
       reg_pairs<R, B, 2>(v);
-    else if (kind == 3)
-      reg_pairs<R, B, 3>(v);
     else
-      reg_pairs<R, B, 4>(v);
+      reg_pairs<R, B, 3>(v);
   }
 }
 
@@ -148,9 +141,7 @@ __device__ __forceinline__ void reg_gate(float2 (&v)[1 << R], int b, int kind) {
 // as pair_update).
 template <int KIND>
 __device__ __forceinline__ float2 side_update(float2 o, float2 p, float sg) {
-  if (KIND == 4) {  // X: the partner's value on both sides
-    return p;
-  } else if (KIND == 1) {  // o - i p on both sides
+  if (KIND == 1) {  // o - i p on both sides
     return __ffma2_rn(make_float2(1.f, -1.f), make_float2(p.y, p.x), o);
   } else if (KIND == 2) {  // side 0: o - p, side 1: o + p
     return __ffma2_rn(make_float2(sg, sg), p, o);
@@ -375,8 +366,6 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
     if (op->type == OP_GATE) {
       const int lq = op->lq;
       const int kind = op->kind;
-      // an X^l slot of a cut controlled X: only in the copies with l_m = 1
-      if (op->cond >= 0 && !((ne.node_id >> op->cond) & 1ull)) continue;
       if (lq >= 8) {
         reg_gate<R>(v, lq - 8, kind);
       } else if (lq < 5) {
@@ -386,10 +375,8 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
           lane_gate_k<R, 1>(v, mask, sg);
         else if (kind == 2)
           lane_gate_k<R, 2>(v, mask, sg);
-        else if (kind == 3)
-          lane_gate_k<R, 3>(v, mask, sg);
         else
-          lane_gate_k<R, 4>(v, mask, sg);
+          lane_gate_k<R, 3>(v, mask, sg);
       } else {
         const float sg = ((t >> lq) & 1) ? 1.f : -1.f;
         const int pt = t ^ (1 << lq);
@@ -397,10 +384,8 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
           smem_gate_k<R, 1>(v, xs, t, pt, sg);
         else if (kind == 2)
           smem_gate_k<R, 2>(v, xs, t, pt, sg);
-        else if (kind == 3)
-          smem_gate_k<R, 3>(v, xs, t, pt, sg);
         else
-          smem_gate_k<R, 4>(v, xs, t, pt, sg);
+          smem_gate_k<R, 3>(v, xs, t, pt, sg);
       }
     } else {
       // exponent of w at x = xt | r(j): the thread part (T and CZ terms within xt)
