@@ -278,59 +278,70 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
   } else if (a.src == SRC_ZERO) {
 #pragma unroll
     for (int j = 0; j < NE; ++j) v[j] = make_float2((st | sreg(j)) == 0 ? 1.f : 0.f, 0.f);
-  } else if (R >= 2 && a.vec4) {
+  } else if constexpr (R >= 2) {
 #pragma unroll
     for (int j = 0; j < NE; j += 4) load_run4(src + (lt | lreg(j)), v[j], v[j + 1], v[j + 2], v[j + 3]);
   } else {
 #pragma unroll
     for (int j = 0; j < NE; ++j) v[j] = src[st | sreg(j)];
   }
-  // shared-memory slots: storage index s = t + 256 j sits at s ^ swz(s); the
-  // compute-order element (t, j) is storage index P(t) | P(j).  Byte offsets: the
-  // storage slot of (t, j) is (sb_t ^ zb(j)) + 2048 j (the swizzle touches only the
-  // low 4 slot bits, below the j bits), the compute slot cb_t ^ cb(j).
-  const uint32_t sb_t = ((uint32_t)t ^ swz_thread(a, (uint32_t)t)) << 3;
-  uint32_t zb_r[R > 0 ? R : 1], cb_r[R > 0 ? R : 1];
+  // Storage <-> compute order through shared memory, for passes with fewer than
+  // two register bits (wider passes load and store 256-bit runs in compute order
+  // and never transpose, so none of this is live across their ops): storage index
+  // s = t + 256 j sits at s ^ swz(s); the compute-order element (t, j) is storage
+  // index P(t) | P(j).  Byte offsets: the storage slot of (t, j) is
+  // (sb_t ^ zb(j)) + 2048 j (the swizzle touches only the low 4 slot bits, below
+  // the j bits), the compute slot cb_t ^ cb(j).
+  auto transpose = [&](bool to_compute) {
+    const uint32_t sb_t = ((uint32_t)t ^ swz_thread(a, (uint32_t)t)) << 3;
+    uint32_t zb_r[R > 0 ? R : 1], cb_r[R > 0 ? R : 1];
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    zb_r[r] = (uint32_t)a.swz[8 + r] << 3;
-    cb_r[r] = ((1u << a.c2s[8 + r]) ^ a.cswz[8 + r]) << 3;
-  }
-  auto sbyte = [&](int j) {
-    uint32_t z = 0;
+    for (int r = 0; r < R; ++r) {
+      zb_r[r] = (uint32_t)a.swz[8 + r] << 3;
+      cb_r[r] = ((1u << a.c2s[8 + r]) ^ a.cswz[8 + r]) << 3;
+    }
+    auto sbyte = [&](int j) {
+      uint32_t z = 0;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      if ((j >> r) & 1) z ^= zb_r[r];
-    return (sb_t ^ z) + ((uint32_t)j << 11);
-  };
-  uint32_t cb_t = 0;
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-    if ((t >> r) & 1) cb_t |= 1u << a.c2s[r];
-  {
-    uint32_t z = 0;
+      for (int r = 0; r < R; ++r)
+        if ((j >> r) & 1) z ^= zb_r[r];
+      return (sb_t ^ z) + ((uint32_t)j << 11);
+    };
+    uint32_t cb_t = 0, z = 0;
 #pragma unroll
     for (int r = 0; r < 8; ++r)
-      if ((t >> r) & 1) z ^= a.cswz[r];
+      if ((t >> r) & 1) {
+        cb_t |= 1u << a.c2s[r];
+        z ^= a.cswz[r];
+      }
     cb_t = (cb_t ^ z) << 3;
-  }
-  auto cbyte = [&](int j) {
-    uint32_t o = cb_t;
+    auto cbyte = [&](int j) {
+      uint32_t o = cb_t;
 #pragma unroll
-    for (int r = 0; r < R; ++r)
-      if ((j >> r) & 1) o ^= cb_r[r];
-    return o;
+      for (int r = 0; r < R; ++r)
+        if ((j >> r) & 1) o ^= cb_r[r];
+      return o;
+    };
+    char* xsb = (char*)xs;
+    if (to_compute) {
+#pragma unroll
+      for (int j = 0; j < NE; ++j) *(float2*)(xsb + sbyte(j)) = v[j];
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < NE; ++j) v[j] = *(const float2*)(xsb + cbyte(j));
+      __syncthreads();
+    } else {
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < NE; ++j) *(float2*)(xsb + cbyte(j)) = v[j];
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < NE; ++j) v[j] = *(const float2*)(xsb + sbyte(j));
+    }
   };
-  char* xsb = (char*)xs;
   __syncthreads();  // s_omega, s_ops
-  if (a.transpose) {
-#pragma unroll
-    for (int j = 0; j < NE; ++j) *(float2*)(xsb + sbyte(j)) = v[j];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NE; ++j) v[j] = *(const float2*)(xsb + cbyte(j));
-    __syncthreads();
-  }
+  if constexpr (R < 2)
+    if (a.transpose) transpose(true);
   // compute-order global index bits for the diagonal ops
   uint32_t xt = base;
 #pragma unroll
@@ -474,21 +485,15 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
       }
     }
   }
-  if (a.transpose) {
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NE; ++j) *(float2*)(xsb + cbyte(j)) = v[j];
-    __syncthreads();
-#pragma unroll
-    for (int j = 0; j < NE; ++j) v[j] = *(const float2*)(xsb + sbyte(j));
-  }
+  if constexpr (R < 2)
+    if (a.transpose) transpose(false);
   if (a.phase_op < 0 && a.phase_e != 0) {
     const float2 w = s_omega[a.phase_e & 7];
 #pragma unroll
     for (int j = 0; j < NE; ++j) v[j] = cmul(v[j], w);
   }
   const float2 sc2 = make_float2(a.scale, a.scale);
-  if (R >= 2 && a.vec4) {
+  if constexpr (R >= 2) {
 #pragma unroll
     for (int j = 0; j < NE; j += 4)
       store_run4(dst + (st | sreg(j)), __fmul2_rn(v[j], sc2), __fmul2_rn(v[j + 1], sc2), __fmul2_rn(v[j + 2], sc2),
@@ -550,8 +555,9 @@ cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s) {
   for (int q = 0; q < 32; ++q) srank[q] = -1;
   // vec4: runs of 4 amplitudes on register bits 0, 1 in both the load (initial)
   // and the store (final) order
-  if (L.vec4 && (L.k < 10 || L.transpose || L.order[8] != 0 || L.order[9] != 1 || L.sorder[8] != 0 ||
-                 L.sorder[9] != 1))
+  // (k >= 10 always: those kernels are compiled for this layout only)
+  if ((L.k >= 10) != (L.vec4 != 0)) return cudaErrorInvalidValue;
+  if (L.vec4 && (L.transpose || L.order[8] != 0 || L.order[9] != 1 || L.sorder[8] != 0 || L.sorder[9] != 1))
     return cudaErrorInvalidValue;
   for (int r = 0; r < L.k; ++r) {
     const int qc = L.order[r], qs = L.sorder[r];
