@@ -211,30 +211,36 @@ def sweep_hbm(sim, torch, stream, reps=3, cols=10, fuse=0):
     sel = np.zeros(1, dtype=np.uint64)
     info = {}
     try:
-        best = {}
-        for name, prec, phase in (("fused_c64", sim.SIM_C64, sim.SIM_PHASE_SWEEP),
-                                  ("plain_c128", sim.SIM_C128_PLAIN, sim.SIM_PHASE_PLAIN)):
+        best, passes = {}, {}
+        # in-order pass formation first, then the default (dependency-aware) one; evolve
+        # re-plans for another fuse width or pass order, and the pass counts are read
+        # from the schedule that ran
+        for name, prec, phase, order in (("in_order_c64", sim.SIM_C64, sim.SIM_PHASE_SWEEP, 1),
+                                         ("fused_c64", sim.SIM_C64, sim.SIM_PHASE_SWEEP, 0),
+                                         ("plain_c128", sim.SIM_C128_PLAIN, sim.SIM_PHASE_PLAIN, 0)):
             ts = []
             for _ in range(reps):
                 sim.sim_profile_read(reset=True)
                 sim.sim_profile_enable(True)
-                h = sim.sim_evolve_halves(plan, prec, 0, 1, sel, sel, opts={"fuse_qubits": fuse} if fuse else None,
+                h = sim.sim_evolve_halves(plan, prec, 0, 1, sel, sel, opts={"fuse_qubits": fuse, "pass_order": order},
                                           stream=stream)
                 sim.sim_status(stream)
                 sim.sim_profile_enable(False)
                 ts.append(sim.sim_profile_read(reset=True)["ms"][phase])
                 sim.sim_destroy_halves(h)
             best[name] = min(ts)
+            passes[name] = [sim.sim_plan_schedule(plan, hh)[1] for hh in (0, 1)]
         sim.sim_release_cache()
-        # the pass counts of the schedule that ran (evolve re-plans for another fuse width)
-        fused = [sim.sim_plan_schedule(plan, hh)[1] for hh in (0, 1)]
+        fused = passes["fused_c64"]
         plain = [sim.sim_plan_schedule(plan, hh)[2] for hh in (0, 1)]
         amps = 1 << nu
         fused_bytes = sum(16 * f - 8 for f in fused) * amps
+        io_bytes = sum(16 * f - 8 for f in passes["in_order_c64"]) * amps
         plain_bytes_c128 = sum(32 * p for p in plain) * amps
         plain_equiv_c64 = sum(16 * p for p in plain) * amps
         hbm = peaks()[0]
         fg = fused_bytes / (best["fused_c64"] / 1e3) / 1e9
+        iog = io_bytes / (best["in_order_c64"] / 1e3) / 1e9
         info = {"workload": "one copy of a %d-qubit 6x%d grid circuit, depth 16: two %d-qubit halves "
                             "(%.1f GB complex64 each)" % (6 * Cc, Cc, 3 * Cc, 8 * 2.0 ** (3 * Cc) / 1e9),
                 "fused_passes": fused, "plain_passes": plain,
@@ -243,6 +249,9 @@ def sweep_hbm(sim, torch, stream, reps=3, cols=10, fuse=0):
                 "plain_c128_ms": best["plain_c128"],
                 "plain_c128_gbs": plain_bytes_c128 / (best["plain_c128"] / 1e3) / 1e9,
                 "speedup_vs_plain": best["plain_c128"] / best["fused_c64"],
+                "in_order": {"fused_passes": passes["in_order_c64"], "fused_ms": best["in_order_c64"],
+                             "fused_gbs": iog, "fused_frac_of_hbm": iog / hbm,
+                             "note": "passes end at the first gate that does not fit (sim_opts.pass_order = 1)"},
                 "peak_gbs": hbm,
                 "note": "fused_gbs counts the bytes the fused passes must move; plain_equiv_gbs counts the "
                         "complex64 bytes the Section 2.4 scheme would move for the same circuit in the same time"}

@@ -97,13 +97,18 @@ typedef struct {
  *   sweep_threads  threads per block of the staged sweep (64..256, multiple of 32)
  *   gemm_group_m   m-blocks per raster group of the persistent contraction
  *   sweep_kernel   1: staged shared-memory sweep; 0 or 2: register-blocked sweep
- *                  wherever the pass allows it (8 <= k <= 13), staged otherwise */
+ *                  wherever the pass allows it (8 <= k <= 13), staged otherwise
+ *   pass_order     0: dependency-aware pass formation (a gate whose qubit does not
+ *                  fit is left for a later pass, together with everything that
+ *                  depends on it, and the pass goes on with the rest; fewer passes);
+ *                  1: in order (a pass ends at the first gate that does not fit) */
 typedef struct {
   int fuse_qubits;
   int sweep_threads;
   int gemm_group_m;
   int sweep_kernel;
-  int reserved[4];
+  int pass_order;
+  int reserved[3];
 } sim_opts;
 
 /* Build a circuit (Supplementary A, Eq. 3 circuit model; gate rules of the random

@@ -57,7 +57,8 @@ class BatchOpts(ctypes.Structure):
 
 class SimOpts(ctypes.Structure):
     _fields_ = [("fuse_qubits", ctypes.c_int), ("sweep_threads", ctypes.c_int),
-                ("gemm_group_m", ctypes.c_int), ("sweep_kernel", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("gemm_group_m", ctypes.c_int), ("sweep_kernel", ctypes.c_int), ("pass_order", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 _lib = None

@@ -840,9 +840,12 @@ namespace {
 int evolve_halves_impl(sim_cut_plan plan, int precision, CopySet&& cs, const uint64_t* sel_u, uint64_t n_u,
                        const uint64_t* sel_l, uint64_t n_l, const sim_opts* opts, void* stream, sim_halves* out) {
   CutPlan& P = plan->p;
-  if (opts && opts->fuse_qubits && opts->fuse_qubits != P.fuse_qubits) {
+  const int want_fuse = (opts && opts->fuse_qubits) ? opts->fuse_qubits : P.fuse_qubits;
+  const int want_order = opts ? opts->pass_order : P.pass_order;
+  if (want_fuse != P.fuse_qubits || want_order != P.pass_order) {
     CutPlan np;
-    std::string err = build_cut_plan(P.circ, P.circ.cut_row ? (P.n_u / P.circ.C) : 0, opts->fuse_qubits, np);
+    std::string err =
+        build_cut_plan(P.circ, P.circ.cut_row ? (P.n_u / P.circ.C) : 0, want_fuse, np, want_order);
     if (!err.empty()) return fail(SIM_EINVAL, err);
     free_plan_ops(P);
     P = np;

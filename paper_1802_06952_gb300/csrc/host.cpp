@@ -291,19 +291,124 @@ void make_diags(uint32_t tmask, const std::vector<std::pair<int, int>>& cz, cons
   }
 }
 
-// Greedy pass split of an op sequence: each pass stages k local qubits, always
-// the low `low` bits (coalesced rows) plus the qubits of the upcoming gates in
-// order; a pass ends before the first gate whose qubit no longer fits.  With
-// k < n at most k - 1 low bits are reserved, so every pass takes at least the
-// gate it starts with.
-void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
+// An item of a level's op sequence before the passes are formed: a non-diagonal
+// gate, or the diagonal terms of one layer (T qubits, CZ pairs, cut slots), kept
+// apart so that a pass can apply the terms on some qubits and leave the others.
+struct SeqItem {
+  bool is_gate = false;
+  OpRec gate;
+  uint32_t tmask = 0;
+  std::vector<std::pair<int, int>> cz;
+  std::vector<CutSlot> cuts;
+  bool empty_diag() const { return !is_gate && tmask == 0 && cz.empty() && cuts.empty(); }
+};
+
+SeqItem gate_item(const OpRec& o) {
+  SeqItem it;
+  it.is_gate = true;
+  it.gate = o;
+  return it;
+}
+
+SeqItem diag_item(uint32_t tmask, const std::vector<std::pair<int, int>>& cz, const std::vector<CutSlot>& cuts) {
+  SeqItem it;
+  it.tmask = tmask;
+  it.cz = cz;
+  it.cuts = cuts;
+  return it;
+}
+
+// Pass formation (Section 2.2's n_i fused passes, Section 2.4's combined diagonals).
+// Each pass stages k local qubits: the low `low` bits (coalesced rows) and the
+// qubits of the gates it applies, in sequence order.  The scan runs over the whole
+// remaining sequence: a gate whose qubit no longer fits is left for a later pass
+// and its qubit is blocked, and so is every later item that touches a blocked
+// qubit (a diagonal term on a blocked qubit blocks all of its qubits), so that
+// everything a pass applies comes after everything it depends on.  Diagonal terms
+// need no staged qubit (their phase depends on the full index), so every term on
+// unblocked qubits is applied where the scan meets it.  Items left over keep their
+// order for the next pass.  With k < n at most k - 1 low bits are reserved, so
+// every pass applies at least the item it starts with.  In order (in_order), a
+// pass instead ends at the first gate that does not fit.
+std::vector<std::vector<OpRec>> form_passes(int k, int low, std::vector<SeqItem> items, bool in_order) {
+  std::vector<std::vector<OpRec>> out;
+  const uint32_t low_mask = (1u << low) - 1;
+  while (!items.empty()) {
+    uint32_t staged = low_mask, blocked = 0;
+    int cnt = low;
+    bool full = false;
+    std::vector<OpRec> pass;
+    std::vector<SeqItem> rest;
+    // Applied diagonal terms are held back and merged into one diagonal op until a
+    // gate touches one of their qubits or a new term shares a qubit with them
+    // (diagonal terms commute with each other and with gates on other qubits).
+    SeqItem pend;
+    uint32_t pend_q = 0;
+    auto flush = [&]() {
+      if (pend_q) make_diags(pend.tmask, pend.cz, pend.cuts, pass);
+      pend = SeqItem();
+      pend_q = 0;
+    };
+    for (const SeqItem& it : items) {
+      if (full) {
+        rest.push_back(it);
+        continue;
+      }
+      if (it.is_gate) {
+        const uint32_t b = 1u << it.gate.q;
+        if (!(blocked & b) && ((staged & b) || cnt < k)) {
+          if (!(staged & b)) {
+            staged |= b;
+            ++cnt;
+          }
+          if (pend_q & b) flush();
+          pass.push_back(it.gate);
+        } else {
+          blocked |= b;
+          rest.push_back(it);
+          if (in_order) full = true;  // the pass ends here
+        }
+      } else {
+        // the terms of one layer act on distinct qubits: each is applied or left
+        SeqItem now, later;
+        now.tmask = it.tmask & ~blocked;
+        later.tmask = it.tmask & blocked;
+        for (const auto& pr : it.cz)
+          ((blocked >> pr.first) & 1u || (blocked >> pr.second) & 1u ? later.cz : now.cz).push_back(pr);
+        for (const CutSlot& sl : it.cuts) ((blocked >> sl.q) & 1u ? later.cuts : now.cuts).push_back(sl);
+        for (const auto& pr : later.cz) blocked |= (1u << pr.first) | (1u << pr.second);
+        if (!now.empty_diag()) {
+          uint32_t q = now.tmask;
+          for (const auto& pr : now.cz) q |= (1u << pr.first) | (1u << pr.second);
+          for (const CutSlot& sl : now.cuts) q |= 1u << sl.q;
+          if (pend_q & q) flush();
+          pend.tmask |= now.tmask;
+          pend.cz.insert(pend.cz.end(), now.cz.begin(), now.cz.end());
+          pend.cuts.insert(pend.cuts.end(), now.cuts.begin(), now.cuts.end());
+          pend_q |= q;
+        }
+        if (!later.empty_diag()) rest.push_back(later);
+      }
+      // room for the exchanges of the register-blocked sweep
+      if ((int)pass.size() >= kMaxPassOps - 24) full = true;
+    }
+    flush();
+    if (pass.empty()) throw std::logic_error("pass formation made no progress");
+    out.push_back(std::move(pass));
+    items.swap(rest);
+  }
+  return out;
+}
+
+// The passes of one copy-tree level: formed as above, then each given its rank
+// order (which staged qubit sits on which lane, warp and register bit).
+void split_passes(int n, int kmax, const std::vector<SeqItem>& items, int first_src, bool in_order,
                   std::vector<PassDesc>& passes, std::vector<OpRec>& ops) {
   const int k = std::min(n, kmax);
   const int low = k < n ? std::min(5, k - 1) : std::min(5, k);
   const uint32_t low_mask = (1u << low) - 1;
-  size_t i = 0;
   bool first = true;
-  if (seq.empty()) {
+  if (items.empty()) {
     PassDesc p;
     memset(&p, 0, sizeof p);
     p.k = k;
@@ -319,20 +424,16 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
     passes.push_back(p);
     return;
   }
-  while (i < seq.size()) {
+  for (const std::vector<OpRec>& seq : form_passes(k, low, items, in_order)) {
+    const size_t i = 0, j = seq.size();
     uint32_t local = low_mask;
     int cnt = low;
-    size_t j = i;
-    for (; j < seq.size(); ++j) {
-      if ((int)(j - i) >= kMaxPassOps - 24) break;  // room for the exchanges of the register-blocked sweep
-      if (seq[j].type != OP_GATE) continue;
-      uint32_t bit = 1u << seq[j].q;
-      if (local & bit) continue;
-      if (cnt == k) break;
-      local |= bit;
-      ++cnt;
-    }
-    if (j == i) throw std::logic_error("pass split made no progress");
+    for (const OpRec& o : seq)
+      if (o.type == OP_GATE && !(local & (1u << o.q))) {
+        local |= 1u << o.q;
+        ++cnt;
+      }
+    if (cnt > k) throw std::logic_error("pass stages more than k qubits");
     // fill the remaining local slots with the lowest unused qubits
     for (int q = 0; q < n && cnt < k; ++q)
       if (!(local & (1u << q))) { local |= 1u << q; ++cnt; }
@@ -545,13 +646,12 @@ void split_passes(int n, int kmax, const std::vector<OpRec>& seq, int first_src,
     p.phase_e = n_xy & 7;
     passes.push_back(p);
     first = false;
-    i = j;
   }
 }
 
 }  // namespace
 
-std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan) {
+std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan, int pass_order) {
   const int b = cut_row > 0 ? cut_row : c.R / 2;
   if (b < 1 || b >= c.R) return "cut row must lie strictly inside the grid";
   plan = CutPlan();
@@ -561,6 +661,8 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
   if (plan.n_u > 32 || plan.n_l > 32) return "each half must have at most 32 qubits";
   plan.fuse_qubits = fuse_qubits > 0 ? fuse_qubits : 13;
   if (plan.fuse_qubits < 4 || plan.fuse_qubits > 13) return "fuse_qubits must be in 4..13";
+  if (pass_order < 0 || pass_order > 1) return "pass_order must be 0 or 1";
+  plan.pass_order = pass_order;
   const int nu = plan.n_u;
   // E_int: CZs (and controlled X gates) with one endpoint in each half, numbered by
   // (layer, upper qubit)
@@ -652,7 +754,7 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
       L.bits_total = bits;
       const int t_begin = j == 0 ? 0 : branch[j - 1];
       const int t_end = j + 1 < nlev ? branch[j] : c.depth - 1;  // inclusive
-      std::vector<OpRec> seq;
+      std::vector<SeqItem> seq;
       for (int t = t_begin; t <= t_end; ++t) {
         const bool own_cut_layer = (j > 0 && t == t_begin);
         if (own_cut_layer) {
@@ -663,20 +765,21 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
           // qubits no other gate of the layer touches.
           std::vector<CutSlot> slots = hl[h].cuts[t];
           for (auto& p : hl[h].xcuts[t]) {
-            seq.push_back(make_gate(G_H, p.first));
+            seq.push_back(gate_item(make_gate(G_H, p.first)));
             slots.push_back({p.first, p.second, true});
           }
-          make_diags(0, {}, slots, seq);
-          for (auto& p : hl[h].xcuts[t]) seq.push_back(make_gate(G_H, p.first));
+          seq.push_back(diag_item(0, {}, slots));
+          for (auto& p : hl[h].xcuts[t]) seq.push_back(gate_item(make_gate(G_H, p.first)));
           continue;
         }
         if (!(j == 0 && t == 0 && uniform))
-          for (auto& p : hl[h].nondiag[t]) seq.push_back(make_gate(p.second, p.first));
+          for (auto& p : hl[h].nondiag[t]) seq.push_back(gate_item(make_gate(p.second, p.first)));
         const bool next_branch = (j + 1 < nlev && t == t_end);
-        make_diags(hl[h].tmask[t], hl[h].cz[t], next_branch ? std::vector<CutSlot>() : hl[h].cuts[t], seq);
+        SeqItem d = diag_item(hl[h].tmask[t], hl[h].cz[t], next_branch ? std::vector<CutSlot>() : hl[h].cuts[t]);
+        if (!d.empty_diag()) seq.push_back(d);
       }
       int first_src = j == 0 ? (uniform ? SRC_UNIFORM : SRC_ZERO) : SRC_PARENT;
-      split_passes(n, plan.fuse_qubits, seq, first_src, L.passes, S.ops);
+      split_passes(n, plan.fuse_qubits, seq, first_src, plan.pass_order == 1, L.passes, S.ops);
       S.levels.push_back(L);
     }
 

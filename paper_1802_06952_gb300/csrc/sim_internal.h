@@ -160,6 +160,7 @@ struct CutPlan {
   HalfSchedule sched[2];
   std::vector<PlainLayer> plain[2];
   int fuse_qubits = 0;
+  int pass_order = 0;
   // device copies of the op tables (uploaded lazily, freed with the plan)
   OpRec* d_ops[2] = {nullptr, nullptr};
   OpRec* d_plain_ops[2] = {nullptr, nullptr};
@@ -188,7 +189,8 @@ void note_bytes(uint64_t h2d, uint64_t d2h);
 std::string generate_circuit(int R, int C, int depth, uint64_t seed, int cut_row, Circuit& out, int t_in_pool = 0);
 std::string parse_circuit(const char* text, Circuit& out);
 std::string circuit_text(const Circuit& c);
-std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan);
+// pass_order: 0 dependency-aware pass formation, 1 in order (sim_opts.pass_order)
+std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan, int pass_order = 0);
 void select_indices(int nq, uint64_t count, uint64_t& state, std::vector<uint64_t>& out);
 uint64_t splitmix64_next(uint64_t& state);
 

@@ -385,12 +385,15 @@ def test_fuse_widths_and_sweep_kernels_agree(R, C, d, seed, b):
     5-7 warp gates through smem, 8+ register gates), the staged one otherwise."""
     gates, plan = oc.grid_cut(R, C, d, seed, b)
     ref = oracle.cut_amplitudes(plan)
-    for fq, kern in ((4, 0), (7, 0), (8, 0), (9, 0), (10, 1), (10, 2), (12, 1), (12, 2), (13, 0)):
+    # pass orders: 0 dependency-aware formation (the default), 1 in order
+    for fq, kern, order in ((4, 0, 0), (7, 0, 0), (8, 0, 0), (9, 0, 0), (10, 1, 0), (10, 2, 0), (12, 1, 0),
+                            (12, 2, 0), (13, 0, 0), (4, 0, 1), (9, 0, 1), (10, 2, 1), (13, 0, 1)):
         r = Run(R, C, d, seed, b)
         try:
-            h = r.evolve(sim.SIM_C64, opts={"fuse_qubits": fq, "sweep_threads": 128, "sweep_kernel": kern})
+            h = r.evolve(sim.SIM_C64, opts={"fuse_qubits": fq, "sweep_threads": 128, "sweep_kernel": kern,
+                                            "pass_order": order})
             got = amplitudes(h, sim.SIM_SPLIT_FP16, 1 << plan.n_l, 1 << plan.n_u).cpu().numpy()
-            assert rel_err(got, ref) <= TOL_SPLIT, (fq, kern)
+            assert rel_err(got, ref) <= TOL_SPLIT, (fq, kern, order)
             for k in (0, plan.copies - 1):
                 for half, nq in ((0, plan.n_u), (1, plan.n_l)):
                     buf = torch.zeros(1 << nq, dtype=torch.complex64, device="cuda")
@@ -399,7 +402,7 @@ def test_fuse_widths_and_sweep_kernels_agree(R, C, d, seed, b):
                     # a leaf can be exactly zero (two projectors on one cut qubit with
                     # opposite bits): the floor is the state's natural scale 2^{-n/2}
                     scale = max(np.max(np.abs(hs)), 2.0 ** (-nq / 2))
-                    assert np.max(np.abs(buf.cpu().numpy() - hs)) <= 1e-5 * scale, (fq, kern)
+                    assert np.max(np.abs(buf.cpu().numpy() - hs)) <= 1e-5 * scale, (fq, kern, order)
         finally:
             r.close()
 
@@ -407,6 +410,9 @@ def test_fuse_widths_and_sweep_kernels_agree(R, C, d, seed, b):
 def test_gpu_argument_errors():
     r = Run(4, 4, 10, 0)
     try:
+        with pytest.raises(sim.SimError) as e:
+            r.evolve(sim.SIM_C64, opts={"pass_order": 2})
+        assert e.value.code == sim.SIM_EINVAL
         with pytest.raises(sim.SimError) as e:
             r.evolve(sim.SIM_C64, 5, 5)
         assert e.value.code == sim.SIM_EINVAL
