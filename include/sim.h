@@ -135,6 +135,31 @@ int sim_circuit_text(sim_circuit circ, char* buf, size_t cap, size_t* len_out);
 int sim_cut(sim_circuit circ, int cut_row, sim_cut_plan* out, int* c_out,
             uint64_t* copies_out, int* n_upper_out, int* n_lower_out);
 
+/* Options of sim_cut_ex; a zero field keeps sim_cut's behaviour.
+ *   output_phase_cuts  1: a cut CZ at layer t with no non-diagonal gate (X^1/2,
+ *                      Y^1/2, H, controlled X) on either of its qubits after t
+ *                      commutes with every later gate, so it is applied to the final
+ *                      amplitudes as the sign (-1)^{x_h x_k} instead of being split
+ *                      by Supplementary A, Eq. 1 into two copies: 2^c shrinks by 2
+ *                      per such cut.  The amplitudes are the same; the leaves of
+ *                      sim_halves_leaf then lack those CZs.  (Not in the paper: an
+ *                      exact rewrite of the last cut layers.) */
+typedef struct {
+  int output_phase_cuts;
+  int reserved[7];
+} sim_cut_opts;
+
+/* sim_cut with options (opts may be NULL).  Same outputs and errors as sim_cut;
+ * SIM_EINVAL for an unknown option value. */
+int sim_cut_ex(sim_circuit circ, int cut_row, const sim_cut_opts* opts, sim_cut_plan* out, int* c_out,
+               uint64_t* copies_out, int* n_upper_out, int* n_lower_out);
+
+/* The output-sign cuts of a plan (sim_cut_ex with output_phase_cuts) as int32 pairs
+ * {upper qubit, lower qubit}: every amplitude A(x) is multiplied by
+ * (-1)^{sum over pairs of x_h x_k}.  Writes at most cap pairs; *n_out receives
+ * their number.  Host only. */
+int sim_cut_output_phases(sim_cut_plan plan, int32_t* pairs_out, int cap, int* n_out);
+
 /* The cut list as int32 triples {layer, upper qubit, lower qubit}, ordered by copy
  * bit m (3*c values).  *n_equiv_out (may be NULL) receives N_e of Section 3:
  * qubits per half + log2(number of half-circuits).  Host only. */

@@ -33,7 +33,7 @@ EXPORTS = (
     "sim_destroy_cut", "sim_destroy_halves", "sim_last_error", "sim_version",
     "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc", "sim_amplitudes_stats",
     "sim_evolve_halves_list", "sim_plan_levels", "sim_batch_create", "sim_batch_run", "sim_batch_results",
-    "sim_batch_info", "sim_destroy_batch", "sim_born_sample",
+    "sim_batch_info", "sim_destroy_batch", "sim_born_sample", "sim_cut_ex", "sim_cut_output_phases",
 )
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -53,6 +53,10 @@ class _Desc(ctypes.Structure):
 class BatchOpts(ctypes.Structure):
     _fields_ = [("contraction", ctypes.c_int), ("autotune", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("reserved", ctypes.c_int * 5)]
+
+
+class SimCutOpts(ctypes.Structure):
+    _fields_ = [("output_phase_cuts", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class SimOpts(ctypes.Structure):
@@ -80,6 +84,9 @@ def lib():
         "sim_circuit_info": (ctypes.c_int, [vp, ip, ip, ip]),
         "sim_circuit_text": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
         "sim_cut": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(vp), ip, u64p, ip, ip]),
+        "sim_cut_ex": (ctypes.c_int, [vp, ctypes.c_int, ctypes.POINTER(SimCutOpts), ctypes.POINTER(vp), ip, u64p,
+                                      ip, ip]),
+        "sim_cut_output_phases": (ctypes.c_int, [vp, i32p, ctypes.c_int, ip]),
         "sim_cut_list": (ctypes.c_int, [vp, i32p, ip]),
         "sim_plan_schedule": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ip]),
         "sim_plan_levels": (ctypes.c_int, [vp, ctypes.c_int, i32p, ctypes.c_int, ip]),
@@ -190,6 +197,26 @@ def sim_cut(circ, cut_row=0):
     _check(lib().sim_cut(circ, cut_row, ctypes.byref(p), ctypes.byref(c), ctypes.byref(copies),
                          ctypes.byref(nu), ctypes.byref(nl)))
     return p.value, c.value, copies.value, nu.value, nl.value
+
+
+def sim_cut_ex(circ, cut_row=0, output_phase_cuts=False):
+    """sim_cut with options; returns (plan, c, copies, n_upper, n_lower)."""
+    o = SimCutOpts(int(output_phase_cuts))
+    p = ctypes.c_void_p()
+    c, nu, nl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    copies = ctypes.c_uint64()
+    _check(lib().sim_cut_ex(circ, cut_row, ctypes.byref(o), ctypes.byref(p), ctypes.byref(c), ctypes.byref(copies),
+                            ctypes.byref(nu), ctypes.byref(nl)))
+    return p.value, c.value, copies.value, nu.value, nl.value
+
+
+def sim_cut_output_phases(plan):
+    """Output-sign cuts of a plan: list of (upper qubit, lower qubit)."""
+    n = ctypes.c_int()
+    _check(lib().sim_cut_output_phases(plan, None, 0, ctypes.byref(n)))
+    arr = (ctypes.c_int32 * max(2 * n.value, 1))()
+    _check(lib().sim_cut_output_phases(plan, arr, n.value, ctypes.byref(n)))
+    return [tuple(arr[2 * i:2 * i + 2]) for i in range(n.value)]
 
 
 def sim_cut_list(plan, c):

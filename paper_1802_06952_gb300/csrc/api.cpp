@@ -35,6 +35,7 @@ struct sim_halves_s {
   bool full[2] = {true, true};
   void* d_sel[2] = {nullptr, nullptr};
   void* leafsel[2] = {nullptr, nullptr};  // [K][nsel] complex64 or complex128
+  uint32_t* out_code[2] = {nullptr, nullptr};  // output-phase codes per selected index (or NULL)
   cudaStream_t stream = nullptr;
   int device = 0;
 };
@@ -565,8 +566,13 @@ int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cu
   if (contraction == SIM_FP64_PLAIN) {
     {
       PhaseScope ps(SIM_PHASE_FP64_GEMM, st);
+      // output-phase cuts: a separate sign pass (before and after on an accumulated
+      // block, which signs only this contraction's part)
+      const bool sign = h->out_code[0] && h->out_code[1];
+      if (sign && accumulate) CK(launch_out_sign(out, 1, M, N, h->out_code[1], h->out_code[0], st));
       CK(launch_fp64_gemm(h->leafsel[1], h->leafsel[0], h->precision == SIM_C128_PLAIN, K, M, N, accumulate, out,
                           st));
+      if (sign) CK(launch_out_sign(out, 1, M, N, h->out_code[1], h->out_code[0], st));
     }
     if (st_acc && st_hist) {
       PhaseScope ps(SIM_PHASE_STATS, st);
@@ -612,6 +618,8 @@ int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cu
   g.w_scale = std::ldexp(1.f, nq);
   g.st_acc = st_acc;
   g.st_hist = st_hist;
+  g.out_lcode = h->out_code[1];
+  g.out_ucode = h->out_code[0];
   PhaseScope ps(SIM_PHASE_CONTRACT, st);
   CK(launch_tc_gemm(g, st));
   return SIM_OK;
@@ -672,6 +680,7 @@ bool halves_view(const sim_halves_s* h, HalvesView* v) {
   for (int i = 0; i < 2; ++i) {
     v->nsel[i] = h->nsel[i];
     v->leafsel[i] = h->leafsel[i];
+    v->out_code[i] = h->out_code[i];
   }
   return true;
 }
@@ -772,11 +781,30 @@ int sim_circuit_text(sim_circuit circ, char* buf, size_t cap, size_t* len_out) {
 
 int sim_cut(sim_circuit circ, int cut_row, sim_cut_plan* out, int* c_out, uint64_t* copies_out, int* n_upper_out,
             int* n_lower_out) {
+  return sim_cut_ex(circ, cut_row, nullptr, out, c_out, copies_out, n_upper_out, n_lower_out);
+}
+
+int sim_cut_output_phases(sim_cut_plan plan, int32_t* pairs_out, int cap, int* n_out) {
+  if (!plan || !n_out) return fail(SIM_EINVAL, "plan and n_out must not be NULL");
+  const CutPlan& P = plan->p;
+  *n_out = (int)P.out_cz.size();
+  if (pairs_out)
+    for (int i = 0; i < (int)P.out_cz.size() && i < cap; ++i) {
+      pairs_out[2 * i] = P.out_cz[i].first;
+      pairs_out[2 * i + 1] = P.out_cz[i].second;
+    }
+  return SIM_OK;
+}
+
+int sim_cut_ex(sim_circuit circ, int cut_row, const sim_cut_opts* opts, sim_cut_plan* out, int* c_out,
+               uint64_t* copies_out, int* n_upper_out, int* n_lower_out) {
   API_BEGIN
   if (!circ || !out) return fail(SIM_EINVAL, "circuit and out must not be NULL");
   *out = nullptr;
+  if (opts && (opts->output_phase_cuts < 0 || opts->output_phase_cuts > 1))
+    return fail(SIM_EINVAL, "output_phase_cuts must be 0 or 1");
   auto* p = new sim_cut_s();
-  std::string err = build_cut_plan(circ->c, cut_row, 0, p->p);
+  std::string err = build_cut_plan(circ->c, cut_row, 0, p->p, 0, opts && opts->output_phase_cuts);
   if (!err.empty()) {
     delete p;
     return fail(err.find("at most") != std::string::npos || err.find("more than") != std::string::npos ||
@@ -844,8 +872,8 @@ int evolve_halves_impl(sim_cut_plan plan, int precision, CopySet&& cs, const uin
   const int want_order = opts ? opts->pass_order : P.pass_order;
   if (want_fuse != P.fuse_qubits || want_order != P.pass_order) {
     CutPlan np;
-    std::string err =
-        build_cut_plan(P.circ, P.circ.cut_row ? (P.n_u / P.circ.C) : 0, want_fuse, np, want_order);
+    // the plan's own cut row (n_u = b C), whatever row the circuit was built with
+    std::string err = build_cut_plan(P.circ, P.n_u / P.circ.C, want_fuse, np, want_order, P.out_phase_cuts);
     if (!err.empty()) return fail(SIM_EINVAL, err);
     free_plan_ops(P);
     P = np;
@@ -892,6 +920,22 @@ int evolve_halves_impl(sim_cut_plan plan, int precision, CopySet&& cs, const uin
       if (e != cudaSuccess) {
         cleanup();
         return fail(SIM_ECUDA, std::string("selection upload: ") + cudaGetErrorString(e));
+      }
+    }
+  }
+  // output-phase cuts: per selected index of each half, the bits of its cuts
+  if (!P.out_cz.empty()) {
+    for (int hh = 0; hh < 2; ++hh) {
+      std::vector<int> qs;
+      for (const auto& pr : P.out_cz) qs.push_back(hh == 0 ? pr.first : pr.second - P.n_u);
+      cudaError_t e = pool().alloc((void**)&h->out_code[hh], sizeof(uint32_t) * h->nsel[hh]);
+      if (e == cudaSuccess)
+        e = launch_out_codes((const uint64_t*)h->d_sel[hh], h->nsel[hh], qs.data(), (int)qs.size(), h->out_code[hh],
+                             st);
+      if (e != cudaSuccess) {
+        cleanup();
+        return fail(e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA,
+                    std::string("output-phase codes: ") + cudaGetErrorString(e));
       }
     }
   }
@@ -1138,6 +1182,7 @@ void sim_destroy_halves(sim_halves h) {
   for (int i = 0; i < 2; ++i) {
     pool().free(h->leafsel[i]);
     pool().free(h->d_sel[i]);
+    pool().free(h->out_code[i]);
   }
   delete h;
 }

@@ -524,9 +524,23 @@ bool make_map(CUtensorMap* map, const void* base, int64_t rows, int64_t kpad, in
 
 }  // namespace
 
+cudaError_t launch_tc_gemm_single(const TcGemmArgs& a, cudaStream_t s);
+
 cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s) {
   const bool want_pair = a.variant == 2 || (a.variant == 0 && tc_gemm_pair_enabled());
+  // the CTA-pair kernel applies output-phase signs in its epilogue
   if (want_pair && tc_gemm_pair_supported(a)) return launch_tc_gemm_pair(a, s);
+  if (!a.out_lcode || !a.out_ucode) return launch_tc_gemm_single(a, s);
+  // here a separate pass signs the block: on an accumulated block it flips the old
+  // values first and the sum after, which signs only this contraction's part
+  cudaError_t e = cudaSuccess;
+  if (a.accumulate) e = launch_out_sign(a.C, 0, a.M, a.N2 / 2, a.out_lcode, a.out_ucode, s);
+  if (e == cudaSuccess) e = launch_tc_gemm_single(a, s);
+  if (e == cudaSuccess) e = launch_out_sign(a.C, 0, a.M, a.N2 / 2, a.out_lcode, a.out_ucode, s);
+  return e;
+}
+
+cudaError_t launch_tc_gemm_single(const TcGemmArgs& a, cudaStream_t s) {
   if (a.M <= 0 || a.N2 <= 0) return cudaSuccess;
   if (a.kpad <= 0 || a.kpad % BK != 0 || a.M > (1ll << 31) - BM || a.N2 > (1ll << 31) - BN)
     return cudaErrorInvalidValue;

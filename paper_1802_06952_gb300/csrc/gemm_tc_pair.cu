@@ -255,6 +255,8 @@ struct PairArgs {
   float w_scale;
   double* st_acc;
   unsigned long long* st_hist;
+  const uint32_t* out_lcode;  // output-phase codes of the rows and complex columns (NULL: none)
+  const uint32_t* out_ucode;
   __device__ int chunk_kblocks(int c) const {
     const int b0 = c * ckb;
     const int b1 = b0 + ckb < nkb ? b0 + ckb : nkb;
@@ -271,7 +273,7 @@ struct PairArgs {
 // STATS: fuse the FP64 statistics of the final amplitudes into the epilogue.
 // STG: operand stages.  SW: accumulator columns per epilogue step (8 or 16), which
 // sets the staging box (32 rows x SW floats, 32- or 64-byte TMA swizzle).
-template <bool STATS, int STG, int SW, int NBUF, int UNR, int EW>
+template <bool STATS, bool SIGN, int STG, int SW, int NBUF, int UNR, int EW>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constant__ CUtensorMap mapA_lo,
                         const __grid_constant__ CUtensorMap mapB_hi, const __grid_constant__ CUtensorMap mapB_lo,
@@ -477,6 +479,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
         const int64_t col_half0 = nb * BN + cpart * COLS;
         const int64_t grow = row0 + lane;
         const bool rowok = grow < args.M;
+        const uint32_t lcode = (SIGN && rowok) ? __ldg(args.out_lcode + grow) : 0u;
         const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * ACC_COLS + cpart * COLS);
         // per-job partial statistics in fp32 (at most 64 terms per lane), folded into
         // the FP64 totals once per job
@@ -487,6 +490,18 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
 #pragma unroll
           for (int j = 0; j < SW; ++j) v[j] = __uint_as_float(r[j]) * oscale;
           const int64_t gcol0 = col_half0 + c * SW;
+          if (SIGN && lcode) {
+            // output-phase cuts: (-1)^{popc(row code & column code)} on this part
+            const uint32_t* uc = args.out_ucode + (gcol0 >> 1);
+#pragma unroll
+            for (int j = 0; j < SW / 2; ++j) {
+              const uint32_t u = (gcol0 + 2 * j < args.N2) ? __ldg(uc + j) : 0u;
+              if (__popc(lcode & u) & 1) {
+                v[2 * j] = -v[2 * j];
+                v[2 * j + 1] = -v[2 * j + 1];
+              }
+            }
+          }
           if (rmw_regs && rowok) {
             const float* src = args.C + grow * args.N2 + gcol0;
 #pragma unroll
@@ -636,14 +651,14 @@ bool make_output_map(CUtensorMap* map, float* C, int64_t M, int64_t N2, int sw) 
   return r == CUDA_SUCCESS;
 }
 
-template <bool STATS, int STG, int SW, int NBUF, int UNR, int EW>
+template <bool STATS, bool SIGN, int STG, int SW, int NBUF, int UNR, int EW>
 cudaError_t launch_variant(const CUtensorMap (&maps)[4], const CUtensorMap& mapC, const PairArgs& k, uint32_t idesc,
                            int num_sms, cudaStream_t s) {
   constexpr int SMEM = PairSmem<STG, SW, NBUF, EW>::BYTES;
   constexpr int THREADS = 32 * (2 + EW);
   static int max_pairs = 0;
   if (max_pairs == 0) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_pair_kernel<STATS, STG, SW, NBUF, UNR, EW>,
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
     if (e != cudaSuccess) return e;
     // one resident pair per SM pair: as many clusters as can be co-scheduled at once
@@ -652,7 +667,7 @@ cudaError_t launch_variant(const CUtensorMap (&maps)[4], const CUtensorMap& mapC
     cfg.blockDim = dim3(THREADS, 1, 1);
     cfg.dynamicSmemBytes = SMEM;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_pair_kernel<STATS, STG, SW, NBUF, UNR, EW>, &cfg) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW>, &cfg) != cudaSuccess || n < 1) {
       cudaGetLastError();
       n = num_sms / 2;
     }
@@ -661,7 +676,7 @@ cudaError_t launch_variant(const CUtensorMap (&maps)[4], const CUtensorMap& mapC
   int pairs = max_pairs;
   if ((int64_t)pairs > k.num_tiles) pairs = (int)k.num_tiles;
   if (pairs < 1) pairs = 1;
-  tc_gemm_pair_kernel<STATS, STG, SW, NBUF, UNR, EW><<<2 * pairs, THREADS, SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], mapC, k,
+  tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW><<<2 * pairs, THREADS, SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], mapC, k,
                                                                       idesc);
   return cudaGetLastError();
 }
@@ -719,14 +734,26 @@ cudaError_t launch_tc_gemm_pair(const TcGemmArgs& a, cudaStream_t s) {
   k.w_scale = a.w_scale;
   k.st_acc = a.st_acc;
   k.st_hist = a.st_hist;
+  k.out_lcode = (a.out_lcode && a.out_ucode) ? a.out_lcode : nullptr;
+  k.out_ucode = k.out_lcode ? a.out_ucode : nullptr;
   const uint32_t idesc = instr_desc_pair(a.fp16 != 0);
   const int nsm = a.num_sms > 0 ? a.num_sms : 148;
   const bool stats = a.st_acc && a.st_hist;
-  // 6 operand stages, 16-column epilogue steps, one staging buffer per epilogue
-  // warp, two steps per loop iteration, 8 epilogue warps (230,912 bytes of shared
-  // memory per CTA)
-  cudaError_t e = stats ? launch_variant<true, 6, 16, 1, 2, 8>(maps, mapC, k, idesc, nsm, s)
-                        : launch_variant<false, 6, 16, 1, 2, 8>(maps, mapC, k, idesc, nsm, s);
+  // 16-column epilogue steps, one staging buffer per epilogue warp, two steps per
+  // loop iteration
+  const bool sign = k.out_lcode != nullptr;
+  // Epilogue shape by the length of a tile's main loop: with few k-blocks per tile
+  // (K <= 128 copies) the epilogue is the bound and 16 epilogue warps hide its
+  // latency (5 operand stages, 214,528 bytes of shared memory); otherwise 6 stages
+  // and 8 epilogue warps (230,912 bytes).  Measured on the 2^30-amplitude workload:
+  // K = 32: 3.16 ms against 4.97 ms with 8 warps; K = 256: 4.32 against 4.31 ms.
+#define LV(G, E)                                                                                          \
+  (stats ? (sign ? launch_variant<true, true, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s)                 \
+                 : launch_variant<true, false, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s))               \
+         : (sign ? launch_variant<false, true, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s)                \
+                 : launch_variant<false, false, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s)))
+  cudaError_t e = k.nkb <= 4 ? LV(5, 16) : LV(6, 8);
+#undef LV
   note_launches(SIM_PHASE_CONTRACT, 1);
   return e;
 }

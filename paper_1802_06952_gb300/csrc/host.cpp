@@ -651,7 +651,8 @@ void split_passes(int n, int kmax, const std::vector<SeqItem>& items, int first_
 
 }  // namespace
 
-std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan, int pass_order) {
+std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan, int pass_order,
+                           bool out_phase_cuts) {
   const int b = cut_row > 0 ? cut_row : c.R / 2;
   if (b < 1 || b >= c.R) return "cut row must lie strictly inside the grid";
   plan = CutPlan();
@@ -664,10 +665,29 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
   if (pass_order < 0 || pass_order > 1) return "pass_order must be 0 or 1";
   plan.pass_order = pass_order;
   const int nu = plan.n_u;
+  // Output-phase cuts (when asked for): a cut CZ at layer t with no non-diagonal
+  // gate on either of its qubits after t commutes with every later gate, so it can
+  // be applied to the final amplitudes as the sign (-1)^{x_h x_k} instead of being
+  // split into copies.
+  plan.out_phase_cuts = out_phase_cuts;
+  std::vector<int> last_nondiag(c.n, -1);  // last layer with a non-diagonal gate on a qubit
+  for (const Gate& g : c.gates)
+    if (g.code != G_T && g.code != G_CZ) {
+      last_nondiag[g.q1] = std::max(last_nondiag[g.q1], g.t);
+      if (g.q2 >= 0) last_nondiag[g.q2] = std::max(last_nondiag[g.q2], g.t);
+    }
+  std::set<std::pair<int, int>> out_keys;  // (layer, upper qubit) of the output-phase cuts
   // E_int: CZs (and controlled X gates) with one endpoint in each half, numbered by
   // (layer, upper qubit)
   for (const Gate& g : c.gates) {
-    if (g.code == G_CZ && g.q1 < nu && g.q2 >= nu) plan.cuts.push_back({g.t, g.q1, g.q2, 0});
+    if (g.code == G_CZ && g.q1 < nu && g.q2 >= nu) {
+      if (out_phase_cuts && last_nondiag[g.q1] < g.t && last_nondiag[g.q2] < g.t) {
+        plan.out_cz.emplace_back(g.q1, g.q2);
+        out_keys.insert({g.t, g.q1});
+        continue;
+      }
+      plan.cuts.push_back({g.t, g.q1, g.q2, 0});
+    }
     if (g.code == G_CX) {
       const int a = std::min(g.q1, g.q2), b2 = std::max(g.q1, g.q2);
       if (!(a < nu && b2 >= nu)) return "a controlled X inside one half is not supported (only across the cut)";
@@ -696,7 +716,7 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
         hl[0].cz[g.t].emplace_back(g.q1, g.q2);
       } else if (g.q1 >= nu) {
         hl[1].cz[g.t].emplace_back(g.q1 - nu, g.q2 - nu);
-      } else {
+      } else if (!out_keys.count({g.t, g.q1})) {
         int m = cut_index[{g.t, g.q1}];
         hl[0].cuts[g.t].push_back({g.q1, m, false});
         hl[1].cuts[g.t].push_back({g.q2 - nu, m, true});

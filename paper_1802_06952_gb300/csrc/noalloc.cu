@@ -125,6 +125,8 @@ extern "C" int sim_amplitudes_noalloc(sim_halves h, int contraction, int accumul
     g.group_m = 0;
     g.num_sms = num_sms;
     g.d_status = d_status;
+    g.out_lcode = v.out_code[1];
+    g.out_ucode = v.out_code[0];
     e = launch_tc_gemm(g, st);
   }
   // wait, then report a bounded device wait that gave up

@@ -161,6 +161,10 @@ struct CutPlan {
   std::vector<PlainLayer> plain[2];
   int fuse_qubits = 0;
   int pass_order = 0;
+  // output-phase cuts: (upper qubit, lower qubit) of each cut CZ applied as the sign
+  // (-1)^{x_h x_k} of the final amplitudes instead of a copy bit
+  bool out_phase_cuts = false;
+  std::vector<std::pair<int, int>> out_cz;
   // device copies of the op tables (uploaded lazily, freed with the plan)
   OpRec* d_ops[2] = {nullptr, nullptr};
   OpRec* d_plain_ops[2] = {nullptr, nullptr};
@@ -176,6 +180,7 @@ struct HalvesView {
   uint64_t K;  // copies held (leaf rows)
   int64_t nsel[2];
   const void* leafsel[2];
+  const uint32_t* out_code[2];  // output-phase codes of the upper / lower selection (NULL: none)
 };
 bool halves_view(const sim_halves_s* h, HalvesView* v);
 // Sets the thread's last-error text and returns code.
@@ -189,8 +194,11 @@ void note_bytes(uint64_t h2d, uint64_t d2h);
 std::string generate_circuit(int R, int C, int depth, uint64_t seed, int cut_row, Circuit& out, int t_in_pool = 0);
 std::string parse_circuit(const char* text, Circuit& out);
 std::string circuit_text(const Circuit& c);
-// pass_order: 0 dependency-aware pass formation, 1 in order (sim_opts.pass_order)
-std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan, int pass_order = 0);
+// pass_order: 0 dependency-aware pass formation, 1 in order (sim_opts.pass_order);
+// out_phase_cuts: cut CZs with no later non-diagonal gate on their qubits become
+// output signs instead of copy bits (sim_cut_opts.output_phase_cuts)
+std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan, int pass_order = 0,
+                           bool out_phase_cuts = false);
 void select_indices(int nq, uint64_t count, uint64_t& state, std::vector<uint64_t>& out);
 uint64_t splitmix64_next(uint64_t& state);
 
@@ -283,6 +291,11 @@ struct TcGemmArgs {
   // selects the single-CTA one); 1: single-CTA kernel; 2: CTA-pair kernel where it
   // applies (16-byte output rows), the single-CTA kernel otherwise
   int variant = 0;
+  // output-phase cuts (both NULL: none): entry (r, c) of the block is multiplied by
+  // (-1)^{popc(out_lcode[r] & out_ucode[c])}, c the complex column (< N2 / 2); an
+  // accumulated block gets the sign on this contraction's part only
+  const uint32_t* out_lcode = nullptr;
+  const uint32_t* out_ucode = nullptr;
 };
 cudaError_t launch_tc_gemm(const TcGemmArgs& a, cudaStream_t s);
 // CTA-pair variant of the same contraction (tcgen05 cta_group::2, M = 256 per pair)
@@ -297,6 +310,15 @@ constexpr int SIM_TIMEOUT_CODE_EPI = 0x103;
 // Plain FP64 contraction C[M][N] (+)= sum_k Lsel[k][m] * Usel[k][j] (complex128 out)
 cudaError_t launch_fp64_gemm(const void* lsel, const void* usel, int in_c128, int64_t K,
                              int64_t M, int64_t N, int accumulate, void* C, cudaStream_t s);
+
+// Output-phase cuts (phase.cu): out[i] = bit m set where index x = sel[i] (or i
+// when sel is NULL) has bit qubits[m], m < nm <= 32; and the sign flip of an
+// M x N complex64 (is_c128 = 0) or complex128 block by the parity of
+// lcode[row] & ucode[column]
+cudaError_t launch_out_codes(const uint64_t* sel, int64_t n, const int* qubits, int nm, uint32_t* out,
+                             cudaStream_t s);
+cudaError_t launch_out_sign(void* C, int is_c128, int64_t M, int64_t N, const uint32_t* lcode, const uint32_t* ucode,
+                            cudaStream_t s);
 
 // FP64 statistics over an amplitude block: acc[0] = sum p, acc[1] = sum ln w over
 // p > 0, acc[2] = number of p > 0 (as double); hist[SIM_KS_BINS] counts.

@@ -239,3 +239,64 @@ def test_cut_invariance_under_gate_order_text():
     finally:
         sim.sim_destroy_cut(p)
         sim.sim_destroy_circuit(c)
+
+
+def _expected_output_phase_cuts(gates, n_u):
+    """Cut CZs (upper < n_u <= lower) with no non-diagonal gate on either qubit at a
+    later layer, from the oracle generator's gate list."""
+    last = {}
+    for g in gates:
+        if g[1] not in ("T", "CZ"):
+            for q in g[2:]:
+                last[q] = max(last.get(q, -1), g[0])
+    out, kept = [], []
+    for g in gates:
+        if g[1] == "CZ":
+            a, b = min(g[2], g[3]), max(g[2], g[3])
+            if a < n_u <= b:
+                if last.get(a, -1) < g[0] and last.get(b, -1) < g[0]:
+                    out.append((a, b))
+                else:
+                    kept.append((g[0], a, b))
+    return out, kept
+
+
+@pytest.mark.parametrize("R,C,d,seed,b", [(6, 5, 16, 0, 3), (6, 5, 16, 3, 3), (4, 4, 9, 0, 2), (4, 4, 10, 0, 2),
+                                          (6, 7, 22, 0, 3), (5, 4, 15, 2, 2)])
+def test_output_phase_cuts_on_the_host(R, C, d, seed, b):
+    """sim_cut_ex(output_phase_cuts): which cut CZs leave the copy index (the rule
+    recomputed from the oracle's generator), the remaining cut list in copy-bit order,
+    and 2^c; without the option the plan is sim_cut's."""
+    gates = oc.generate(R, C, d, seed, b)
+    n_u = b * C
+    want_out, want_kept = _expected_output_phase_cuts(gates, n_u)
+    circ = sim.sim_build_circuit(R, C, d, seed, b)
+    try:
+        p0, c0, _, _, _ = sim.sim_cut(circ, b)
+        p1, c1, copies1, _, _ = sim.sim_cut_ex(circ, b, output_phase_cuts=True)
+        p2, c2, _, _, _ = sim.sim_cut_ex(circ, b, output_phase_cuts=False)
+        try:
+            assert c2 == c0 and sim.sim_cut_output_phases(p0) == [] and sim.sim_cut_output_phases(p2) == []
+            assert sorted(sim.sim_cut_output_phases(p1)) == sorted(want_out)
+            assert c1 == c0 - len(want_out) and copies1 == 1 << c1
+            assert sim.sim_cut_list(p1, c1)[0] == sorted(want_kept)
+        finally:
+            for p in (p0, p1, p2):
+                sim.sim_destroy_cut(p)
+    finally:
+        sim.sim_destroy_circuit(circ)
+    # the 30-qubit workload: the three cuts of its last layer (15) leave, c = 8 -> 5
+    if (R, C, d, b) == (6, 5, 16, 3):
+        assert len(want_out) == 3 and c1 == 5
+
+
+def test_output_phase_cuts_rejects_bad_option():
+    import ctypes
+    circ = sim.sim_build_circuit(4, 4, 9, 0, 2)
+    try:
+        o = sim.SimCutOpts(2)
+        p = ctypes.c_void_p()
+        rc = sim.lib().sim_cut_ex(circ, 2, ctypes.byref(o), ctypes.byref(p), None, None, None, None)
+        assert rc == sim.SIM_EINVAL and not p.value
+    finally:
+        sim.sim_destroy_circuit(circ)

@@ -492,3 +492,84 @@ def test_controlled_x_cuts(seed):
     finally:
         sim.sim_destroy_cut(cp)
         sim.sim_destroy_circuit(circ)
+
+
+class PhaseRun(Run):
+    """Run whose cut applies the last cut layers as output signs (sim_cut_ex)."""
+
+    def __init__(self, R, C, d, seed, b):
+        self.circ = sim.sim_build_circuit(R, C, d, seed, b)
+        self.plan, self.c, self.copies, self.nu, self.nl = sim.sim_cut_ex(self.circ, b, output_phase_cuts=True)
+        self.halves = []
+
+
+def test_output_phase_cuts_full_vector():
+    """4x4 grid, depth 9: the two cut CZs of the last layer become output signs
+    (c = 4 -> 2).  The rewrite is exact, so every contraction path gives the uncut
+    state vector: split bf16 / fp16 (CTA-pair kernel, sign in the epilogue) and FP64
+    plain (separate sign pass)."""
+    gates = oc.generate(4, 4, 9, 0, 2)
+    ref = oracle.statevector(16, gates).reshape(256, 256)
+    r = PhaseRun(4, 4, 9, 0, 2)
+    try:
+        assert r.c == 2 and len(sim.sim_cut_output_phases(r.plan)) == 2
+        h = r.evolve(sim.SIM_C64)
+        for kind in (sim.SIM_SPLIT_BF16, sim.SIM_SPLIT_FP16):
+            assert rel_err(amplitudes(h, kind, 256, 256).cpu().numpy(), ref) <= TOL_SPLIT
+        hp = r.evolve(sim.SIM_C128_PLAIN)
+        assert rel_err(amplitudes(hp, sim.SIM_FP64_PLAIN, 256, 256).cpu().numpy(), ref) <= TOL_PLAIN
+    finally:
+        r.close()
+
+
+@pytest.mark.parametrize("nsu", [256, 255])
+def test_output_phase_cuts_accumulate_and_selections(nsu):
+    """Selections (255 upper indices: the single-CTA kernel with separate sign passes;
+    256: the CTA-pair kernel) and accumulation over copy batches: each batch's part
+    gets the sign, the earlier sum keeps its own."""
+    R, C, d, seed, b = 6, 4, 16, 3, 3
+    gates, plan = oc.grid_cut(R, C, d, seed, b)
+    rng = np.random.default_rng(nsu)
+    su = np.sort(rng.permutation(1 << plan.n_u)[:nsu]).astype(np.uint64)
+    sl = np.sort(rng.permutation(1 << plan.n_l)[:200]).astype(np.uint64)
+    ref = oracle.cut_amplitudes(plan, su, sl)
+    r = PhaseRun(R, C, d, seed, b)
+    try:
+        assert r.c < plan.c
+        out = torch.zeros((sl.size, su.size), dtype=torch.complex64, device="cuda")
+        outp = torch.zeros((sl.size, su.size), dtype=torch.complex128, device="cuda")
+        bounds = [0, 1, r.copies // 2, r.copies]
+        for a, bnd in zip(bounds[:-1], bounds[1:]):
+            h = r.evolve(sim.SIM_C64, a, bnd, su, sl)
+            sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, True, out)
+            hp = r.evolve(sim.SIM_C128_PLAIN, a, bnd, su, sl)
+            sim.sim_amplitudes(hp, sim.SIM_FP64_PLAIN, True, outp)
+        sim.sim_status()
+        assert rel_err(out.cpu().numpy(), ref) <= TOL_SPLIT
+        assert rel_err(outp.cpu().numpy(), ref) <= TOL_PLAIN
+    finally:
+        r.close()
+
+
+def test_output_phase_cuts_30q_sampled():
+    """The 30-qubit workload (6x5, depth 16) with its last cut layer as output signs:
+    c = 8 -> 5 (32 copies), the full 2^30 vector against the oracle's cut-and-sum on
+    sampled amplitudes, and the statistics fused into the same contraction."""
+    gates, plan = oc.grid_cut(6, 5, 16, 1, 3)
+    rng = np.random.default_rng(5)
+    su = np.unique(rng.integers(0, 1 << 15, size=64)).astype(np.uint64)
+    sl = np.unique(rng.integers(0, 1 << 15, size=64)).astype(np.uint64)
+    ref = oracle.cut_amplitudes(plan, su, sl)
+    r = PhaseRun(6, 5, 16, 1, 3)
+    try:
+        assert r.c == 5
+        h = r.evolve(sim.SIM_C64)
+        out = torch.empty((1 << 15, 1 << 15), dtype=torch.complex64, device="cuda")
+        st = sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_BF16, False, out)
+        got = out[torch.from_numpy(sl.astype(np.int64)).cuda()][:, torch.from_numpy(su.astype(np.int64)).cuda()]
+        assert rel_err(got.cpu().numpy(), ref) <= TOL_SPLIT
+        assert abs(st[0] - 1.0) < 1e-4
+        del out
+        torch.cuda.empty_cache()
+    finally:
+        r.close()

@@ -90,3 +90,24 @@ def test_noalloc_rejects_oversized_and_host_output():
         sim.sim_destroy_halves(h)
         sim.sim_destroy_cut(plan)
         sim.sim_destroy_circuit(circ)
+
+
+def test_noalloc_with_output_phase_cuts():
+    """Output-phase cuts (sim_cut_ex): the fixed-scratch contraction signs the block
+    like sim_amplitudes, also when it accumulates into an earlier result."""
+    circ = sim.sim_build_circuit(4, 4, 9, 0, 2)
+    plan, c, copies, nu, nl = sim.sim_cut_ex(circ, 2, output_phase_cuts=True)
+    try:
+        assert c == 2
+        h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, copies)
+        ref = torch.zeros((1 << nl, 1 << nu), dtype=torch.complex64, device="cuda")
+        sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, ref)
+        got = torch.zeros_like(ref)
+        sim.sim_amplitudes_noalloc(h, sim.SIM_SPLIT_BF16, False, got)
+        assert rel(got.cpu().numpy(), ref.cpu().numpy()) <= TOL
+        sim.sim_amplitudes_noalloc(h, sim.SIM_SPLIT_BF16, True, got)
+        assert rel(got.cpu().numpy(), 2 * ref.cpu().numpy()) <= TOL
+        sim.sim_destroy_halves(h)
+    finally:
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(circ)
