@@ -54,10 +54,23 @@ __device__ __forceinline__ bool decide(const float2* amps, uint64_t count, uint6
   return u * pmax < prob(amps, *idx);
 }
 
+// Exact FP64 maximum of |A|^2 with an FP32 screen: fmaf(re, re, im * im) is within
+// 2^-23 of the FP64 value (two roundings of 2^-24), so an element whose FP32 value
+// stays below (1 - 2^-20) times the largest FP32 value this thread has seen cannot
+// exceed the FP64 maximum it holds.  Only the others are computed in FP64, so the
+// pass runs at the speed of its loads instead of GB300's FP64 rate.
 __global__ void pmax_kernel(const float2* amps, uint64_t count, double* block_max) {
   double m = 0.0;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += (uint64_t)gridDim.x * blockDim.x)
-    m = fmax(m, prob(amps, i));
+  float thr = 0.f;
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
+       i += (uint64_t)gridDim.x * blockDim.x) {
+    const float2 a = amps[i];
+    const float p32 = fmaf(a.x, a.x, a.y * a.y);
+    if (p32 >= thr) {
+      m = fmax(m, prob(amps, i));
+      thr = fmaxf(thr, p32 * (1.f - 9.5367431640625e-07f));
+    }
+  }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   __shared__ double sm[32];
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
