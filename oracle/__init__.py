@@ -7,7 +7,8 @@ and the library never imports it.
 
 Contents
   circuit.py  random grid circuit generator, canonical gate-list text, cut plan
-              (Supplementary A, Eqs. 3-8; Section 2.1, Eq. 1)
+              (Supplementary A, Eqs. 3-8; Section 2.1, Eq. 1), multi-part cut
+              plan (Section 3, Fig. 3)
   oracle.c    plain FP64 state-vector evolution (Supplementary A, Eq. 4) and the
               cut-and-sum reconstruction (Supplementary A, Eq. 8)
   this file   ctypes binding, the amplitude selection draw, the FP64
@@ -16,8 +17,7 @@ Contents
 
 Parity status: every function here is pinned by tests under ``tests/`` that do
 not call the oracle to make their expected values (brute-force Kronecker
-products, closed forms, counts printed in the paper, invariants).  The
-``rule_t_in_pool`` gate-rule variant is not implemented.
+products, closed forms, counts printed in the paper, invariants).
 """
 import ctypes
 import math
@@ -27,7 +27,7 @@ import subprocess
 import numpy as np
 
 from . import circuit  # noqa: F401
-from .circuit import SplitMix64, CutPlan, generate, grid_cut, to_text, parse_text  # noqa: F401
+from .circuit import SplitMix64, CutPlan, MultiCutPlan, generate, grid_cut, to_text, parse_text  # noqa: F401
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
@@ -154,6 +154,58 @@ def cut_amplitudes(plan, sel_u=None, sel_l=None, k_begin=0, k_end=None, out=None
                           _ptr(out, ctypes.c_double))
     assert rc == 0
     return out
+
+
+def part_state(plan, p, k):
+    """State of part p of a MultiCutPlan for its copy index k (FP64)."""
+    n_p = plan.nq[p]
+    tmpl = _encode(plan.parts[p])
+    psi = np.zeros(1 << n_p, dtype=np.complex128)
+    rc = lib().or_half_state(n_p, _ptr(tmpl, ctypes.c_int32), tmpl.shape[0], k, _ptr(psi, ctypes.c_double))
+    assert rc == 0
+    return psi
+
+
+def multi_cut_amplitudes(plan, sels=None):
+    """Section 3 / Fig. 3 multi-part cut-and-sum:
+        A(x_0, ..., x_{t-1}) = sum over l_1 .. l_{t-1} of  prod_p  S_p[l_p, l_{p+1}][x_p]
+    with S_p the state of part p for boundary values l_p (above) and l_{p+1}
+    (below).  sels[p] selects indices of part p (None: all).  Returns complex128
+    [n_{t-1}, ..., n_0] (row-major; with no selection the full vector in index
+    order x = x_0 + 2^{q_0} x_1 + ...).  The sum over the boundary bits is one
+    numpy einsum over the part tensors."""
+    t = plan.t
+    sels = sels or [None] * t
+    tensors = []
+    for p in range(t):
+        n_above = 1 << plan.c(p) if p > 0 else 1
+        n_below = 1 << plan.c(p + 1) if p < t - 1 else 1
+        sel = np.arange(1 << plan.nq[p]) if sels[p] is None else np.asarray(sels[p], dtype=np.int64)
+        S = np.zeros((n_above, n_below, sel.size), dtype=np.complex128)
+        for la in range(n_above):
+            for lb in range(n_below):
+                S[la, lb] = part_state(plan, p, plan.part_index(p, la, lb))[sel]
+        tensors.append(S)
+    # einsum subscripts: boundary j -> letter b_j, part p's index -> letter x_p
+    letters = "abcdefghijklmnopqrstuvwxyz"
+    bl = [None] + [letters[j] for j in range(1, t)]
+    xl = [letters[13 + p].upper() for p in range(t)]
+    terms, ops = [], []
+    for p in range(t):
+        above = bl[p] if p > 0 else "y"
+        below = bl[p + 1] if p < t - 1 else "z"
+        T = tensors[p]
+        if p == 0:
+            T = T[0]
+            terms.append(below + xl[p])
+        elif p == t - 1:
+            T = T[:, 0]
+            terms.append(above + xl[p])
+        else:
+            terms.append(above + below + xl[p])
+        ops.append(T)
+    out = "".join(reversed(xl))
+    return np.einsum(",".join(terms) + "->" + out, *ops, optimize=True)
 
 
 def floyd_select(rng, universe, count):

@@ -242,3 +242,92 @@ def grid_cut(R, C, depth, seed, b=None, t_in_pool=False):
         b = R // 2
     gates = generate(R, C, depth, seed, b, t_in_pool)
     return gates, CutPlan(R * C, b * C, gates)
+
+
+class MultiCutPlan:
+    """Section 3 / Fig. 3: the grid split into t row bands (parts) at the cut rows
+    r_1 < ... < r_{t-1}.  Every CZ across a band boundary is rewritten by Eq. 1: P_l
+    on its upper qubit, Z^l on its lower qubit, l one bit of the copy index, so the
+    circuit is the sum over all boundary bits of products of t part circuits.
+
+    Boundary j (between parts j-1 and j) has c_j cut CZs, numbered by (layer, upper
+    qubit) ascending; its bits form l_j in [0, 2^{c_j}).  Part p carries the Z^l
+    slots of boundary p (above it) and the P_l slots of boundary p+1 (below it).
+    Its own copy index numbers its slots by (layer, upper qubit) ascending, so
+    part_index() maps (l_p, l_{p+1}) to the part's copy index.  Parts are indexed
+    from the top; qubit q of part p is global qubit q + offset[p].
+    """
+
+    def __init__(self, R, C, cut_rows, gates):
+        rows = [0] + list(cut_rows) + [R]
+        assert all(rows[i] < rows[i + 1] for i in range(len(rows) - 1)), "cut rows must increase inside the grid"
+        self.R, self.C = R, C
+        self.t = len(rows) - 1
+        self.offset = [r * C for r in rows[:-1]]
+        self.nq = [(rows[i + 1] - rows[i]) * C for i in range(self.t)]
+        part_of = {}
+        for p in range(self.t):
+            for q in range(self.offset[p], self.offset[p] + self.nq[p]):
+                part_of[q] = p
+        # cut CZs per boundary j = 1 .. t-1 (index 0 unused)
+        self.cuts = [[] for _ in range(self.t)]
+        for g in gates:
+            if g[1] == "CZ":
+                a, b = min(g[2], g[3]), max(g[2], g[3])
+                pa, pb = part_of[a], part_of[b]
+                assert pb - pa <= 1, "a CZ may cross one boundary at most"
+                if pa != pb:
+                    self.cuts[pb].append((g[0], a, b))
+            elif g[1] not in GATE_NAMES:
+                raise ValueError("multi-part cuts take H, X2, Y2, T and CZ gates")
+        for j in range(1, self.t):
+            self.cuts[j].sort()
+        bidx = {}
+        for j in range(1, self.t):
+            for i, cz in enumerate(self.cuts[j]):
+                bidx[cz] = (j, i)
+        # each part's slots in (layer, upper qubit) order: (t, upper, boundary, bit in boundary)
+        slots = [[] for _ in range(self.t)]
+        for j in range(1, self.t):
+            for i, (tt, a, b) in enumerate(self.cuts[j]):
+                slots[j - 1].append((tt, a, j, i))
+                slots[j].append((tt, a, j, i))
+        self.local = []          # per part: {(boundary, bit): local bit}
+        for p in range(self.t):
+            slots[p].sort()
+            self.local.append({(s[2], s[3]): m for m, s in enumerate(slots[p])})
+        self.parts = [[] for _ in range(self.t)]
+        for g in gates:
+            tt = g[0]
+            if g[1] == "CZ":
+                a, b = min(g[2], g[3]), max(g[2], g[3])
+                pa, pb = part_of[a], part_of[b]
+                if pa == pb:
+                    o = self.offset[pa]
+                    self.parts[pa].append((tt, "CZ", a - o, b - o))
+                else:
+                    j, i = bidx[(tt, a, b)]
+                    self.parts[pa].append((tt, "CUTP", self.local[pa][(j, i)], a - self.offset[pa]))
+                    self.parts[pb].append((tt, "CUTZ", self.local[pb][(j, i)], b - self.offset[pb]))
+            else:
+                p = part_of[g[2]]
+                self.parts[p].append((tt, g[1], g[2] - self.offset[p]))
+
+    def c(self, j):
+        """Cut CZs across boundary j (1 .. t-1)."""
+        return len(self.cuts[j])
+
+    @property
+    def c_total(self):
+        return sum(len(self.cuts[j]) for j in range(1, self.t))
+
+    def part_bits(self, p):
+        return len(self.local[p])
+
+    def part_index(self, p, l_above, l_below):
+        """Part p's copy index for boundary values l_p = l_above and l_{p+1} = l_below."""
+        k = 0
+        for (j, i), m in self.local[p].items():
+            v = l_above if j == p else l_below
+            k |= ((v >> i) & 1) << m
+        return k
