@@ -68,6 +68,7 @@ enum {
 typedef struct sim_circuit_s* sim_circuit;
 typedef struct sim_cut_s* sim_cut_plan;
 typedef struct sim_halves_s* sim_halves;
+typedef struct sim_multi_s* sim_multi_plan;
 
 /* Circuit description for sim_build_circuit.
  *   rows, cols   grid shape R x C (R*C <= 64)
@@ -159,6 +160,38 @@ int sim_cut_ex(sim_circuit circ, int cut_row, const sim_cut_opts* opts, sim_cut_
  * (-1)^{sum over pairs of x_h x_k}.  Writes at most cap pairs; *n_out receives
  * their number.  Host only. */
 int sim_cut_output_phases(sim_cut_plan plan, int32_t* pairs_out, int cap, int* n_out);
+
+/* Multi-part cut (Section 3, Fig. 3): the grid is cut between rows r-1 and r for
+ * every r of cut_rows (strictly increasing, inside the grid), giving t = n_cut_rows
+ * + 1 row bands (parts, numbered from the top).  Every CZ across a boundary is
+ * rewritten by Eq. 1: P_l on its upper qubit, Z^l on its lower one, one copy bit
+ * l each; the amplitude is the sum over all boundary bits of the products of the
+ * t part states.  Outputs (any may be NULL): t, the cut CZs per boundary
+ * (c_out[j-1] for boundary j, n_cut_rows values) and the qubits per part (nq_out,
+ * t values).  Host only.  SIM_EUNSUPPORTED if the circuit holds a controlled X, a
+ * part exceeds 32 qubits or its copy bits exceed 40. */
+int sim_cut_multi(sim_circuit circ, int n_cut_rows, const int* cut_rows, sim_multi_plan* out, int* parts_out,
+                  int* c_out, int* nq_out);
+
+/* Amplitudes of a multi-part cut for the selected indices of every part: sels[p]
+ * is a host array of nsel[p] distinct indices < 2^{nq[p]} (sels == NULL or
+ * sels[p] == NULL: all of them in order).  Every part is evolved for each of its
+ * 2^{c_p + c_{p+1}} copies (the copy tree of Section 2.3.2 over its own cut
+ * layers), then the parts are contracted boundary by boundary from the top, each
+ * step one contraction over that boundary's copy bits.
+ *   precision, contraction   SIM_C64 with SIM_SPLIT_BF16 / SIM_SPLIT_FP16 (complex64
+ *                            out; the fp16 split keeps chained contractions within
+ *                            1e-5), or SIM_C128_PLAIN with SIM_FP64_PLAIN (complex128)
+ *   out_dev                  caller-owned device array [n_{t-1}] ... [n_0], row-major
+ *                            (x_0 fastest); with no selection the full vector in
+ *                            index order
+ * Device memory: all parts' leaves, plus after part p the partial product of
+ * 2^{c_{p+1}} n_p ... n_0 values.  Returns when the work has finished.
+ * SIM_ENOMEM if it does not fit. */
+int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, const uint64_t* const* sels,
+                         const uint64_t* nsel, void* out_dev, const sim_opts* opts, void* stream);
+
+void sim_destroy_multi(sim_multi_plan plan);
 
 /* The cut list as int32 triples {layer, upper qubit, lower qubit}, ordered by copy
  * bit m (3*c values).  *n_equiv_out (may be NULL) receives N_e of Section 3:

@@ -34,6 +34,7 @@ EXPORTS = (
     "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc", "sim_amplitudes_stats",
     "sim_evolve_halves_list", "sim_plan_levels", "sim_batch_create", "sim_batch_run", "sim_batch_results",
     "sim_batch_info", "sim_destroy_batch", "sim_born_sample", "sim_cut_ex", "sim_cut_output_phases",
+    "sim_cut_multi", "sim_multi_amplitudes", "sim_destroy_multi",
 )
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -88,6 +89,10 @@ def lib():
                                       ip, ip]),
         "sim_cut_output_phases": (ctypes.c_int, [vp, i32p, ctypes.c_int, ip]),
         "sim_cut_list": (ctypes.c_int, [vp, i32p, ip]),
+        "sim_cut_multi": (ctypes.c_int, [vp, ctypes.c_int, ip, ctypes.POINTER(vp), ip, ip, ip]),
+        "sim_multi_amplitudes": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(u64p), u64p, vp,
+                                                ctypes.POINTER(SimOpts), vp]),
+        "sim_destroy_multi": (None, [vp]),
         "sim_plan_schedule": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ip]),
         "sim_plan_levels": (ctypes.c_int, [vp, ctypes.c_int, i32p, ctypes.c_int, ip]),
         "sim_evolve_halves": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u64p, u64, u64p, u64,
@@ -217,6 +222,43 @@ def sim_cut_output_phases(plan):
     arr = (ctypes.c_int32 * max(2 * n.value, 1))()
     _check(lib().sim_cut_output_phases(plan, arr, n.value, ctypes.byref(n)))
     return [tuple(arr[2 * i:2 * i + 2]) for i in range(n.value)]
+
+
+def sim_cut_multi(circ, cut_rows):
+    """Multi-part cut at the given rows; returns (plan, t, [c_j per boundary], [qubits per part])."""
+    rows = (ctypes.c_int * len(cut_rows))(*cut_rows)
+    p = ctypes.c_void_p()
+    t = ctypes.c_int()
+    cs = (ctypes.c_int * len(cut_rows))()
+    nq = (ctypes.c_int * (len(cut_rows) + 1))()
+    _check(lib().sim_cut_multi(circ, len(cut_rows), rows, ctypes.byref(p), ctypes.byref(t), cs, nq))
+    return p.value, t.value, list(cs), list(nq)
+
+
+def sim_multi_amplitudes(plan, precision, contraction, out, sels=None, opts=None, stream=None):
+    """Amplitudes of a multi-part cut into the device tensor out ([n_{t-1}] ... [n_0]);
+    sels: list with one array (or None) per part."""
+    P = ctypes.POINTER(ctypes.c_uint64)
+    arr, ptrs, ns = None, None, None
+    keep = []
+    if sels is not None:
+        ptrs = (P * len(sels))()
+        ns = (ctypes.c_uint64 * len(sels))()
+        for i, sel in enumerate(sels):
+            if sel is None:
+                ptrs[i] = P()
+                ns[i] = 0
+            else:
+                a = np.ascontiguousarray(sel, dtype=np.uint64)
+                keep.append(a)
+                ptrs[i] = a.ctypes.data_as(P)
+                ns[i] = a.size
+    _check(lib().sim_multi_amplitudes(plan, precision, contraction, ptrs, ns, _ptr(out), _opts(opts),
+                                      _stream(stream)))
+
+
+def sim_destroy_multi(plan):
+    lib().sim_destroy_multi(plan)
 
 
 def sim_cut_list(plan, c):

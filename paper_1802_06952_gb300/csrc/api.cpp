@@ -27,6 +27,10 @@ struct sim_cut_s {
   CutPlan p;
 };
 
+struct sim_multi_s {
+  MultiPlan mp;
+};
+
 struct sim_halves_s {
   CutPlan* plan = nullptr;
   int precision = SIM_C64;
@@ -555,24 +559,26 @@ int check_device_status(DeviceInfo* di) {
 // Contraction into device memory; with st_acc / st_hist (zeroed by the caller)
 // also the statistics of the written block (fused into the split contraction's
 // epilogue; a separate pass after the FP64 contraction).
-int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cudaStream_t st,
-                    double* st_acc = nullptr, unsigned long long* st_hist = nullptr) {
+// The contraction out[M][N] (+)= sum_k lA[k][m] * lB[k][n] of two leaf arrays
+// ([K][M] and [K][N], complex64 or complex128 by precision) into device memory;
+// nq sets w = 2^nq |A|^2 of the optional statistics; lcode / ucode the optional
+// output-phase codes of the rows and columns.
+int contract_impl(const void* lA, const void* lB, int64_t K, int64_t M, int64_t N, int precision, int contraction,
+                  int accumulate, void* out, cudaStream_t st, int nq, double* st_acc = nullptr,
+                  unsigned long long* st_hist = nullptr, const uint32_t* lcode = nullptr,
+                  const uint32_t* ucode = nullptr) {
   DeviceInfo* di = nullptr;
   int rc = device_info(&di);
   if (rc) return rc;
-  const int64_t M = h->nsel[1], N = h->nsel[0];
-  const int64_t K = (int64_t)h->cs.size();
-  const int nq = h->plan->circ.n;
   if (contraction == SIM_FP64_PLAIN) {
     {
       PhaseScope ps(SIM_PHASE_FP64_GEMM, st);
       // output-phase cuts: a separate sign pass (before and after on an accumulated
       // block, which signs only this contraction's part)
-      const bool sign = h->out_code[0] && h->out_code[1];
-      if (sign && accumulate) CK(launch_out_sign(out, 1, M, N, h->out_code[1], h->out_code[0], st));
-      CK(launch_fp64_gemm(h->leafsel[1], h->leafsel[0], h->precision == SIM_C128_PLAIN, K, M, N, accumulate, out,
-                          st));
-      if (sign) CK(launch_out_sign(out, 1, M, N, h->out_code[1], h->out_code[0], st));
+      const bool sign = lcode && ucode;
+      if (sign && accumulate) CK(launch_out_sign(out, 1, M, N, lcode, ucode, st));
+      CK(launch_fp64_gemm(lA, lB, precision == SIM_C128_PLAIN, K, M, N, accumulate, out, st));
+      if (sign) CK(launch_out_sign(out, 1, M, N, lcode, ucode, st));
     }
     if (st_acc && st_hist) {
       PhaseScope ps(SIM_PHASE_STATS, st);
@@ -582,7 +588,7 @@ int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cu
   }
   if (contraction != SIM_SPLIT_BF16 && contraction != SIM_SPLIT_FP16)
     return fail(SIM_EINVAL, "unknown contraction");
-  if (h->precision != SIM_C64) return fail(SIM_EINVAL, "split contractions need complex64 halves (SIM_C64)");
+  if (precision != SIM_C64) return fail(SIM_EINVAL, "split contractions need complex64 halves (SIM_C64)");
   const int fp16 = contraction == SIM_SPLIT_FP16;
   const int64_t kpad = ((2 * K + 63) / 64) * 64;
   const int64_t N2 = 2 * N;
@@ -597,13 +603,13 @@ int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cu
   PhaseScope ps(SIM_PHASE_PACK, st);
   if (fp16) {
     CK(sc.alloc(4 * sizeof(float)));
-    CK(launch_absmax_c64(h->leafsel[1], K * M, sc.as<float>(), st));
-    CK(launch_absmax_c64(h->leafsel[0], K * N, sc.as<float>() + 2, st));
+    CK(launch_absmax_c64(lA, K * M, sc.as<float>(), st));
+    CK(launch_absmax_c64(lB, K * N, sc.as<float>() + 2, st));
     sa = sc.as<float>() + 1;
     sb = sc.as<float>() + 3;
   }
-  CK(launch_pack_a(h->leafsel[1], K, M, kpad, fp16, sa, ahi.p, alo.p, st));
-  CK(launch_pack_b(h->leafsel[0], K, N, kpad, fp16, sb, bhi.p, blo.p, st));
+  CK(launch_pack_a(lA, K, M, kpad, fp16, sa, ahi.p, alo.p, st));
+  CK(launch_pack_b(lB, K, N, kpad, fp16, sb, bhi.p, blo.p, st));
   }
   TcGemmArgs g;
   g.a_hi = ahi.p; g.a_lo = alo.p; g.b_hi = bhi.p; g.b_lo = blo.p;
@@ -618,11 +624,20 @@ int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cu
   g.w_scale = std::ldexp(1.f, nq);
   g.st_acc = st_acc;
   g.st_hist = st_hist;
-  g.out_lcode = h->out_code[1];
-  g.out_ucode = h->out_code[0];
+  g.out_lcode = lcode;
+  g.out_ucode = ucode;
   PhaseScope ps(SIM_PHASE_CONTRACT, st);
   CK(launch_tc_gemm(g, st));
   return SIM_OK;
+}
+
+// Contraction of evolved halves: rows are the lower half's selection, columns the
+// upper half's (Supplementary A, Eq. 8).
+int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cudaStream_t st,
+                    double* st_acc = nullptr, unsigned long long* st_hist = nullptr) {
+  return contract_impl(h->leafsel[1], h->leafsel[0], (int64_t)h->cs.size(), h->nsel[1], h->nsel[0], h->precision,
+                       contraction, accumulate, out, st, h->plan->circ.n, st_acc, st_hist, h->out_code[1],
+                       h->out_code[0]);
 }
 
 // stats_out from the FP64 sums {sum |A|^2, sum ln w, count of w > 0} and the
@@ -1172,6 +1187,124 @@ void sim_destroy_circuit(sim_circuit circ) { delete circ; }
 void sim_destroy_cut(sim_cut_plan plan) {
   if (!plan) return;
   free_plan_ops(plan->p);
+  delete plan;
+}
+
+int sim_cut_multi(sim_circuit circ, int n_cut_rows, const int* cut_rows, sim_multi_plan* out, int* parts_out,
+                  int* c_out, int* nq_out) {
+  API_BEGIN
+  if (!circ || !out || !cut_rows || n_cut_rows < 1) return fail(SIM_EINVAL, "circuit, cut rows and out are required");
+  *out = nullptr;
+  auto* m = new sim_multi_s();
+  std::string err = build_multi_plan(circ->c, std::vector<int>(cut_rows, cut_rows + n_cut_rows), 0, 0, m->mp);
+  if (!err.empty()) {
+    delete m;
+    return fail(err.find("more than") != std::string::npos || err.find("only") != std::string::npos
+                    ? SIM_EUNSUPPORTED
+                    : SIM_EINVAL,
+                err);
+  }
+  if (parts_out) *parts_out = m->mp.t;
+  if (c_out)
+    for (int j = 1; j < m->mp.t; ++j) c_out[j - 1] = m->mp.c[j];
+  if (nq_out)
+    for (int p = 0; p < m->mp.t; ++p) nq_out[p] = m->mp.nq[p];
+  *out = m;
+  return SIM_OK;
+  API_END
+}
+
+int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, const uint64_t* const* sels,
+                         const uint64_t* nsel, void* out_dev, const sim_opts* opts, void* stream) {
+  API_BEGIN
+  if (!plan || !out_dev) return fail(SIM_EINVAL, "plan and out_dev must not be NULL");
+  if (!is_device_ptr(out_dev)) return fail(SIM_EINVAL, "sim_multi_amplitudes writes device memory only");
+  const bool split = contraction == SIM_SPLIT_BF16 || contraction == SIM_SPLIT_FP16;
+  if (!((precision == SIM_C64 && split) || (precision == SIM_C128_PLAIN && contraction == SIM_FP64_PLAIN)))
+    return fail(SIM_EINVAL, "multi-part cuts take SIM_C64 with a split contraction or SIM_C128_PLAIN with SIM_FP64_PLAIN");
+  if (opts && opts->sweep_threads && (opts->sweep_threads < 64 || opts->sweep_threads > 256 || opts->sweep_threads % 32))
+    return fail(SIM_EINVAL, "sweep_threads must be a multiple of 32 in 64..256");
+  MultiPlan& M = plan->mp;
+  cudaStream_t st = (cudaStream_t)stream;
+  // re-plan for another fuse width or pass order
+  const int want_fuse = (opts && opts->fuse_qubits) ? opts->fuse_qubits : M.part[0].fuse_qubits;
+  const int want_order = opts ? opts->pass_order : M.part[0].pass_order;
+  if (want_fuse != M.part[0].fuse_qubits || want_order != M.part[0].pass_order) {
+    std::vector<int> rows;
+    for (int p = 1; p < M.t; ++p) rows.push_back(M.offset[p] / M.circ.C);
+    MultiPlan np;
+    std::string err = build_multi_plan(M.circ, rows, want_fuse, want_order, np);
+    if (!err.empty()) return fail(SIM_EINVAL, err);
+    for (auto& P : M.part) free_plan_ops(P);
+    M = np;
+  }
+  const int t = M.t;
+  const size_t esz = precision == SIM_C64 ? 8 : 16;
+  std::vector<int64_t> n(t);
+  std::vector<DevBuf> dsel(t), leaves(t);
+  for (int p = 0; p < t; ++p) {
+    const bool full = !sels || !sels[p];
+    n[p] = full ? (int64_t)1 << M.nq[p] : (int64_t)nsel[p];
+    if (!full) {
+      if (n[p] == 0) return fail(SIM_EINVAL, "empty selection");
+      for (int64_t i = 0; i < n[p]; ++i)
+        if (sels[p][i] >> M.nq[p]) return fail(SIM_EINVAL, "selected index out of range for its part");
+      CK(dsel[p].alloc(sizeof(uint64_t) * n[p]));
+      CK(cudaMemcpyAsync(dsel[p].p, sels[p], sizeof(uint64_t) * n[p], cudaMemcpyHostToDevice, st));
+      note_bytes(sizeof(uint64_t) * n[p], 0);
+    }
+    // the part's copies in contraction order: the bits of the boundary above it
+    // outermost, those of the boundary below it innermost
+    const int ca = p > 0 ? M.c[p] : 0, cb = p + 1 < t ? M.c[p + 1] : 0;
+    if (ca + cb > 40) return fail(SIM_EUNSUPPORTED, "a part has more than 40 copy bits");
+    CopySet cs;
+    cs.list.reserve((size_t)1 << (ca + cb));
+    for (uint64_t la = 0; la < (1ull << ca); ++la)
+      for (uint64_t lb = 0; lb < (1ull << cb); ++lb) {
+        uint64_t k = 0;
+        for (size_t m = 0; m < M.slot_bits[p].size(); ++m) {
+          const auto& jb = M.slot_bits[p][m];
+          const uint64_t v = jb.first == p ? la : lb;
+          k |= ((v >> jb.second) & 1ull) << m;
+        }
+        cs.row[k] = (int64_t)cs.list.size();
+        cs.list.push_back(k);
+      }
+    int rc = upload_plan_ops(M.part[p], st);
+    if (rc) return rc;
+    CK(leaves[p].alloc(esz * cs.size() * (size_t)n[p]));
+    rc = precision == SIM_C64
+             ? evolve_c64_half(M.part[p], 0, cs, (const uint64_t*)dsel[p].p, n[p], full, leaves[p].p, st, opts)
+             : evolve_plain_half(M.part[p], 0, cs, (const uint64_t*)dsel[p].p, n[p], full, leaves[p].p, st);
+    if (rc) return rc;
+  }
+  // the multi-way sum, one boundary at a time from the top: after part p the
+  // partial product is [l_{p+1}][x_p][x_{p-1} .. x_0], the next contraction's
+  // right operand over the copy bits l_{p+1}
+  DevBuf tb[2];
+  const void* right = leaves[0].p;
+  int64_t ncols = n[0];
+  for (int p = 1; p < t; ++p) {
+    const int64_t K = (int64_t)1 << M.c[p];
+    const int64_t rows = (p + 1 < t ? ((int64_t)1 << M.c[p + 1]) : 1) * n[p];
+    void* dst = out_dev;
+    if (p + 1 < t) {
+      CK(tb[p & 1].alloc(esz * (size_t)rows * (size_t)ncols));
+      dst = tb[p & 1].p;
+    }
+    int rc = contract_impl(leaves[p].p, right, K, rows, ncols, precision, contraction, 0, dst, st, M.circ.n);
+    if (rc) return rc;
+    right = dst;
+    ncols *= n[p];
+  }
+  CK(cudaStreamSynchronize(st));
+  return SIM_OK;
+  API_END
+}
+
+void sim_destroy_multi(sim_multi_plan plan) {
+  if (!plan) return;
+  for (auto& P : plan->mp.part) free_plan_ops(P);
   delete plan;
 }
 

@@ -9,6 +9,7 @@
 #include <set>
 #include <sstream>
 #include <stdexcept>
+#include <tuple>
 
 #include "sim_internal.h"
 
@@ -649,6 +650,78 @@ void split_passes(int n, int kmax, const std::vector<SeqItem>& items, int first_
   }
 }
 
+// The fused schedule and the plain layers of one half-circuit (or one part of a
+// multi-part cut) from its gate lists: branch[j] is the j-th layer holding its cut
+// slots, branch_bits[j] the number of copy bits those slots fix (its copy bits are
+// numbered by layer, so each level fixes the next ones).
+void build_half(const Circuit& c, const HalfGateLists& H, int n, const std::vector<int>& branch,
+                const std::vector<int>& branch_bits, int fuse, bool in_order, HalfSchedule& S,
+                std::vector<PlainLayer>& plain_layers) {
+  S.n = n;
+  // plain pass count (Section 2.4): one per non-diagonal gate, one per layer
+  // holding any diagonal gate (T, CZ, or cut slot)
+  int plain = 0;
+  for (int t = 0; t < c.depth; ++t) {
+    plain += (int)H.nondiag[t].size() + (int)H.xcuts[t].size();
+    if (H.tmask[t] || !H.cz[t].empty() || !H.cuts[t].empty()) ++plain;
+  }
+  S.plain_passes = plain;
+  // does layer 0 put H on every qubit of the half?
+  bool uniform = c.depth > 0 && (int)H.nondiag[0].size() == n && H.tmask[0] == 0 &&
+                 H.cz[0].empty() && H.cuts[0].empty();
+  if (uniform)
+    for (auto& p : H.nondiag[0])
+      if (p.second != G_H) uniform = false;
+
+  const int nlev = (int)branch.size() + 1;
+  int bits = 0;
+  for (int j = 0; j < nlev; ++j) {
+    Level L;
+    L.branch_layer = j == 0 ? -1 : branch[j - 1];
+    L.bits_before = bits;
+    bits += j > 0 ? branch_bits[j - 1] : 0;
+    L.bits_total = bits;
+    const int t_begin = j == 0 ? 0 : branch[j - 1];
+    const int t_end = j + 1 < nlev ? branch[j] : c.depth - 1;  // inclusive
+    std::vector<SeqItem> seq;
+    for (int t = t_begin; t <= t_end; ++t) {
+      const bool own_cut_layer = (j > 0 && t == t_begin);
+      if (own_cut_layer) {
+        // this level applies only the cut slots of its branch layer here.  An X^l
+        // slot becomes H Z^l H (H Z H = X, H H = I): the fused passes need no
+        // copy-dependent gate, only the diagonal slot Z^l between two H gates,
+        // whose common factor 1/2 is the same in every copy.  The X^l slots act on
+        // qubits no other gate of the layer touches.
+        std::vector<CutSlot> slots = H.cuts[t];
+        for (auto& p : H.xcuts[t]) {
+          seq.push_back(gate_item(make_gate(G_H, p.first)));
+          slots.push_back({p.first, p.second, true});
+        }
+        seq.push_back(diag_item(0, {}, slots));
+        for (auto& p : H.xcuts[t]) seq.push_back(gate_item(make_gate(G_H, p.first)));
+        continue;
+      }
+      if (!(j == 0 && t == 0 && uniform))
+        for (auto& p : H.nondiag[t]) seq.push_back(gate_item(make_gate(p.second, p.first)));
+      const bool next_branch = (j + 1 < nlev && t == t_end);
+      SeqItem d = diag_item(H.tmask[t], H.cz[t], next_branch ? std::vector<CutSlot>() : H.cuts[t]);
+      if (!d.empty_diag()) seq.push_back(d);
+    }
+    int first_src = j == 0 ? (uniform ? SRC_UNIFORM : SRC_ZERO) : SRC_PARENT;
+    split_passes(n, fuse, seq, first_src, in_order, L.passes, S.ops);
+    S.levels.push_back(L);
+  }
+
+  // plain complex128 path: per layer, one op per non-diagonal gate, then the
+  // combined diagonal of the layer with this copy's cut slots
+  plain_layers.assign(c.depth, PlainLayer());
+  for (int t = 0; t < c.depth; ++t) {
+    for (auto& p : H.nondiag[t]) plain_layers[t].gates.push_back(make_gate(p.second, p.first));
+    for (auto& p : H.xcuts[t]) plain_layers[t].gates.push_back(make_gate(G_X, p.first, p.second));
+    make_diags(H.tmask[t], H.cz[t], H.cuts[t], plain_layers[t].diags);
+  }
+}
+
 }  // namespace
 
 std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPlan& plan, int pass_order,
@@ -741,76 +814,115 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
   for (const CutCZ& x : plan.cuts)
     if (branch.empty() || branch.back() != x.t) branch.push_back(x.t);
 
-  for (int h = 0; h < 2; ++h) {
-    HalfSchedule& S = plan.sched[h];
-    const int n = h ? plan.n_l : plan.n_u;
-    S.n = n;
-    // plain pass count (Section 2.4): one per non-diagonal gate, one per layer
-    // holding any diagonal gate (T, CZ, or cut slot)
-    int plain = 0;
-    for (int t = 0; t < c.depth; ++t) {
-      plain += (int)hl[h].nondiag[t].size() + (int)hl[h].xcuts[t].size();
-      if (hl[h].tmask[t] || !hl[h].cz[t].empty() || !hl[h].cuts[t].empty()) ++plain;
-    }
-    S.plain_passes = plain;
-    // does layer 0 put H on every qubit of the half?
-    bool uniform = c.depth > 0 && (int)hl[h].nondiag[0].size() == n && hl[h].tmask[0] == 0 &&
-                   hl[h].cz[0].empty() && hl[h].cuts[0].empty();
-    if (uniform)
-      for (auto& p : hl[h].nondiag[0])
-        if (p.second != G_H) uniform = false;
+  std::vector<int> branch_bits;
+  for (int t : branch) {
+    int nb = 0;
+    for (const CutCZ& x : plan.cuts)
+      if (x.t == t) ++nb;
+    branch_bits.push_back(nb);
+  }
+  for (int h = 0; h < 2; ++h)
+    build_half(c, hl[h], h ? plan.n_l : plan.n_u, branch, branch_bits, plan.fuse_qubits, plan.pass_order == 1,
+               plan.sched[h], plan.plain[h]);
+  return "";
+}
 
-    const int nlev = (int)branch.size() + 1;
-    int bits = 0;
-    for (int j = 0; j < nlev; ++j) {
-      Level L;
-      L.branch_layer = j == 0 ? -1 : branch[j - 1];
-      L.bits_before = bits;
-      int nb = 0;
-      if (j > 0)
-        for (const CutCZ& x : plan.cuts)
-          if (x.t == L.branch_layer) ++nb;
-      bits += nb;
-      L.bits_total = bits;
-      const int t_begin = j == 0 ? 0 : branch[j - 1];
-      const int t_end = j + 1 < nlev ? branch[j] : c.depth - 1;  // inclusive
-      std::vector<SeqItem> seq;
-      for (int t = t_begin; t <= t_end; ++t) {
-        const bool own_cut_layer = (j > 0 && t == t_begin);
-        if (own_cut_layer) {
-          // this level applies only the cut slots of its branch layer here.  An X^l
-          // slot becomes H Z^l H (H Z H = X, H H = I): the fused passes need no
-          // copy-dependent gate, only the diagonal slot Z^l between two H gates,
-          // whose common factor 1/2 is the same in every copy.  The X^l slots act on
-          // qubits no other gate of the layer touches.
-          std::vector<CutSlot> slots = hl[h].cuts[t];
-          for (auto& p : hl[h].xcuts[t]) {
-            seq.push_back(gate_item(make_gate(G_H, p.first)));
-            slots.push_back({p.first, p.second, true});
-          }
-          seq.push_back(diag_item(0, {}, slots));
-          for (auto& p : hl[h].xcuts[t]) seq.push_back(gate_item(make_gate(G_H, p.first)));
-          continue;
-        }
-        if (!(j == 0 && t == 0 && uniform))
-          for (auto& p : hl[h].nondiag[t]) seq.push_back(gate_item(make_gate(p.second, p.first)));
-        const bool next_branch = (j + 1 < nlev && t == t_end);
-        SeqItem d = diag_item(hl[h].tmask[t], hl[h].cz[t], next_branch ? std::vector<CutSlot>() : hl[h].cuts[t]);
-        if (!d.empty_diag()) seq.push_back(d);
+std::string build_multi_plan(const Circuit& c, const std::vector<int>& cut_rows, int fuse_qubits, int pass_order,
+                             MultiPlan& mp) {
+  mp = MultiPlan();
+  mp.circ = c;
+  std::vector<int> rows = {0};
+  for (int r : cut_rows) rows.push_back(r);
+  rows.push_back(c.R);
+  for (size_t i = 0; i + 1 < rows.size(); ++i)
+    if (rows[i] >= rows[i + 1]) return "cut rows must increase strictly inside the grid";
+  const int fuse = fuse_qubits > 0 ? fuse_qubits : 13;
+  if (fuse < 4 || fuse > 13) return "fuse_qubits must be in 4..13";
+  if (pass_order < 0 || pass_order > 1) return "pass_order must be 0 or 1";
+  mp.t = (int)rows.size() - 1;
+  std::vector<int> part_of(c.n, 0);
+  for (int p = 0; p < mp.t; ++p) {
+    mp.offset.push_back(rows[p] * c.C);
+    mp.nq.push_back((rows[p + 1] - rows[p]) * c.C);
+    if (mp.nq.back() > 32) return "a part has more than 32 qubits";
+    for (int q = rows[p] * c.C; q < rows[p + 1] * c.C; ++q) part_of[q] = p;
+  }
+  // cut CZs per boundary, numbered by (layer, upper qubit)
+  std::vector<std::vector<CutCZ>> cuts(mp.t);
+  for (const Gate& g : c.gates) {
+    if (g.code == G_CX || g.code == G_X) return "multi-part cuts take H, X^1/2, Y^1/2, T and CZ gates only";
+    if (g.code != G_CZ) continue;
+    const int pa = part_of[g.q1], pb = part_of[g.q2];  // q1 < q2
+    if (pb - pa > 1) return "a CZ crosses more than one boundary";
+    if (pb != pa) cuts[pb].push_back({g.t, g.q1, g.q2, 0});
+  }
+  mp.c.assign(mp.t, 0);
+  std::map<std::pair<int, int>, std::pair<int, int>> where;  // (layer, upper qubit) -> (boundary, bit)
+  for (int j = 1; j < mp.t; ++j) {
+    std::sort(cuts[j].begin(), cuts[j].end(),
+              [](const CutCZ& a, const CutCZ& b2) { return a.t != b2.t ? a.t < b2.t : a.h < b2.h; });
+    mp.c[j] = (int)cuts[j].size();
+    for (int i = 0; i < mp.c[j]; ++i) where[{cuts[j][i].t, cuts[j][i].h}] = {j, i};
+  }
+  // each part's slots in (layer, upper qubit) order -> its local copy bits
+  mp.slot_bits.assign(mp.t, {});
+  std::vector<std::map<std::pair<int, int>, int>> local(mp.t);  // (boundary, bit) -> local bit
+  for (int p = 0; p < mp.t; ++p) {
+    std::vector<std::tuple<int, int, int, int>> sl;  // (layer, upper qubit, boundary, bit)
+    if (p > 0)
+      for (int i = 0; i < mp.c[p]; ++i) sl.emplace_back(cuts[p][i].t, cuts[p][i].h, p, i);
+    if (p + 1 < mp.t)
+      for (int i = 0; i < mp.c[p + 1]; ++i) sl.emplace_back(cuts[p + 1][i].t, cuts[p + 1][i].h, p + 1, i);
+    std::sort(sl.begin(), sl.end());
+    if (sl.size() > 40) return "a part has more than 40 copy bits";
+    for (size_t m = 0; m < sl.size(); ++m) {
+      mp.slot_bits[p].push_back({std::get<2>(sl[m]), std::get<3>(sl[m])});
+      local[p][{std::get<2>(sl[m]), std::get<3>(sl[m])}] = (int)m;
+    }
+  }
+  // gate lists per part
+  std::vector<HalfGateLists> hl(mp.t);
+  for (auto& H : hl) {
+    H.nondiag.assign(c.depth, {});
+    H.tmask.assign(c.depth, 0);
+    H.cz.assign(c.depth, {});
+    H.cuts.assign(c.depth, {});
+    H.xcuts.assign(c.depth, {});
+  }
+  for (const Gate& g : c.gates) {
+    const int p = part_of[g.q1];
+    const int o = mp.offset[p];
+    if (g.code == G_CZ) {
+      const int pb = part_of[g.q2];
+      if (pb == p) {
+        hl[p].cz[g.t].emplace_back(g.q1 - o, g.q2 - o);
+      } else {
+        const auto jb = where[{g.t, g.q1}];
+        hl[p].cuts[g.t].push_back({g.q1 - o, local[p][jb], false});                    // P_l above the boundary
+        hl[pb].cuts[g.t].push_back({g.q2 - mp.offset[pb], local[pb][jb], true});      // Z^l below it
       }
-      int first_src = j == 0 ? (uniform ? SRC_UNIFORM : SRC_ZERO) : SRC_PARENT;
-      split_passes(n, plan.fuse_qubits, seq, first_src, plan.pass_order == 1, L.passes, S.ops);
-      S.levels.push_back(L);
+    } else if (g.code == G_T) {
+      hl[p].tmask[g.t] |= 1u << (g.q1 - o);
+    } else {
+      hl[p].nondiag[g.t].emplace_back(g.q1 - o, g.code);
     }
-
-    // plain complex128 path: per layer, one op per non-diagonal gate, then the
-    // combined diagonal of the layer with this copy's cut slots
-    plan.plain[h].assign(c.depth, PlainLayer());
-    for (int t = 0; t < c.depth; ++t) {
-      for (auto& p : hl[h].nondiag[t]) plan.plain[h][t].gates.push_back(make_gate(p.second, p.first));
-      for (auto& p : hl[h].xcuts[t]) plan.plain[h][t].gates.push_back(make_gate(G_X, p.first, p.second));
-      make_diags(hl[h].tmask[t], hl[h].cz[t], hl[h].cuts[t], plan.plain[h][t].diags);
-    }
+  }
+  mp.part.assign(mp.t, CutPlan());
+  for (int p = 0; p < mp.t; ++p) {
+    CutPlan& P = mp.part[p];
+    P.circ = c;
+    P.n_u = mp.nq[p];
+    P.n_l = 0;
+    P.c = (int)mp.slot_bits[p].size();
+    P.fuse_qubits = fuse;
+    P.pass_order = pass_order;
+    std::vector<int> branch, bits;
+    for (int t = 0; t < c.depth; ++t)
+      if (!hl[p].cuts[t].empty()) {
+        branch.push_back(t);
+        bits.push_back((int)hl[p].cuts[t].size());
+      }
+    build_half(c, hl[p], mp.nq[p], branch, bits, fuse, pass_order == 1, P.sched[0], P.plain[0]);
   }
   return "";
 }

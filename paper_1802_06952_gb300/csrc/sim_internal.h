@@ -173,6 +173,23 @@ struct CutPlan {
   int device = -1;
 };
 
+// Multi-part cut (Section 3, Fig. 3): the grid cut into row bands; every CZ across
+// a band boundary is rewritten by Eq. 1 (P_l on its upper qubit, Z^l on its lower
+// one).  Part p carries the Z^l slots of boundary p (above it) and the P_l slots of
+// boundary p + 1 (below it); its copy bits number its slots by (layer, upper
+// qubit), so that its copy tree branches at its own slot layers.
+struct MultiPlan {
+  Circuit circ;
+  int t = 0;                        // parts
+  std::vector<int> offset, nq;      // first global qubit and qubit count per part
+  std::vector<int> c;               // cut CZs per boundary j = 1 .. t-1 (c[0] = 0)
+  // per part, per local copy bit: (boundary, bit within that boundary)
+  std::vector<std::vector<std::pair<int, int>>> slot_bits;
+  std::vector<CutPlan> part;        // part p as half 0 (sched[0], plain[0], n_u = nq[p])
+};
+std::string build_multi_plan(const Circuit& c, const std::vector<int>& cut_rows, int fuse_qubits, int pass_order,
+                             MultiPlan& mp);
+
 // Read-only view of an evolved-halves handle (defined in api.cpp), for entry
 // points kept in other files; returns false for a NULL handle.
 struct HalvesView {

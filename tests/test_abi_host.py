@@ -300,3 +300,37 @@ def test_output_phase_cuts_rejects_bad_option():
         assert rc == sim.SIM_EINVAL and not p.value
     finally:
         sim.sim_destroy_circuit(circ)
+
+
+@pytest.mark.parametrize("R,C,d,rows", [(6, 3, 12, [2, 4]), (8, 8, 22, [3, 5]), (8, 2, 12, [2, 4, 6]),
+                                        (8, 7, 10, [2, 5])])
+def test_multi_part_plan_on_the_host(R, C, d, rows):
+    """sim_cut_multi: parts and crossing counts against the oracle's multi-part plan."""
+    circ = sim.sim_build_circuit(R, C, d, 0, rows[0])
+    try:
+        plan, t, cs, nq = sim.sim_cut_multi(circ, rows)
+        sim.sim_destroy_multi(plan)
+        mp = oc.MultiCutPlan(R, C, rows, oc.generate(R, C, d, 0, rows[0]))
+        assert t == mp.t and nq == mp.nq and cs == [mp.c(j) for j in range(1, mp.t)]
+    finally:
+        sim.sim_destroy_circuit(circ)
+
+
+def test_multi_part_plan_rejects_bad_rows_and_gates():
+    circ = sim.sim_build_circuit(6, 3, 12, 1, 2)
+    try:
+        for rows in ([4, 2], [0, 3], [2, 6], [3, 3]):
+            with pytest.raises(sim.SimError) as e:
+                sim.sim_cut_multi(circ, rows)
+            assert e.value.code == sim.SIM_EINVAL, rows
+    finally:
+        sim.sim_destroy_circuit(circ)
+    from circuits import cx_cut_circuit
+    R, C, b, depth, gates = cx_cut_circuit(0)
+    circ = sim.sim_build_circuit(gate_list=oc.to_text(R, C, depth, 0, gates))
+    try:
+        with pytest.raises(sim.SimError) as e:
+            sim.sim_cut_multi(circ, [1, 3])
+        assert e.value.code == sim.SIM_EUNSUPPORTED
+    finally:
+        sim.sim_destroy_circuit(circ)

@@ -1,0 +1,126 @@
+"""GPU parity of multi-part cuts (Section 3, Fig. 3) through the C-ABI: the grid in
+three or four row bands, each part evolved for all its copies, the parts contracted
+boundary by boundary.  References: the oracle's uncut state vector (the rewrite is
+an identity) and its multi-part cut-and-sum on selections.
+
+Tolerances: FP64 plain <= 1e-12; split fp16 <= 1e-5 (two chained contractions);
+split bf16 against its per-element bound.  Each chained contraction leaves at most
+3 * 2^-16 of the magnitude sum of its products, so two steps leave at most about
+2 * 3 * 2^-16 * sum_{l1, l2} |P0| |P1| |P2|, plus the complex64 leaves' rounding."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import circuit as oc
+import paper_1802_06952_gb300 as sim
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_06952_gb300 import build
+    build.build()
+    sim.lib()
+    torch.cuda.set_device(0)
+    yield
+    sim.sim_release_cache()
+
+
+def rel_err(got, ref):
+    return float(np.max(np.abs(got - ref))) / float(np.max(np.abs(ref)))
+
+
+def run(R, C, d, seed, rows, precision, kind, sels=None, opts=None):
+    circ = sim.sim_build_circuit(R, C, d, seed, rows[0])
+    plan, t, cs, nq = sim.sim_cut_multi(circ, rows)
+    try:
+        shape = [(1 << nq[p]) if sels is None or sels[p] is None else len(sels[p]) for p in range(t)][::-1]
+        dt = torch.complex128 if kind == sim.SIM_FP64_PLAIN else torch.complex64
+        out = torch.zeros(shape, dtype=dt, device="cuda")
+        sim.sim_multi_amplitudes(plan, precision, kind, out, sels, opts)
+        return out.cpu().numpy(), cs, nq
+    finally:
+        sim.sim_destroy_multi(plan)
+        sim.sim_destroy_circuit(circ)
+
+
+def magnitude_sum(mp, sels=None):
+    """sum over the boundary bits of prod_p |S_p| (the products' magnitudes)."""
+    t = mp.t
+    ops, terms = [], []
+    letters = "abcdefgh"
+    for p in range(t):
+        na = 1 << mp.c(p) if p > 0 else 1
+        nb = 1 << mp.c(p + 1) if p < t - 1 else 1
+        sel = np.arange(1 << mp.nq[p]) if sels is None or sels[p] is None else np.asarray(sels[p])
+        S = np.zeros((na, nb, sel.size))
+        for la in range(na):
+            for lb in range(nb):
+                S[la, lb] = np.abs(oracle.part_state(mp, p, mp.part_index(p, la, lb))[sel])
+        if p == 0:
+            ops.append(S[0]); terms.append(letters[1] + "P")
+        elif p == t - 1:
+            ops.append(S[:, 0]); terms.append(letters[p] + "PQRS"[p])
+        else:
+            ops.append(S); terms.append(letters[p] + letters[p + 1] + "PQRS"[p])
+    return np.einsum(",".join(terms) + "->" + "PQRS"[:t][::-1], *ops)
+
+
+@pytest.mark.parametrize("R,C,d,seed,rows", [(6, 3, 12, 1, [2, 4]), (8, 2, 12, 0, [2, 4, 6]), (5, 4, 14, 2, [2, 4])])
+def test_multi_part_full_vector(R, C, d, seed, rows):
+    gates = oc.generate(R, C, d, seed, rows[0])
+    mp = oc.MultiCutPlan(R, C, rows, gates)
+    ref = oracle.statevector(R * C, gates).reshape([1 << q for q in mp.nq][::-1])
+    got, cs, nq = run(R, C, d, seed, rows, sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN)
+    assert cs == [mp.c(j) for j in range(1, mp.t)] and nq == mp.nq
+    assert rel_err(got, ref) <= 1e-12
+    got, _, _ = run(R, C, d, seed, rows, sim.SIM_C64, sim.SIM_SPLIT_FP16)
+    assert rel_err(got, ref) <= 1e-5
+    got, _, _ = run(R, C, d, seed, rows, sim.SIM_C64, sim.SIM_SPLIT_BF16)
+    mag = magnitude_sum(mp)
+    steps = mp.t - 1
+    bound = steps * 3 * 2.0 ** -16 * (1 + 1e-3) * mag + 2e-6 * np.max(mag)
+    assert np.all(np.abs(got - ref) <= bound)
+
+
+def test_multi_part_selections_and_options():
+    """27 qubits in three 9-qubit parts, ragged selections per part; both pass
+    formations and a narrower fuse width give the same amplitudes."""
+    R, C, d, seed, rows = 9, 3, 14, 3, [3, 6]
+    gates = oc.generate(R, C, d, seed, rows[0])
+    mp = oc.MultiCutPlan(R, C, rows, gates)
+    rng = np.random.default_rng(1)
+    sels = [np.sort(rng.permutation(1 << q)[:k]).astype(np.uint64) for q, k in zip(mp.nq, (50, 61, 37))]
+    ref = oracle.multi_cut_amplitudes(mp, [s.astype(np.int64) for s in sels])
+    got, _, _ = run(R, C, d, seed, rows, sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN, sels)
+    assert rel_err(got, ref) <= 1e-12
+    for opts in (None, {"pass_order": 1}, {"fuse_qubits": 8}):
+        got, _, _ = run(R, C, d, seed, rows, sim.SIM_C64, sim.SIM_SPLIT_FP16, sels, opts)
+        assert rel_err(got, ref) <= 1e-5, opts
+    # a part given in full among selected ones
+    sels2 = [sels[0], None, sels[2]]
+    ref2 = oracle.multi_cut_amplitudes(mp, [sels[0].astype(np.int64), None, sels[2].astype(np.int64)])
+    got, _, _ = run(R, C, d, seed, rows, sim.SIM_C64, sim.SIM_SPLIT_FP16, sels2)
+    assert rel_err(got, ref2) <= 1e-5
+
+
+def test_multi_part_argument_errors():
+    circ = sim.sim_build_circuit(6, 3, 12, 1, 2)
+    plan, t, cs, nq = sim.sim_cut_multi(circ, [2, 4])
+    try:
+        out = torch.zeros((64, 64, 64), dtype=torch.complex64, device="cuda")
+        for prec, kind in ((sim.SIM_C64, sim.SIM_FP64_PLAIN), (sim.SIM_C128_PLAIN, sim.SIM_SPLIT_BF16)):
+            with pytest.raises(sim.SimError) as e:
+                sim.sim_multi_amplitudes(plan, prec, kind, out)
+            assert e.value.code == sim.SIM_EINVAL
+        with pytest.raises(sim.SimError) as e:
+            sim.sim_multi_amplitudes(plan, sim.SIM_C64, sim.SIM_SPLIT_BF16, out,
+                                     [np.array([64], dtype=np.uint64), None, None])
+        assert e.value.code == sim.SIM_EINVAL
+    finally:
+        sim.sim_destroy_multi(plan)
+        sim.sim_destroy_circuit(circ)
