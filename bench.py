@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--q-only", action="store_true", help="profiling case: only the 42/64-qubit measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-circuit batch measurement")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GPU path on the 30-qubit circuit")
+    ap.add_argument("--no-multi", action="store_true",
+                    help="skip the multi-part cut measurement (56 qubits, three parts against two halves)")
     ap.add_argument("--no-phase-cuts", action="store_true",
                     help="skip the output-phase-cut variant of the bench workload (K = 32 instead of 256)")
     ap.add_argument("--batch-only", action="store_true", help="profiling case: only the batch measurement")
@@ -309,6 +311,58 @@ def run_phase_cuts(sim, torch, stream, out, sel, steps, warmup):
             "stats_last_step": [float(x) for x in st],
             "note": "not the graded configuration (K = 256 there); exact rewrite, checked against the oracle "
                     "in tests/test_gpu_parity.py"}
+
+
+def run_multi(sim, torch, stream, out):
+    """Multi-part cuts (Section 3, Fig. 3) against the two-part cut on one circuit:
+    56 qubits (8x7 grid), depth 10, seed 0.  Three row bands of 14, 21 and 21
+    qubits (cuts between rows 1|2 and 4|5: c = 7 + 7, the middle part with 2^14
+    copies), 2^10 seeded random indices per part = 2^30 amplitudes through two
+    chained split-fp16 contractions; and two 28-qubit halves (cut between rows 3|4,
+    c = 7) on a 2^15 x 2^15 selection = 2^30 amplitudes through one split-bf16
+    contraction.  Each timed from the evolve to the finished block (wall clock
+    after a device synchronize), best of 3 after a warm-up run."""
+    import numpy as np
+    R_, C_, D_, rows = 8, 7, 10, [2, 5]
+    circ = sim.sim_build_circuit(R_, C_, D_, 0, rows[0])
+    res = {"workload": "56-qubit 8x7 grid random circuit, depth 10, seed 0: 2^30 amplitudes of random "
+                       "bitstrings (product selections)"}
+    try:
+        plan, t, cs, nq = sim.sim_cut_multi(circ, rows)
+        rng = np.random.default_rng(0)
+        sels = [np.sort(rng.permutation(1 << q)[:1024]).astype(np.uint64) for q in nq]
+        view = out.view(-1)[:1 << 30].view(1024, 1024, 1024)
+        ts = []
+        for i in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sim.sim_multi_amplitudes(plan, sim.SIM_C64, sim.SIM_SPLIT_FP16, view, sels, stream=stream)
+            ts.append(time.perf_counter() - t0)
+        sim.sim_destroy_multi(plan)
+        ms = min(ts[1:]) * 1e3
+        res["three_part"] = {"parts_qubits": nq, "cuts_per_boundary": cs, "middle_copies": 1 << (cs[0] + cs[1]),
+                             "ms": ms, "amplitudes_per_s": (1 << 30) / (ms / 1e3), "contraction": "split-fp16 x 2"}
+        sim.sim_release_cache()
+        b2 = 4
+        plan2, c2, copies2, nu2, nl2 = sim.sim_cut(circ, b2)
+        su, sl = sim.sim_select(nu2, 1 << 15, nl2, 1 << 15, 0)
+        ts = []
+        for i in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h = sim.sim_evolve_halves(plan2, sim.SIM_C64, 0, copies2, su, sl, stream=stream)
+            sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, out, stream=stream)
+            sim.sim_status(stream)
+            ts.append(time.perf_counter() - t0)
+            sim.sim_destroy_halves(h)
+        sim.sim_destroy_cut(plan2)
+        ms2 = min(ts[1:]) * 1e3
+        res["two_part"] = {"halves_qubits": [nu2, nl2], "c": c2, "copies": copies2, "ms": ms2,
+                           "amplitudes_per_s": (1 << 30) / (ms2 / 1e3), "contraction": "split-bf16"}
+    finally:
+        sim.sim_destroy_circuit(circ)
+        sim.sim_release_cache()
+    return res
 
 
 def timed_selection_run(sim, torch, stream, plan, copies, su, sl, out):
@@ -667,6 +721,8 @@ def run_ours(args):
     if rank == 0 and args.select == 0 and not args.no_phase_cuts:
         line["output_phase_cuts"] = run_phase_cuts(sim, torch, stream, out, sel, min(args.steps, 20),
                                                    max(3, args.warmup))
+    if rank == 0 and args.select == 0 and not args.no_multi:
+        line["multi_part"] = run_multi(sim, torch, stream, out)
     if not args.no_sweep:
         line["sweep_hbm"] = sweep_hbm(sim, torch, stream)
     if rank == 0 and args.select == 0 and not args.no_plain:

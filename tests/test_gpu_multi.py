@@ -124,3 +124,38 @@ def test_multi_part_argument_errors():
     finally:
         sim.sim_destroy_multi(plan)
         sim.sim_destroy_circuit(circ)
+
+
+def test_multi_part_40q_selection():
+    """40 qubits (8x5, depth 10) in parts of 10, 15 and 15 qubits (c = 5 + 5, the
+    middle part with 1024 copies): 16 seeded indices per part against the oracle's
+    multi-part sum; the two-part cut of the same circuit at the matching entries."""
+    R, C, d, seed, rows = 8, 5, 10, 0, [2, 5]
+    gates = oc.generate(R, C, d, seed, rows[0])
+    mp = oc.MultiCutPlan(R, C, rows, gates)
+    rng = np.random.default_rng(2)
+    sels = [np.sort(rng.permutation(1 << q)[:16]).astype(np.uint64) for q in mp.nq]
+    ref = oracle.multi_cut_amplitudes(mp, [s.astype(np.int64) for s in sels])
+    got, cs, nq = run(R, C, d, seed, rows, sim.SIM_C64, sim.SIM_SPLIT_FP16, sels)
+    assert cs == [5, 5] and rel_err(got, ref) <= 1e-5
+    gotp, _, _ = run(R, C, d, seed, rows, sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN, sels)
+    assert rel_err(gotp, ref) <= 1e-12
+    # the same amplitudes through two 20-qubit halves (cut between rows 3 and 4)
+    x = (sels[0][None, None, :] | (sels[1][None, :, None] << np.uint64(10)) |
+         (sels[2][:, None, None] << np.uint64(25))).reshape(-1)
+    xu, xl = x & np.uint64((1 << 20) - 1), x >> np.uint64(20)
+    su, iu = np.unique(xu, return_inverse=True)
+    sl, il = np.unique(xl, return_inverse=True)
+    circ = sim.sim_build_circuit(R, C, d, seed, rows[0])
+    plan, c2, copies, nu, nl = sim.sim_cut(circ, 4)
+    try:
+        h = sim.sim_evolve_halves(plan, sim.SIM_C128_PLAIN, 0, copies, su, sl)
+        out = torch.zeros((sl.size, su.size), dtype=torch.complex128, device="cuda")
+        sim.sim_amplitudes(h, sim.SIM_FP64_PLAIN, False, out)
+        sim.sim_status()
+        two = out.cpu().numpy()[il, iu].reshape(ref.shape)
+        sim.sim_destroy_halves(h)
+        assert rel_err(two, ref) <= 1e-12
+    finally:
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(circ)
