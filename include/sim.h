@@ -47,7 +47,7 @@ enum {
   SIM_ENOMEM = 2,        /* host or device allocation failed */
   SIM_ECUDA = 3,         /* a CUDA runtime or driver call failed */
   SIM_ETIMEOUT = 4,      /* a device-side wait gave up (see sim_status) */
-  SIM_EUNSUPPORTED = 5   /* request outside what this build handles */
+  SIM_EUNSUPPORTED = 5   /* request outside what the library handles */
 };
 
 /* Half-state precision for sim_evolve_halves. */
