@@ -1,0 +1,112 @@
+"""Degenerate cases through the C-ABI against the oracle's uncut state vector:
+no cut at all (c = 0, one copy), halves of one to three qubits (the staged sweep
+with fewer local qubits than a warp), output-phase cuts that remove every copy
+bit, and a multi-part cut whose boundaries carry no CZ (one-copy contractions)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import circuit as oc
+import paper_1802_06952_gb300 as sim
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1802_06952_gb300 import build
+    build.build()
+    sim.lib()
+    torch.cuda.set_device(0)
+    yield
+    sim.sim_release_cache()
+
+
+def rel_err(got, ref):
+    return float(np.max(np.abs(got - ref))) / float(np.max(np.abs(ref)))
+
+
+def full_vector(R, C, d, seed, b, phase_cuts=False):
+    """(c, {contraction: amplitudes [2^n_l, 2^n_u]}) through every contraction."""
+    circ = sim.sim_build_circuit(R, C, d, seed, b)
+    plan, c, copies, nu, nl = sim.sim_cut_ex(circ, b, output_phase_cuts=phase_cuts)
+    res = {}
+    try:
+        for prec, kind in ((sim.SIM_C64, sim.SIM_SPLIT_BF16), (sim.SIM_C64, sim.SIM_SPLIT_FP16),
+                           (sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN)):
+            h = sim.sim_evolve_halves(plan, prec, 0, copies)
+            dt = torch.complex128 if kind == sim.SIM_FP64_PLAIN else torch.complex64
+            out = torch.zeros((1 << nl, 1 << nu), dtype=dt, device="cuda")
+            sim.sim_amplitudes(h, kind, False, out)
+            sim.sim_status()
+            res[kind] = out.cpu().numpy()
+            sim.sim_destroy_halves(h)
+    finally:
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(circ)
+    return c, res
+
+
+def check(res, ref, c):
+    """With one copy (c = 0) the amplitude is a single product U_0 L_0, so the bf16
+    split shows its per-product worst case: each real component keeps a residual of
+    2^-16 of itself after hi + lo and lo * lo is dropped, 3 * 2^-16 |U_0| |L_0| =
+    3 * 2^-16 |A| in all (plus the leaves' complex64 rounding).  Sums over more
+    copies average it out below 1e-5; the fp16 split stays below 1e-5 either way."""
+    if c == 0:
+        err = np.abs(res[sim.SIM_SPLIT_BF16] - ref)
+        assert np.all(err <= 3 * 2.0 ** -16 * np.abs(ref) + 2e-6 * np.max(np.abs(ref)))
+    else:
+        assert rel_err(res[sim.SIM_SPLIT_BF16], ref) <= 1e-5
+    assert rel_err(res[sim.SIM_SPLIT_FP16], ref) <= 1e-5
+    assert rel_err(res[sim.SIM_FP64_PLAIN], ref) <= 1e-12
+
+
+def test_no_cut_layers():
+    """Depth 6 reaches no CZ pattern that crosses the cut: c = 0, one copy."""
+    R, C, d, seed, b = 4, 4, 6, 3, 2
+    gates = oc.generate(R, C, d, seed, b)
+    c, res = full_vector(R, C, d, seed, b)
+    assert c == 0
+    check(res, oracle.statevector(R * C, gates).reshape(1 << 8, 1 << 8), c)
+
+
+@pytest.mark.parametrize("R,C,d,seed,b", [(2, 1, 12, 0, 1), (2, 2, 10, 1, 1), (3, 1, 17, 2, 1), (2, 3, 9, 4, 1),
+                                          (3, 2, 16, 5, 2)])
+def test_tiny_halves(R, C, d, seed, b):
+    gates = oc.generate(R, C, d, seed, b)
+    plan = oc.CutPlan(R * C, b * C, gates)
+    c, res = full_vector(R, C, d, seed, b)
+    assert c == plan.c
+    check(res, oracle.statevector(R * C, gates).reshape(1 << plan.n_l, 1 << plan.n_u), c)
+
+
+def test_output_phase_cuts_remove_every_copy_bit():
+    """Depth 8 ends on the only cut layer (7): every cut becomes an output sign."""
+    R, C, d, seed, b = 4, 4, 8, 1, 2
+    gates = oc.generate(R, C, d, seed, b)
+    c, res = full_vector(R, C, d, seed, b, phase_cuts=True)
+    assert c == 0 and oc.CutPlan(16, 8, gates).c > 0
+    check(res, oracle.statevector(16, gates).reshape(256, 256), c)
+
+
+def test_multi_part_without_crossing_cz():
+    R, C, d, seed, rows = 6, 3, 6, 2, [2, 4]
+    gates = oc.generate(R, C, d, seed, rows[0])
+    circ = sim.sim_build_circuit(R, C, d, seed, rows[0])
+    plan, t, cs, nq = sim.sim_cut_multi(circ, rows)
+    try:
+        assert cs == [0, 0]
+        ref = oracle.statevector(R * C, gates).reshape(64, 64, 64)
+        out = torch.zeros((64, 64, 64), dtype=torch.complex64, device="cuda")
+        sim.sim_multi_amplitudes(plan, sim.SIM_C64, sim.SIM_SPLIT_FP16, out)
+        assert rel_err(out.cpu().numpy(), ref) <= 1e-5
+        outp = torch.zeros((64, 64, 64), dtype=torch.complex128, device="cuda")
+        sim.sim_multi_amplitudes(plan, sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN, outp)
+        assert rel_err(outp.cpu().numpy(), ref) <= 1e-12
+    finally:
+        sim.sim_destroy_multi(plan)
+        sim.sim_destroy_circuit(circ)
