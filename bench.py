@@ -58,6 +58,9 @@ def parse():
     ap.add_argument("--q-only", action="store_true", help="profiling case: only the 42/64-qubit measurements")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-circuit batch measurement")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain FP64 GPU path on the 30-qubit circuit")
+    ap.add_argument("--host-levels", action="store_true",
+                    help="measurement case: sweeps with copy-tree levels in pinned host memory against device "
+                         "memory (one copy, 3 x --sweep-cols qubit halves; use --sweep-cols 9)")
     ap.add_argument("--no-multi", action="store_true",
                     help="skip the multi-part cut measurement (56 qubits, three parts against two halves)")
     ap.add_argument("--no-phase-cuts", action="store_true",
@@ -365,6 +368,40 @@ def run_multi(sim, torch, stream, out):
     return res
 
 
+def sweep_host_levels(sim, torch, stream, cols=9, reps=2):
+    """Copy-tree levels in pinned host memory (sim_opts.host_levels) against device
+    memory: one copy of a 54-qubit 6x9 grid circuit (depth 16, two 27-qubit halves
+    of 1.07 GB), the fused sweeps timed by the library's phase profiler.  Bytes: 16
+    per amplitude per fused pass (8 for the first)."""
+    import numpy as np
+    circ = sim.sim_build_circuit(6, cols, 16, 0, 3)
+    plan, c, copies, nu, nl = sim.sim_cut(circ, 3)
+    sel = np.zeros(1, dtype=np.uint64)
+    best = {}
+    try:
+        for host in (0, 1):
+            ts = []
+            for _ in range(reps):
+                sim.sim_profile_read(reset=True)
+                sim.sim_profile_enable(True)
+                h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, 1, sel, sel, opts={"host_levels": host},
+                                          stream=stream)
+                sim.sim_status(stream)
+                sim.sim_profile_enable(False)
+                ts.append(sim.sim_profile_read(reset=True)["ms"][sim.SIM_PHASE_SWEEP])
+                sim.sim_destroy_halves(h)
+            best[host] = min(ts)
+        passes = [sim.sim_plan_schedule(plan, hh)[1] for hh in (0, 1)]
+        gb = sum(16 * p - 8 for p in passes) * (1 << nu) / 1e9
+    finally:
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(circ)
+    return {"workload": "one copy of a %d-qubit 6x%d grid circuit, depth 16: two %d-qubit halves" % (6 * cols, cols, 3 * cols),
+            "fused_passes": passes, "device_levels_ms": best[0], "device_levels_gbs": gb / (best[0] / 1e3),
+            "host_levels_ms": best[1], "host_levels_gbs": gb / (best[1] / 1e3),
+            "note": "host levels: the sweep kernels read and write pinned host memory over NVLink-C2C"}
+
+
 def timed_selection_run(sim, torch, stream, plan, copies, su, sl, out):
     """One evolve (range of all copies, or a list) + split-bf16 contraction with the
     fused statistics, timed with CUDA events on the stream; returns (ms, phases, stats)."""
@@ -575,6 +612,10 @@ def run_ours(args):
         if rank == 0:
             print(json.dumps(sweep_hbm(sim, torch, stream, reps=1, cols=args.sweep_cols, fuse=args.sweep_fuse)),
                   flush=True)
+        return
+    if args.host_levels:
+        if rank == 0:
+            print(json.dumps(sweep_host_levels(sim, torch, stream, cols=args.sweep_cols)), flush=True)
         return
     if args.batch_only:
         if rank == 0:

@@ -102,14 +102,23 @@ typedef struct {
  *   pass_order     0: dependency-aware pass formation (a gate whose qubit does not
  *                  fit is left for a later pass, together with everything that
  *                  depends on it, and the pass goes on with the rest; fewer passes);
- *                  1: in order (a pass ends at the first gate that does not fit) */
+ *                  1: in order (a pass ends at the first gate that does not fit)
+ *   host_levels    1: the copy-tree level buffers of the complex64 sweeps (the
+ *                  half-states a level keeps for its children, Section 2.3.2, and
+ *                  the states it works on) live in pinned host memory, which the
+ *                  sweep kernels read and write over NVLink-C2C; their chunk budget
+ *                  is a quarter of the available host memory.  For halves whose
+ *                  levels do not fit in device memory; each pass then runs at the
+ *                  host link's bandwidth.  The leaves stay in device memory, and
+ *                  the results are those of device-resident levels. */
 typedef struct {
   int fuse_qubits;
   int sweep_threads;
   int gemm_group_m;
   int sweep_kernel;
   int pass_order;
-  int reserved[3];
+  int host_levels;
+  int reserved[2];
 } sim_opts;
 
 /* Build a circuit (Supplementary A, Eq. 3 circuit model; gate rules of the random

@@ -63,7 +63,7 @@ class SimCutOpts(ctypes.Structure):
 class SimOpts(ctypes.Structure):
     _fields_ = [("fuse_qubits", ctypes.c_int), ("sweep_threads", ctypes.c_int),
                 ("gemm_group_m", ctypes.c_int), ("sweep_kernel", ctypes.c_int), ("pass_order", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("host_levels", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <unistd.h>
 #include <map>
 #include <mutex>
 #include <new>
@@ -454,31 +455,68 @@ int enqueue_tree(const CutPlan& P, int h, const TreeProgram& prog, void* const* 
   return SIM_OK;
 }
 
+// Pinned host buffer that the GPU reads and writes through its unified address;
+// the owner synchronizes the stream that uses it before it is released.
+struct HostBuf {
+  void* p = nullptr;
+  HostBuf() = default;
+  HostBuf(const HostBuf&) = delete;
+  HostBuf& operator=(const HostBuf&) = delete;
+  ~HostBuf() {
+    if (p) cudaFreeHost(p);
+  }
+  cudaError_t alloc(size_t n) { return cudaHostAlloc(&p, n ? n : 1, cudaHostAllocMapped); }
+};
+
 int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel, int64_t nsel, bool full,
                     void* leafsel, cudaStream_t st, const sim_opts* opts) {
   const HalfSchedule& S = P.sched[h];
   const size_t state_bytes = sizeof(float) * 2 * ((size_t)1 << S.n);
   const int J = (int)S.levels.size();
-  // chunk capacity per level from the free device memory
-  size_t fr = 0, tot = 0;
-  CK(cudaMemGetInfo(&fr, &tot));
-  const TreeProgram prog = plan_tree(S, cs, full, (size_t)(fr * 0.6));
+  const bool host = opts && opts->host_levels;
+  // chunk capacity per level from the free device memory, or (host levels) a
+  // quarter of the available host memory
+  size_t budget = 0;
+  if (host) {
+    const long pages = sysconf(_SC_AVPHYS_PAGES), psz = sysconf(_SC_PAGESIZE);
+    if (pages <= 0 || psz <= 0) return fail(SIM_ECUDA, "cannot read the available host memory");
+    budget = (size_t)pages * (size_t)psz / 4;
+  } else {
+    size_t fr = 0, tot = 0;
+    CK(cudaMemGetInfo(&fr, &tot));
+    budget = (size_t)(fr * 0.6);
+  }
+  const TreeProgram prog = plan_tree(S, cs, full, budget);
   std::vector<DevBuf> lvl(J);
+  std::vector<HostBuf> hlvl(J);
   std::vector<void*> lp(J, nullptr);
   for (int j = 0; j < J; ++j) {
     const bool leaf = (j == J - 1);
     if (leaf && full) continue;
-    CK(lvl[j].alloc(state_bytes * (size_t)prog.level_cap[j]));
-    lp[j] = lvl[j].p;
+    const size_t bytes = state_bytes * (size_t)prog.level_cap[j];
+    if (host) {
+      if (hlvl[j].alloc(bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(SIM_ENOMEM, "cannot allocate pinned host memory for the copy-tree levels");
+      }
+      CK(cudaHostGetDevicePointer(&lp[j], hlvl[j].p, 0));
+    } else {
+      CK(lvl[j].alloc(bytes));
+      lp[j] = lvl[j].p;
+    }
   }
   DevBuf table;
   CK(table.alloc(sizeof(NodeEntry) * (prog.table.size() + 1)));
   CK(cudaMemcpyAsync(table.p, prog.table.data(), sizeof(NodeEntry) * prog.table.size(), cudaMemcpyHostToDevice, st));
   note_bytes(sizeof(NodeEntry) * prog.table.size(), 0);
-  // the pool may hand these buffers to the next call on this stream only after
-  // the launches are enqueued, which keeps reuse stream-ordered
-  return enqueue_tree(P, h, prog, lp.data(), table.as<NodeEntry>(), d_sel, nsel, leafsel, st,
-                      opts ? opts->sweep_kernel : 0, (opts && opts->sweep_threads > 0) ? opts->sweep_threads : 256);
+  // the pool may hand the device buffers to the next call on this stream only
+  // after the launches are enqueued, which keeps reuse stream-ordered; host level
+  // buffers are released after the stream has finished with them
+  const int rc = enqueue_tree(P, h, prog, lp.data(), table.as<NodeEntry>(), d_sel, nsel, leafsel, st,
+                              opts ? opts->sweep_kernel : 0,
+                              (opts && opts->sweep_threads > 0) ? opts->sweep_threads : 256);
+  if (host) CK(cudaStreamSynchronize(st));
+  return rc;
 }
 
 // ---------------------------------------------------------------------------

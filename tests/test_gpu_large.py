@@ -211,3 +211,35 @@ def test_config4_64q_seeded_copy_vs_plain_fp64():
         assert rel_err(ref, pl[:, None] * pu[None, :]) <= TOL_PLAIN
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("R,C,d,seed,b,with_oracle", [(4, 4, 10, 0, 2, True), (6, 5, 16, 1, 3, True),
+                                                      (6, 8, 16, 2, 3, False)])
+def test_host_levels_match_device_levels(R, C, d, seed, b, with_oracle):
+    """Copy-tree level buffers in pinned host memory (sim_opts.host_levels), read and
+    written by the sweep kernels over the host link: the same leaves, bit for bit, as
+    with device-resident levels (same kernels, same order), and the oracle's
+    amplitudes on a selection (where it runs in seconds).  The 6x8 case has
+    24-qubit halves (128 MB states)."""
+    gates, oplan = oc.grid_cut(R, C, d, seed, b)
+    rng = np.random.default_rng(seed)
+    su = np.sort(rng.permutation(1 << oplan.n_u)[:48]).astype(np.uint64)
+    sl = np.sort(rng.permutation(1 << oplan.n_l)[:40]).astype(np.uint64)
+    p = Plan(R, C, d, seed, b)
+    try:
+        ks = np.arange(min(p.copies, 32), dtype=np.uint64)
+        hd = p.keep(sim.sim_evolve_halves_list(p.plan, sim.SIM_C64, ks, su, sl))
+        hh = p.keep(sim.sim_evolve_halves_list(p.plan, sim.SIM_C64, ks, su, sl, opts={"host_levels": 1}))
+        for half, n in ((0, su.size), (1, sl.size)):
+            for k in (int(ks[0]), int(ks[-1])):
+                a = torch.zeros(n, dtype=torch.complex64, device="cuda")
+                bb = torch.zeros(n, dtype=torch.complex64, device="cuda")
+                sim.sim_halves_leaf(hd, half, k, a)
+                sim.sim_halves_leaf(hh, half, k, bb)
+                assert torch.equal(a, bb)
+        if with_oracle:
+            got = contract(hh, sim.SIM_SPLIT_FP16, sl.size, su.size).cpu().numpy()
+            ref = sum(oracle.cut_amplitudes(oplan, su, sl, int(k), int(k) + 1) for k in ks)
+            assert rel_err(got, ref) <= TOL_SPLIT
+    finally:
+        p.close()
