@@ -202,6 +202,16 @@ int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, co
 
 void sim_destroy_multi(sim_multi_plan plan);
 
+/* Health check of the bounded device waits.  One thread waits, with the helper
+ * every contraction kernel uses for its mbarrier waits, on a fresh shared-memory
+ * barrier that nothing arrives on.  It gives up after limit_ms (1 .. 10000),
+ * records the timeout in the device status word and returns.  The GPU is not
+ * faulted and the context stays usable.  The call waits for the stream and returns
+ * what sim_status then reports: SIM_ETIMEOUT when the machinery works (the expected
+ * result), after which the status word is clear again.  SIM_EINVAL for a limit
+ * outside the range. */
+int sim_selftest_wait(int limit_ms, void* stream);
+
 /* The cut list as int32 triples {layer, upper qubit, lower qubit}, ordered by copy
  * bit m (3*c values).  *n_equiv_out (may be NULL) receives N_e of Section 3:
  * qubits per half + log2(number of half-circuits).  Host only. */

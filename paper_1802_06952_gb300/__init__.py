@@ -34,7 +34,7 @@ EXPORTS = (
     "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc", "sim_amplitudes_stats",
     "sim_evolve_halves_list", "sim_plan_levels", "sim_batch_create", "sim_batch_run", "sim_batch_results",
     "sim_batch_info", "sim_destroy_batch", "sim_born_sample", "sim_cut_ex", "sim_cut_output_phases",
-    "sim_cut_multi", "sim_multi_amplitudes", "sim_destroy_multi",
+    "sim_cut_multi", "sim_multi_amplitudes", "sim_destroy_multi", "sim_selftest_wait",
 )
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -93,6 +93,7 @@ def lib():
         "sim_multi_amplitudes": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.POINTER(u64p), u64p, vp,
                                                 ctypes.POINTER(SimOpts), vp]),
         "sim_destroy_multi": (None, [vp]),
+        "sim_selftest_wait": (ctypes.c_int, [ctypes.c_int, vp]),
         "sim_plan_schedule": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ip]),
         "sim_plan_levels": (ctypes.c_int, [vp, ctypes.c_int, i32p, ctypes.c_int, ip]),
         "sim_evolve_halves": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u64p, u64, u64p, u64,
@@ -255,6 +256,12 @@ def sim_multi_amplitudes(plan, precision, contraction, out, sels=None, opts=None
                 ns[i] = a.size
     _check(lib().sim_multi_amplitudes(plan, precision, contraction, ptrs, ns, _ptr(out), _opts(opts),
                                       _stream(stream)))
+
+
+def sim_selftest_wait(limit_ms=100, stream=None):
+    """Health check of the bounded device waits; returns the status code
+    (SIM_ETIMEOUT when the machinery works)."""
+    return lib().sim_selftest_wait(limit_ms, _stream(stream))
 
 
 def sim_destroy_multi(plan):

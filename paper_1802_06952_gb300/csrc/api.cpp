@@ -1228,6 +1228,20 @@ void sim_destroy_cut(sim_cut_plan plan) {
   delete plan;
 }
 
+int sim_selftest_wait(int limit_ms, void* stream) {
+  API_BEGIN
+  if (limit_ms < 1 || limit_ms > 10000) return fail(SIM_EINVAL, "limit_ms must be in 1..10000");
+  DeviceInfo* di = nullptr;
+  int rc = device_info(&di);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  CK(launch_wait_selftest(di->d_status, (unsigned long long)limit_ms * 1000000ull, st));
+  note_launches(SIM_PHASE_CONTRACT, 1);
+  CK(cudaStreamSynchronize(st));
+  return check_device_status(di);
+  API_END
+}
+
 int sim_cut_multi(sim_circuit circ, int n_cut_rows, const int* cut_rows, sim_multi_plan* out, int* parts_out,
                   int* c_out, int* nq_out) {
   API_BEGIN

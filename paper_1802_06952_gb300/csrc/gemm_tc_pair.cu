@@ -107,16 +107,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                       unsigned long long limit_ns = kWaitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255u) == 0) {
       if (*abort_flag) return false;
-      if (global_ns() - t0 > kWaitNs || it > (1u << 30)) return false;
+      if (global_ns() - t0 > limit_ns || it > (1u << 30)) return false;
     }
   }
+}
+
+// Health check of the bounded waits: one thread waits, with the helper the
+// contraction kernels use, for phase 0 of a fresh barrier that nothing arrives on.
+// The wait gives up after limit_ns, the timeout is recorded in the status word and
+// the kernel returns: no trap, no hang, the context stays usable.
+__global__ void wait_selftest_kernel(int* d_status, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && !mbar_wait(smem_u32(&bar), 0u, &abort_flag, limit_ns))
+    atomicExch(d_status, SIM_TIMEOUT_CODE_SELFTEST);
 }
 
 // copy into this CTA's shared memory, completing on a barrier of either CTA of the
@@ -692,6 +710,11 @@ bool tc_gemm_pair_enabled() {
     on = (e && e[0] == '0') ? 0 : 1;
   }
   return on == 1;
+}
+
+cudaError_t launch_wait_selftest(int* d_status, unsigned long long limit_ns, cudaStream_t s) {
+  wait_selftest_kernel<<<1, 32, 0, s>>>(d_status, limit_ns);
+  return cudaGetLastError();
 }
 
 bool tc_gemm_pair_supported(const TcGemmArgs& a) {

@@ -323,6 +323,9 @@ cudaError_t launch_tc_gemm_pair(const TcGemmArgs& a, cudaStream_t s);
 constexpr int SIM_TIMEOUT_CODE_TMA = 0x101;
 constexpr int SIM_TIMEOUT_CODE_MMA = 0x102;
 constexpr int SIM_TIMEOUT_CODE_EPI = 0x103;
+constexpr int SIM_TIMEOUT_CODE_SELFTEST = 0x104;
+// the health check of the bounded waits (sim_selftest_wait)
+cudaError_t launch_wait_selftest(int* d_status, unsigned long long limit_ns, cudaStream_t s);
 
 // Plain FP64 contraction C[M][N] (+)= sum_k Lsel[k][m] * Usel[k][j] (complex128 out)
 cudaError_t launch_fp64_gemm(const void* lsel, const void* usel, int in_c128, int64_t K,

@@ -573,3 +573,26 @@ def test_output_phase_cuts_30q_sampled():
         torch.cuda.empty_cache()
     finally:
         r.close()
+
+
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """The bounded mbarrier wait of the contraction kernels, run on a barrier that
+    nothing arrives on: it gives up after 100 ms, the host reads SIM_ETIMEOUT, the
+    status word is clear afterwards, and the next contraction is correct."""
+    import time
+    t0 = time.perf_counter()
+    rc = sim.sim_selftest_wait(100)
+    dt = time.perf_counter() - t0
+    assert rc == sim.SIM_ETIMEOUT
+    assert 0.09 <= dt < 5.0
+    sim.sim_status()  # raises unless the status word is clear
+    gates, plan = oc.grid_cut(4, 4, 10, 0, 2)
+    ref = oracle.statevector(16, gates).reshape(256, 256)
+    r = Run(4, 4, 10, 0)
+    try:
+        h = r.evolve(sim.SIM_C64)
+        assert rel_err(amplitudes(h, sim.SIM_SPLIT_BF16, 256, 256).cpu().numpy(), ref) <= TOL_SPLIT
+    finally:
+        r.close()
+    with pytest.raises(sim.SimError):
+        sim._check(sim.sim_selftest_wait(0))
