@@ -1,5 +1,6 @@
 """Pins of the oracle's circuit generator and cut plan against counts printed in the
-paper (tests/golden/paper_counts.txt: Table 2, Fig. 4 caption, Fig. 1 / Sections 2.1, 3),
+paper (tests/golden/paper_counts.txt: Table 2, Fig. 4 and Fig. 3 captions, Fig. 1 /
+Sections 2.1, 3) and the partition ordering Section 3 states for Fig. 3,
 plus the generator's structural invariants (Supplementary A, Eq. 3)."""
 import numpy as np
 import pytest
@@ -34,6 +35,35 @@ def test_fig1_example():
     assert 2 * plan.copies == halves and plan.n_u == qh and plan.n_l == qh
     assert plan.n_equivalent() == n_e
     assert sorted(plan.cuts_per_layer()) == [7, 8]
+
+
+def test_fig3_two_part_equivalent_qubits():
+    (R, C, paper_depth, n_e), = golden_rows("fig3")
+    gates, plan = oc.grid_cut(R, C, paper_depth + 1, seed=0, b=R // 2)
+    assert plan.n_equivalent() == n_e
+
+
+def test_fig3_partition_ordering():
+    """Section 3 / Fig. 3: with the complexity of a partition counted as its largest
+    part plus its transformed CZs, three or four parts are no worse than two at small
+    depth, and two parts are best at depths around 22 and 30.  Fig. 3c's three-part
+    split of the 64-qubit circuit has 24 qubits in its largest part."""
+    R = C = 8
+
+    def cost(d):
+        g2 = oc.generate(R, C, d + 1, 0, 4)
+        two = 32 + oc.CutPlan(64, 32, g2).c
+        m3 = oc.MultiCutPlan(R, C, [3, 5], oc.generate(R, C, d + 1, 0, 3))
+        m4 = oc.MultiCutPlan(R, C, [2, 4, 6], oc.generate(R, C, d + 1, 0, 2))
+        return two, max(m3.nq) + m3.c_total, max(m4.nq) + m4.c_total, m3
+
+    for d in (6, 8, 10, 12):
+        two, three, four, _ = cost(d)
+        assert three <= two and four <= two
+    for d in (22, 30):
+        two, three, four, m3 = cost(d)
+        assert two < three and two < four
+        assert max(m3.nq) == 24
 
 
 @pytest.mark.parametrize("R,C,d,c", [(4, 4, 10, 4), (6, 5, 16, 8), (6, 7, 22, 14), (8, 8, 22, 16)])
