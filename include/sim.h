@@ -152,8 +152,10 @@ int sim_cut(sim_circuit circ, int cut_row, sim_cut_plan* out, int* c_out,
  *                      amplitudes as the sign (-1)^{x_h x_k} instead of being split
  *                      by Supplementary A, Eq. 1 into two copies: 2^c shrinks by 2
  *                      per such cut.  The amplitudes are the same; the leaves of
- *                      sim_halves_leaf then lack those CZs.  (Not in the paper: an
- *                      exact rewrite of the last cut layers.) */
+ *                      sim_halves_leaf then lack those CZs.  At most 32 cuts
+ *                      become signs (in copy-bit order); further ones stay copy
+ *                      bits.  (Not in the paper: an exact rewrite of the last cut
+ *                      layers.) */
 typedef struct {
   int output_phase_cuts;
   int reserved[7];
@@ -186,8 +188,8 @@ int sim_cut_multi(sim_circuit circ, int n_cut_rows, const int* cut_rows, sim_mul
  * is a host array of nsel[p] distinct indices < 2^{nq[p]} (sels == NULL or
  * sels[p] == NULL: all of them in order).  Every part is evolved for each of its
  * 2^{c_p + c_{p+1}} copies (the copy tree of Section 2.3.2 over its own cut
- * layers), then the parts are contracted boundary by boundary from the top, each
- * step one contraction over that boundary's copy bits.
+ * layers; SIM_EUNSUPPORTED above 2^24), then the parts are contracted boundary by
+ * boundary from the top, each step one contraction over that boundary's copy bits.
  *   precision, contraction   SIM_C64 with SIM_SPLIT_BF16 / SIM_SPLIT_FP16 (complex64
  *                            out; the fp16 split keeps chained contractions within
  *                            1e-5), or SIM_C128_PLAIN with SIM_FP64_PLAIN (complex128)
@@ -242,7 +244,8 @@ int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passe
  *   stream       cudaStream_t on which the work is enqueued
  * The returned handle keeps, for every copy in the range, the selected entries of
  * both leaf half-states (complex64 or complex128) for sim_amplitudes.
- * SIM_ENOMEM if the device cannot hold them. */
+ * SIM_ENOMEM if the device cannot hold them; SIM_EUNSUPPORTED for more than 2^26
+ * copies in one call (evolve copy ranges and accumulate their contractions). */
 int sim_evolve_halves(sim_cut_plan plan, int precision, uint64_t copy_begin,
                       uint64_t copy_end, const uint64_t* sel_u, uint64_t n_u,
                       const uint64_t* sel_l, uint64_t n_l, const sim_opts* opts,

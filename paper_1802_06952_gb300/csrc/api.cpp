@@ -933,6 +933,9 @@ int evolve_halves_impl(sim_cut_plan plan, int precision, CopySet&& cs, const uin
   }
   if (opts && opts->sweep_threads && (opts->sweep_threads < 64 || opts->sweep_threads > 256 || opts->sweep_threads % 32))
     return fail(SIM_EINVAL, "sweep_threads must be a multiple of 32 in 64..256");
+  // the copy tree's node table is built on the host: keep one call bounded
+  if (cs.size() > (1ull << 26))
+    return fail(SIM_EUNSUPPORTED, "more than 2^26 copies in one call: evolve copy ranges and accumulate");
   const uint64_t* sels[2] = {sel_u, sel_l};
   const uint64_t nreq[2] = {n_u, n_l};
   const int nq[2] = {P.n_u, P.n_l};
@@ -1308,7 +1311,9 @@ int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, co
     // the part's copies in contraction order: the bits of the boundary above it
     // outermost, those of the boundary below it innermost
     const int ca = p > 0 ? M.c[p] : 0, cb = p + 1 < t ? M.c[p + 1] : 0;
-    if (ca + cb > 40) return fail(SIM_EUNSUPPORTED, "a part has more than 40 copy bits");
+    // every copy of every part is listed and evolved: keep the lists (and the host
+    // memory behind them) bounded
+    if (ca + cb > 24) return fail(SIM_EUNSUPPORTED, "a part has more than 2^24 copies");
     CopySet cs;
     cs.list.reserve((size_t)1 << (ca + cb));
     for (uint64_t la = 0; la < (1ull << ca); ++la)

@@ -754,7 +754,8 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
   // (layer, upper qubit)
   for (const Gate& g : c.gates) {
     if (g.code == G_CZ && g.q1 < nu && g.q2 >= nu) {
-      if (out_phase_cuts && last_nondiag[g.q1] < g.t && last_nondiag[g.q2] < g.t) {
+      // (at most 32: the output-sign codes are 32-bit; further ones stay copy bits)
+      if (out_phase_cuts && plan.out_cz.size() < 32 && last_nondiag[g.q1] < g.t && last_nondiag[g.q2] < g.t) {
         plan.out_cz.emplace_back(g.q1, g.q2);
         out_keys.insert({g.t, g.q1});
         continue;
