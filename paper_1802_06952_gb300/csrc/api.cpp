@@ -1294,6 +1294,11 @@ int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, co
     M = np;
   }
   const int t = M.t;
+  // every copy of every part is listed and evolved: keep the lists (and the host
+  // memory behind them) bounded, before any work starts
+  for (int p = 0; p < t; ++p)
+    if ((p > 0 ? M.c[p] : 0) + (p + 1 < t ? M.c[p + 1] : 0) > 24)
+      return fail(SIM_EUNSUPPORTED, "a part has more than 2^24 copies");
   const size_t esz = precision == SIM_C64 ? 8 : 16;
   std::vector<int64_t> n(t);
   std::vector<DevBuf> dsel(t), leaves(t);
@@ -1311,9 +1316,6 @@ int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, co
     // the part's copies in contraction order: the bits of the boundary above it
     // outermost, those of the boundary below it innermost
     const int ca = p > 0 ? M.c[p] : 0, cb = p + 1 < t ? M.c[p + 1] : 0;
-    // every copy of every part is listed and evolved: keep the lists (and the host
-    // memory behind them) bounded
-    if (ca + cb > 24) return fail(SIM_EUNSUPPORTED, "a part has more than 2^24 copies");
     CopySet cs;
     cs.list.reserve((size_t)1 << (ca + cb));
     for (uint64_t la = 0; la < (1ull << ca); ++la)
