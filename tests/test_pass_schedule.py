@@ -57,3 +57,15 @@ def test_schedule_on_random_circuits(checker):
         fuse = int(rng.integers(4, 14))
         for order in (0, 1):
             run(checker, R, C, d, int(rng.integers(0, 1000)), b, fuse, order)
+
+
+@pytest.mark.parametrize("R,C,d,seed,rows", [(6, 3, 12, 1, [2, 4]), (8, 2, 12, 0, [2, 4, 6]), (8, 7, 10, 0, [2, 5]),
+                                             (9, 3, 14, 3, [3, 6]), (8, 8, 12, 1, [3, 5]), (4, 4, 10, 3, [1, 2, 3])])
+def test_multi_part_schedules(checker, R, C, d, seed, rows):
+    """Every part of a multi-part cut: its gates, its internal CZs, P_l slots for the
+    boundary below it and Z^l slots for the one above, with its own copy bits."""
+    for order in (0, 1):
+        for fuse in (4, 10, 13):
+            r = subprocess.run([checker, str(R), str(C), str(d), str(seed), "multi", str(fuse), str(order)] +
+                               [str(x) for x in rows], capture_output=True, text=True)
+            assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
