@@ -321,10 +321,22 @@ def sim_evolve_halves_list(plan, precision, copies, sel_u=None, sel_l=None, opts
 
 
 def sim_batch_create(descs, subset_idx=None, contraction=0, autotune=False, use_graph=False, stream=None):
-    """descs: list of (rows, cols, depth, seed, cut_row); subset_idx: uint64 array
-    [n_circuits, S] of flat amplitude indices (or None)."""
+    """descs: list of (rows, cols, depth, seed, cut_row), optionally extended by
+    (gate_list text or None, t_in_pool); subset_idx: uint64 array [n_circuits, S] of
+    flat amplitude indices (or None)."""
     n = len(descs)
-    arr = (_Desc * n)(*[_Desc(r, c, d, s, b, None, 0) for (r, c, d, s, b) in descs])
+    keep = []
+
+    def desc(t):
+        r, c, d, s, b = t[:5]
+        gl = t[5] if len(t) > 5 else None
+        tp = int(t[6]) if len(t) > 6 else 0
+        if gl is not None:
+            gl = gl.encode()
+            keep.append(gl)
+        return _Desc(r, c, d, s, b, gl, tp)
+
+    arr = (_Desc * n)(*[desc(t) for t in descs])
     S = 0
     ptr = None
     if subset_idx is not None:

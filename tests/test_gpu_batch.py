@@ -97,3 +97,31 @@ def test_batch_autotuned_graph_replays(reference):
             assert rows[0][3] > 0 and all(r[3] == 0 for r in rows[1:])   # tuned on the first circuit only
     finally:
         sim.sim_destroy_batch(b)
+
+
+def test_batch_with_gate_lists_and_t_in_pool():
+    """A batch mixing a generated circuit, an explicit gate list with controlled X
+    gates across the cut, and a circuit of the T-in-pool rule: statistics and a
+    random subset of every full vector against the oracle's uncut state vector."""
+    from circuits import cx_cut_circuit
+    R, C, b, depth, gates_cx = cx_cut_circuit(1)
+    descs = [(5, 4, 16, 0, 2), (R, C, depth, 0, b, oc.to_text(R, C, depth, 0, gates_cx), False),
+             (5, 4, 16, 3, 2, None, True)]
+    gate_lists = [oc.generate(5, 4, 16, 0, 2), gates_cx, oc.generate(5, 4, 16, 3, 2, t_in_pool=True)]
+    rng = np.random.default_rng(5)
+    n_sub = 512
+    idx = np.stack([rng.choice(1 << 16, n_sub, replace=False) for _ in descs]).astype(np.uint64)
+    bat = sim.sim_batch_create(descs, idx)
+    try:
+        sim.sim_batch_run(bat)
+        sim.sim_status()
+        st, sub = sim.sim_batch_results(bat, len(descs), n_sub)
+        for i, (d, g) in enumerate(zip(descs, gate_lists)):
+            n = d[0] * d[1]
+            sv = oracle.statevector(n, g)
+            ref = sv[idx[i].astype(np.int64) % (1 << n)]
+            assert abs(st[i, 0] - 1.0) <= 1e-5
+            got = sub[i]
+            assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= TOL_SPLIT, i
+    finally:
+        sim.sim_destroy_batch(bat)
