@@ -334,3 +334,18 @@ def test_multi_part_plan_rejects_bad_rows_and_gates():
         assert e.value.code == sim.SIM_EUNSUPPORTED
     finally:
         sim.sim_destroy_circuit(circ)
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch):
+    """No CPU fallback: with libsim.so absent, every entry point raises instead of
+    computing anything, and the oracle is not reachable from the library package."""
+    monkeypatch.setattr(sim, "_lib", None)
+    monkeypatch.setattr(sim, "LIB_PATH", os.path.join(ROOT, "no-such-dir", "libsim.so"))
+    with pytest.raises(RuntimeError):
+        sim.lib()
+    with pytest.raises(RuntimeError):
+        sim.sim_build_circuit(4, 4, 10, 0, 2)
+    for name in os.listdir(os.path.join(ROOT, "paper_1802_06952_gb300")):
+        if name.endswith(".py"):
+            text = open(os.path.join(ROOT, "paper_1802_06952_gb300", name)).read()
+            assert "import oracle" not in text and "from oracle" not in text, name
