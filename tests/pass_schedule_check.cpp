@@ -6,8 +6,11 @@
 // with its copy bit and type).  Diagonal terms commute with each other, so only
 // their multiset between gates is fixed.
 //
-// usage: pass_schedule_check R C depth seed cut_row fuse pass_order
+// usage: pass_schedule_check R C depth seed cut_row fuse pass_order [phase]
 //        pass_schedule_check R C depth seed multi fuse pass_order r1 [r2 ...]
+// With "phase" the plan turns the cut CZs that commute to the end of the circuit
+// (no non-diagonal gate on either qubit afterwards) into output signs; they then
+// leave the halves' events.
 // The second form checks every part of a multi-part cut at rows r1 < r2 < ...
 // (P_l slots for the boundary below a part, Z^l for the one above, with the part's
 // own copy bits).  Prints "ok <passes per half or part>" or the first difference;
@@ -173,7 +176,8 @@ int main(int argc, char** argv) {
     }
     return check_multi(circ, rows, atoi(argv[6]), atoi(argv[7]));
   }
-  if (argc != 8) return 2;
+  if (argc != 8 && !(argc == 9 && std::string(argv[8]) == "phase")) return 2;
+  const bool phase = argc == 9;
   const int b = atoi(argv[5]), fuse = atoi(argv[6]), order = atoi(argv[7]);
   Circuit circ;
   std::string err = generate_circuit(R, C, depth, seed, b, circ, 0);
@@ -182,12 +186,25 @@ int main(int argc, char** argv) {
     return 1;
   }
   CutPlan plan;
-  err = build_cut_plan(circ, b, fuse, plan, order);
+  err = build_cut_plan(circ, b, fuse, plan, order, phase);
   if (!err.empty()) {
     printf("plan: %s\n", err.c_str());
     return 1;
   }
   const int nu = plan.n_u;
+  // cut CZs that commute to the end: no non-diagonal gate on either qubit later
+  std::vector<int> last(circ.n, -1);
+  for (const Gate& g : circ.gates)
+    if (g.code != G_T && g.code != G_CZ) last[g.q1] = std::max(last[g.q1], g.t);
+  std::set<std::pair<int, int>> signs;  // (layer, upper qubit)
+  if (phase)
+    for (const Gate& g : circ.gates)
+      if (g.code == G_CZ && g.q1 < nu && g.q2 >= nu && last[g.q1] < g.t && last[g.q2] < g.t && signs.size() < 32)
+        signs.insert({g.t, g.q1});
+  if ((int)signs.size() != (int)plan.out_cz.size()) {
+    printf("output signs: want %zu, plan has %zu\n", signs.size(), plan.out_cz.size());
+    return 1;
+  }
   std::map<std::pair<int, int>, int> bit_of;  // (layer, upper qubit) -> copy bit
   for (int m = 0; m < plan.c; ++m) bit_of[{plan.cuts[m].t, plan.cuts[m].h}] = m;
   int npass[2] = {0, 0};
@@ -203,7 +220,7 @@ int main(int argc, char** argv) {
         if (in1 && in2) {
           want[g.q1 - off].push_back({false, "CZ" + std::to_string(g.q2 - off)});
           want[g.q2 - off].push_back({false, "CZ" + std::to_string(g.q1 - off)});
-        } else if (in1 || in2) {
+        } else if ((in1 || in2) && !signs.count({g.t, std::min(g.q1, g.q2)})) {
           const int m = bit_of.at({g.t, std::min(g.q1, g.q2)});
           const bool lower_end = (h == 1);
           const int q = in1 ? g.q1 - off : g.q2 - off;

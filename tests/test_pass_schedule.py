@@ -69,3 +69,15 @@ def test_multi_part_schedules(checker, R, C, d, seed, rows):
             r = subprocess.run([checker, str(R), str(C), str(d), str(seed), "multi", str(fuse), str(order)] +
                                [str(x) for x in rows], capture_output=True, text=True)
             assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+
+
+@pytest.mark.parametrize("R,C,d,seed,b", [(6, 5, 16, 1, 3), (4, 4, 8, 1, 2), (6, 10, 16, 0, 3), (8, 8, 9, 2, 4),
+                                          (5, 4, 15, 2, 2)])
+def test_output_phase_schedules(checker, R, C, d, seed, b):
+    """Output-sign cuts: the cut CZs that commute to the end leave the halves; every
+    other event stays (the checker recomputes which cuts qualify)."""
+    for order in (0, 1):
+        for fuse in (4, 13):
+            r = subprocess.run([checker, str(R), str(C), str(d), str(seed), str(b), str(fuse), str(order), "phase"],
+                               capture_output=True, text=True)
+            assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
