@@ -261,7 +261,9 @@ def sweep_hbm(sim, torch, stream, reps=3, cols=10, fuse=0):
                              "note": "passes end at the first gate that does not fit (sim_opts.pass_order = 1)"},
                 "peak_gbs": hbm,
                 "note": "fused_gbs counts the bytes the fused passes must move; plain_equiv_gbs counts the "
-                        "complex64 bytes the Section 2.4 scheme would move for the same circuit in the same time"}
+                        "complex64 bytes the Section 2.4 scheme would move for the same circuit in the same time; "
+                        "the default (dependency-aware) passes carry more gates each, so they move fewer bytes in "
+                        "less time at a lower fraction of HBM than the in-order ones"}
     finally:
         sim.sim_destroy_cut(plan)
         sim.sim_destroy_circuit(circ)
