@@ -5,9 +5,11 @@ Workload (one step = one circuit through every step of the path):
   CZ patterns 1..8, 1..7), seeds cycling 0..3, cut between rows 2 and 3: c = 8 cut
   CZs -> 256 copies of two 15-qubit halves.  Each step builds the circuit, cuts it,
   evolves all 512 half-circuits in complex64 (fused sweeps, shared prefixes), runs
-  the 32768 x 256 x 32768 complex contraction as split-bf16 products on tcgen05
+  the 32768 x 256 x 32768 complex contraction as split-fp16 products on tcgen05
   (fp32 accumulation) into all 2^30 complex64 amplitudes (8.6 GB in HBM), and
   computes the FP64 statistics (norm, mean 2^n|A|^2, mean ln, KS vs Eq. 7).
+  The error of the last timed circuit's amplitudes against the FP64 oracle is
+  measured on a block of them in the cpu_baseline leg, after the timed region.
 
 Metric: amplitudes/s (2^30 per step), whole job.  Prints one JSON line.
   --impl reference  times the FP64 CPU oracle instead (bounded samples).
@@ -52,7 +54,7 @@ def parse():
     ap.add_argument("--sweep-cols", type=int, default=10,
                     help="columns of the 6-row sweep grid (10: two 30-qubit halves)")
     ap.add_argument("--no-q42", action="store_true", help="skip the 42-qubit (6x7, depth 22, c=14) measurement")
-    ap.add_argument("--q64", type=int, default=0, metavar="LEAVES",
+    ap.add_argument("--q64", type=int, default=8, metavar="LEAVES",
                     help="also time the 64-qubit circuit (8x8, depth 22, c=16) on LEAVES seeded copies and "
                          "extrapolate to all 65536 with Eq. (2)")
     ap.add_argument("--q-only", action="store_true", help="profiling case: only the 42/64-qubit measurements")
@@ -66,6 +68,10 @@ def parse():
     ap.add_argument("--no-phase-cuts", action="store_true",
                     help="skip the output-phase-cut variant of the bench workload (K = 32 instead of 256)")
     ap.add_argument("--batch-only", action="store_true", help="profiling case: only the batch measurement")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "copies"],
+                    help="replicas: one circuit per rank per step (weak scaling, no data-path collective); "
+                         "copies: one circuit per step, its copies dealt out to the ranks as subtrees of the "
+                         "copy tree, partial blocks summed by one all-reduce (strong scaling)")
     ap.add_argument("--select", type=int, default=0,
                     help="profiling case: contract only the first S upper x S lower indices (S*S amplitudes)")
     return ap.parse_args()
@@ -155,22 +161,36 @@ def traffic_from_profile(kernel_src, summary):
         return None
 
 
-def cpu_baseline(seed=0, n=CPU_SAMPLE):
+def sample_indices(n=CPU_SAMPLE):
+    """The cpu_baseline block: n[0] upper indices 7 i mod 2^15 and n[1] lower indices
+    5 i mod 2^15 (odd multipliers, so all distinct)."""
+    import numpy as np
+    su = np.arange(n[0], dtype=np.uint64) * np.uint64(7) % np.uint64(1 << (NQ // 2))
+    sl = np.arange(n[1], dtype=np.uint64) * np.uint64(5) % np.uint64(1 << (NQ // 2))
+    return su, sl
+
+
+def cpu_baseline(seed=0, n=CPU_SAMPLE, gpu_block=None):
     """The FP64 oracle on a bounded sample of the workload: all 256 copies of both
-    halves evolved, then an n[0] x n[1] (upper x lower) block of amplitudes summed."""
+    halves evolved, then an n[0] x n[1] (upper x lower) block of amplitudes summed.
+    gpu_block (host array [n[1]][n[0]], the same block of the GPU's amplitudes of
+    the circuit of this seed) is compared with it: err = max|dA| / max|A|."""
     import numpy as np
     import oracle
     from oracle import circuit as oc
     nu, nl = n
     gates, plan = oc.grid_cut(R, C, DEPTH, seed, CUT_ROW)
-    su = np.arange(nu, dtype=np.uint64) * np.uint64(7) % np.uint64(1 << plan.n_u)
-    sl = np.arange(nl, dtype=np.uint64) * np.uint64(5) % np.uint64(1 << plan.n_l)
+    su, sl = sample_indices(n)
     t = time.perf_counter()
-    oracle.cut_amplitudes(plan, su, sl)
+    ref = oracle.cut_amplitudes(plan, su, sl)
     dt = time.perf_counter() - t
-    return {"value": nu * nl / dt, "unit": "amplitudes/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": "seed %d, all 256 copies evolved in FP64, %d x %d amplitude block (1/%d of the vector), %.1f s"
-                      % (seed, nu, nl, AMPS // (nu * nl), dt)}
+    res = {"value": nu * nl / dt, "unit": "amplitudes/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "seed %d, all 256 copies evolved in FP64, %d x %d amplitude block (1/%d of the vector), %.1f s"
+                     % (seed, nu, nl, AMPS // (nu * nl), dt)}
+    if gpu_block is not None:
+        scale = float(np.max(np.abs(ref)))
+        res["err"] = float(np.max(np.abs(gpu_block.astype(np.complex128) - ref))) / scale
+    return res
 
 
 def run_reference(args):
@@ -284,7 +304,7 @@ def run_phase_cuts(sim, torch, stream, out, sel, steps, warmup):
         circ = sim.sim_build_circuit(R_, C_, D_, SEEDS[i % len(SEEDS)], B_)
         plan, c, copies, nu, nl = sim.sim_cut_ex(circ, B_, output_phase_cuts=True)
         h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, copies, sel, sel, stream=stream)
-        st = sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_BF16, False, out, stream=stream)
+        st = sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_FP16, False, out, stream=stream)
         info["c"], info["out_cuts"] = c, len(sim.sim_cut_output_phases(plan))
         sim.sim_destroy_halves(h)
         sim.sim_destroy_cut(plan)
@@ -324,7 +344,7 @@ def run_multi(sim, torch, stream, out):
     qubits (cuts between rows 1|2 and 4|5: c = 7 + 7, the middle part with 2^14
     copies), 2^10 seeded random indices per part = 2^30 amplitudes through two
     chained split-fp16 contractions; and two 28-qubit halves (cut between rows 3|4,
-    c = 7) on a 2^15 x 2^15 selection = 2^30 amplitudes through one split-bf16
+    c = 7) on a 2^15 x 2^15 selection = 2^30 amplitudes through one split-fp16
     contraction.  Each timed from the evolve to the finished block (wall clock
     after a device synchronize), best of 3 after a warm-up run."""
     import numpy as np
@@ -356,14 +376,14 @@ def run_multi(sim, torch, stream, out):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             h = sim.sim_evolve_halves(plan2, sim.SIM_C64, 0, copies2, su, sl, stream=stream)
-            sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, out, stream=stream)
+            sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, False, out, stream=stream)
             sim.sim_status(stream)
             ts.append(time.perf_counter() - t0)
             sim.sim_destroy_halves(h)
         sim.sim_destroy_cut(plan2)
         ms2 = min(ts[1:]) * 1e3
         res["two_part"] = {"halves_qubits": [nu2, nl2], "c": c2, "copies": copies2, "ms": ms2,
-                           "amplitudes_per_s": (1 << 30) / (ms2 / 1e3), "contraction": "split-bf16"}
+                           "amplitudes_per_s": (1 << 30) / (ms2 / 1e3), "contraction": "split-fp16"}
     finally:
         sim.sim_destroy_circuit(circ)
         sim.sim_release_cache()
@@ -405,7 +425,7 @@ def sweep_host_levels(sim, torch, stream, cols=9, reps=2):
 
 
 def timed_selection_run(sim, torch, stream, plan, copies, su, sl, out):
-    """One evolve (range of all copies, or a list) + split-bf16 contraction with the
+    """One evolve (range of all copies, or a list) + split-fp16 contraction with the
     fused statistics, timed with CUDA events on the stream; returns (ms, phases, stats)."""
     sim.sim_profile_read(reset=True)
     sim.sim_profile_enable(True)
@@ -416,7 +436,7 @@ def timed_selection_run(sim, torch, stream, plan, copies, su, sl, out):
         h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, copies, su, sl, stream=stream)
     else:
         h = sim.sim_evolve_halves_list(plan, sim.SIM_C64, copies, su, sl, stream=stream)
-    st = sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_BF16, False, out, stream=stream)
+    st = sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_FP16, False, out, stream=stream)
     e1.record(stream)
     sim.sim_status(stream)
     sim.sim_profile_enable(False)
@@ -551,7 +571,8 @@ def run_batch(sim, torch, stream, reps=3):
     subset = np.stack([rng.choice(1 << (r * c), 4096, replace=False) for (r, c, d, s, b) in descs]).astype(np.uint64)
     for label, tune in (("fixed", False), ("autotuned", True)):
         t0 = time.perf_counter()
-        b = sim.sim_batch_create(descs, subset, autotune=tune, use_graph=True, stream=stream)
+        b = sim.sim_batch_create(descs, subset, contraction=sim.SIM_SPLIT_FP16, autotune=tune, use_graph=True,
+                                 stream=stream)
         t_create = time.perf_counter() - t0
         try:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -634,17 +655,39 @@ def run_ours(args):
     # pinned host buffer of the end-to-end measurement
     host = None if args.no_e2e else torch.empty((S, S), dtype=torch.complex64).pin_memory()
 
-    def step(i, target):
-        seed = SEEDS[(i * world + rank) % len(SEEDS)]
-        circ = sim.sim_build_circuit(R, C, DEPTH, seed, CUT_ROW)
+    def step_seed(i):
+        return SEEDS[(i * world + rank) % len(SEEDS)]
+
+    shard = args.shard == "copies"
+    if shard:
+        from paper_1802_06952_gb300 import dist as sdist
+        # the workload's copy tree has c = 8 cut CZs: this rank's subtrees
+        my_copies = sdist.rank_list(8, world, rank)
+
+    def step(i, target, split=sim.SIM_SPLIT_FP16):
+        circ = sim.sim_build_circuit(R, C, DEPTH, step_seed(i), CUT_ROW)
         plan, c, copies, nu, nl = sim.sim_cut(circ, CUT_ROW)
-        h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, copies, sel, sel, stream=stream)
         st = None
+        if shard:
+            # this rank's copies -> partial block; one all-reduce sums the ranks' blocks;
+            # the statistics are taken from the summed block
+            h = sim.sim_evolve_halves_list(plan, sim.SIM_C64, my_copies, sel, sel, stream=stream)
+            sim.sim_amplitudes(h, split, False, target, stream=stream)
+            if world > 1 and target.is_cuda:
+                with torch.cuda.stream(stream):
+                    sdist.reduce_amplitudes(target)
+            if target.is_cuda:
+                st = sim.sim_stats(target, False, target.numel(), NQ, stream=stream)
+            sim.sim_destroy_halves(h)
+            sim.sim_destroy_cut(plan)
+            sim.sim_destroy_circuit(circ)
+            return st
+        h = sim.sim_evolve_halves(plan, sim.SIM_C64, 0, copies, sel, sel, stream=stream)
         if target.is_cuda:
             # contraction with the FP64 statistics fused into its epilogue
-            st = sim.sim_amplitudes_stats(h, sim.SIM_SPLIT_BF16, False, target, stream=stream)
+            st = sim.sim_amplitudes_stats(h, split, False, target, stream=stream)
         else:
-            sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, False, target, stream=stream)
+            sim.sim_amplitudes(h, split, False, target, stream=stream)
         sim.sim_destroy_halves(h)
         sim.sim_destroy_cut(plan)
         sim.sim_destroy_circuit(circ)
@@ -661,6 +704,19 @@ def run_ours(args):
     for i in range(args.warmup):
         step(i, out)
     sim.sim_status(stream)
+    # a bf16-split side measurement of the same steps (not timed into the line's
+    # value): the two splits issue the same tensor-core work
+    bf16_ms = None
+    if args.select == 0:
+        eb0, eb1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        kb = min(args.steps, 10)
+        torch.cuda.synchronize()
+        eb0.record(stream)
+        for i in range(kb):
+            step(i, out, sim.SIM_SPLIT_BF16)
+        eb1.record(stream)
+        torch.cuda.synchronize()
+        bf16_ms = eb0.elapsed_time(eb1) / kb
     clk = ClockSampler(local)
     clk.start()
     time.sleep(0.2)
@@ -685,17 +741,33 @@ def run_ours(args):
     clocks = clk.stop()
     sim.sim_status(stream)
     total_ms = max_over_ranks(e0.elapsed_time(e1))
+    # after the timed region: the cpu_baseline block of the last timed circuit's
+    # amplitudes, kept on the host for the comparison with the oracle
+    last_seed = step_seed(args.warmup + args.steps - 1)
+    gpu_block = None
+    if args.select == 0 and rank == 0 and world == 1 and not args.no_cpu_baseline:
+        su_b, sl_b = sample_indices()
+        iu = torch.from_numpy(su_b.astype(np.int64)).to(out.device)
+        il = torch.from_numpy(sl_b.astype(np.int64)).to(out.device)
+        gpu_block = out.index_select(0, il).index_select(1, iu).cpu().numpy()
+        del iu, il
     step_ms = [a.elapsed_time(b) for a, b in per]
-    value = world * args.steps * amps_step / (total_ms / 1e3)
+    # replicas: every rank produced its own circuit's amplitudes; copies: the ranks
+    # together produced one circuit's per step
+    value = (1 if shard else world) * args.steps * amps_step / (total_ms / 1e3)
     ms, inst, launches = prof["ms"], prof["instances"], prof["launches"]
 
-    # dominant kernel: the tcgen05 contraction
+    # dominant kernel: the tcgen05 contraction.  Algorithmic work: 8 M N K real
+    # flops (a complex multiply-add is 4 real multiplies and 4 adds); the split
+    # issues each product three times (hi*hi, hi*lo, lo*hi): 24 M N K on the tensor pipe
     K = 256
     M = N = S
-    flops = 24.0 * M * N * K                      # issued bf16 flops (3 split products)
+    alg_flops = 8.0 * M * N * K
+    issued_flops = 3 * alg_flops
     gemm_ms = ms[sim.SIM_PHASE_CONTRACT] / max(1, inst[sim.SIM_PHASE_CONTRACT])
     hbm, bf16, bf16_sus, src = peaks()
-    achieved = flops / (gemm_ms / 1e3) / 1e12
+    achieved = alg_flops / (gemm_ms / 1e3) / 1e12
+    issued = issued_flops / (gemm_ms / 1e3) / 1e12
     # the CTA-pair kernel unless SIM_TC_PAIR=0 selects the single-CTA one
     pair = os.environ.get("SIM_TC_PAIR", "1") != "0"
     kernel_src = os.path.join(ROOT, "paper_1802_06952_gb300", "csrc", "gemm_tc_pair.cu" if pair else "gemm_tc.cu")
@@ -707,29 +779,36 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16",
-        "precision": "complex64 half-states; 3-term split-bf16 products, fp32 accumulation; FP64 statistics",
+        "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": "fp16",
+        "precision": "complex64 half-states; 3-term split-fp16 products (power-of-two pre-scaled), fp32 "
+                     "accumulation; FP64 statistics",
         "data": "synthetic: seeded random grid circuits (splitmix64 seeds 0-3), paper's circuit model",
-        "config": {"workload": WORKLOAD, "seeds": list(SEEDS), "contraction": "split-bf16 (tcgen05)",
-                   "parallelism": "one circuit per step per GPU (weak)" if world > 1 else "1 GPU",
+        "config": {"workload": WORKLOAD, "seeds": list(SEEDS), "contraction": "split-fp16 (tcgen05)",
+                   "parallelism": ("copies of one circuit dealt out to %d GPU(s) as copy-tree subtrees, one "
+                                   "all-reduce of the amplitude block per step" % world) if shard else
+                                  ("one circuit per step per GPU (weak)" if world > 1 else "1 GPU"),
                    "l2": "each step writes 8.6 GB of amplitudes (> 129 MB L2); no data carried across steps",
                    "step_ms_median": statistics.median(step_ms)},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
                      "frac": achieved / bf16, "traffic": traffic,
-                     "kernel": ("tc_gemm_pair_kernel (split-bf16 contraction, CTA pairs)" if pair
-                                else "tc_gemm_kernel (split-bf16 contraction)"),
-                     "peak_source": "%s bf16 burst" % src,
+                     "kernel": ("tc_gemm_pair_kernel (split-fp16 contraction, CTA pairs)" if pair
+                                else "tc_gemm_kernel (split-fp16 contraction)"),
+                     "peak_source": "%s bf16 burst (fp16 runs at the same kind::f16 rate)" % src,
                      "frac_of_sustained": (achieved / bf16_sus) if bf16_sus else None,
                      "peak_note": "the timed region is short (about 0.25 s) and runs at full clocks, so the burst "
                                   "peak applies; the sustained one (a 4 s cuBLAS loop, clocks down to ~1.5 GHz) is "
                                   "given for comparison",
-                     "achieved_def": "24*M*N*K issued bf16 flops (M=N=32768, K=256) / avg launch ms (CUDA events)",
+                     "achieved_def": "8*M*N*K algorithmic real flops of the complex contraction (M=N=32768, K=256) "
+                                     "/ avg launch ms (CUDA events)",
+                     "issued_tflops": issued, "issued_frac": issued / bf16,
+                     "issued_def": "24*M*N*K: the three split products (hi*hi, hi*lo, lo*hi) each issue the 8*M*N*K",
                      "launch_ms": gemm_ms},
         "phases": phases,
         "sweep": {"ms_per_step": sweep_ms, "note": "15-qubit halves are L2-resident; HBM fraction not meaningful here"},
         "gpu_launches": int(sum(launches)),
         "clocks": clocks,
         "stats_last_step": [float(x) for x in stats[-1]] if stats[-1] is not None else None,
+        "bf16_split_ms_per_step": bf16_ms,
     }
 
     # end to end through the C-ABI with a host output buffer
@@ -780,10 +859,15 @@ def run_ours(args):
     if rank == 0 and not args.no_q42 and args.select == 0:
         line["q42"] = run_q42(sim, torch, stream)
     if rank == 0 and args.q64 and args.select == 0:
-        line["q64"] = run_q64(sim, torch, stream, args.q64, achieved)
+        line["q64"] = run_q64(sim, torch, stream, args.q64, issued)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline()
+        line["cpu_baseline"] = cpu_baseline(last_seed, gpu_block=gpu_block)
+        if gpu_block is not None:
+            line["err"] = line["cpu_baseline"].pop("err")
+            line["err_def"] = ("max|dA| / max|A| of the last timed circuit (seed %d) against the FP64 oracle's "
+                               "cut-and-sum on the cpu_baseline's %d x %d block, taken after the timed region"
+                               % (last_seed, CPU_SAMPLE[0], CPU_SAMPLE[1]))
     if args.select > 0:
         line["config"]["workload"] = "PROFILING CASE (not the benchmark): first %d x %d indices of the 30-qubit workload" % (S, S)
     if rank == 0:

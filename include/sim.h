@@ -190,9 +190,12 @@ int sim_cut_multi(sim_circuit circ, int n_cut_rows, const int* cut_rows, sim_mul
  * 2^{c_p + c_{p+1}} copies (the copy tree of Section 2.3.2 over its own cut
  * layers; SIM_EUNSUPPORTED above 2^24), then the parts are contracted boundary by
  * boundary from the top, each step one contraction over that boundary's copy bits.
- *   precision, contraction   SIM_C64 with SIM_SPLIT_BF16 / SIM_SPLIT_FP16 (complex64
- *                            out; the fp16 split keeps chained contractions within
- *                            1e-5), or SIM_C128_PLAIN with SIM_FP64_PLAIN (complex128)
+ *   precision, contraction   SIM_C64 with SIM_SPLIT_FP16 (complex64 out; keeps the
+ *                            chained contractions within 1e-5) or SIM_SPLIT_BF16 (two
+ *                            parts with at least 16 copies only: chained bf16
+ *                            roundings add up past 1e-5, so three or more parts
+ *                            return SIM_EUNSUPPORTED), or SIM_C128_PLAIN with
+ *                            SIM_FP64_PLAIN (complex128)
  *   out_dev                  caller-owned device array [n_{t-1}] ... [n_0], row-major
  *                            (x_0 fastest); with no selection the full vector in
  *                            index order
@@ -280,9 +283,11 @@ int sim_halves_leaf(sim_halves h, int half, uint64_t copy, void* out_dev, void* 
  *                buffer; the call then returns after the copy has finished).
  * Accuracy of the split contractions: each product U_k L_k is off by at most
  * 3 * 2^-(2p+2) |U_k| |L_k| (p = 7 mantissa bits for bf16, 10 for fp16) plus the
- * fp32 accumulation.  Sums over many copies average the bf16 error to a few 1e-6
- * of max |A|; with few copies (a single copy: up to 4.6e-5) SIM_SPLIT_FP16 keeps
- * max|dA| / max|A| within 1e-5. */
+ * fp32 accumulation.  SIM_SPLIT_FP16 (2^-22 per product) keeps max|dA| / max|A|
+ * within 1e-5 for any number of copies.  The bf16 bound (4.6e-5 for one product)
+ * is averaged below 1e-5 only by summing many copies, so SIM_SPLIT_BF16 is
+ * refused with SIM_EUNSUPPORTED when the halves hold fewer than 16 copies
+ * (whatever accumulate says: accumulate copy batches with SIM_SPLIT_FP16). */
 int sim_amplitudes(sim_halves h, int contraction, int accumulate, void* out, void* stream);
 
 /* sim_amplitudes without allocation: the same split-precision tensor-core
@@ -291,19 +296,29 @@ int sim_amplitudes(sim_halves h, int contraction, int accumulate, void* out, voi
  * memory already belongs to its own allocator, or a latency-bound loop that cannot
  * afford cudaMalloc / cudaFree (they can block the host and synchronise the
  * device).  The paper has no counterpart; this is a deployment variant.
- *   h, contraction, accumulate   as for sim_amplitudes
- *   out_dev   caller-owned DEVICE buffer of n_l * n_u complex64 values
+ *   h, contraction, accumulate   as for sim_amplitudes (the same split-bf16 rule)
+ *   out_dev   caller-owned DEVICE buffer of n_l * n_u complex64 values on the
+ *             current device (a buffer of another device returns SIM_EINVAL)
  * Scratch: a fixed device array of SIM_NOALLOC_SCRATCH_BYTES inside the library
  * (the two split copies of both operands, 4 * (n_l + 2 n_u) * kpad bytes with
  * kpad = 2K rounded up to 64, plus 1 KiB).  Larger requests return SIM_EINVAL
- * with the number of bytes they would need.  Every GPU on which this function is
- * called holds the array until the process exits.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture begins.  All calls share the array and it keeps the previous call's contents:
- * calls whose work can overlap on the GPU (other streams, other host threads)
- * race on it and must be serialised by the caller.  The call synchronises the
- * stream and returns SIM_ETIMEOUT if a bounded device wait gave up.  It never
- * calls cudaMalloc, cudaFree or an allocating library routine. */
+ * with the number of bytes they would need.
+ * When the array comes into being: it belongs to the library's CUDA module, which
+ * the runtime loads into a device's context lazily by default, at this function's
+ * first call on that device (the call that looks up the array's device address
+ * with cudaGetSymbolAddress, with that device current).  That first call
+ * therefore reserves the SIM_NOALLOC_SCRATCH_BYTES of device memory itself: make
+ * it before the application's allocator takes the device's memory.  Under
+ * CUDA_MODULE_LOADING=EAGER every context that loads the library holds the array
+ * from the start, whether or not this function is called.  Every GPU that holds
+ * the array keeps it until the process exits.
+ * All calls share the array and it keeps the previous call's contents: calls whose
+ * work can overlap on the GPU (other streams, other host threads) race on it and
+ * must be serialised by the caller.  Every call synchronises the stream and reads
+ * a status word back from the device, so it cannot be called while the stream is
+ * being captured into a CUDA graph.  It returns SIM_ETIMEOUT if a bounded device
+ * wait gave up.  It never calls cudaMalloc, cudaFree or an allocating library
+ * routine. */
 #define SIM_NOALLOC_SCRATCH_BYTES (32u << 20)
 int sim_amplitudes_noalloc(sim_halves h, int contraction, int accumulate, void* out_dev,
                            void* stream);
@@ -337,7 +352,7 @@ int sim_amplitudes_stats(sim_halves h, int contraction, int accumulate, void* ou
 int sim_select(int nq_u, uint64_t n_u, int nq_l, uint64_t n_l, uint64_t seed,
                uint64_t* sel_u_out, uint64_t* sel_l_out);
 
-/* Selection + evolution + split-bf16 contraction + statistics in one call:
+/* Selection + evolution + split-fp16 contraction + statistics in one call:
  * draws the selection (sim_select), evolves all copies in complex64, writes the
  * [n_l][n_u] complex64 block to amps_dev_out (caller-owned device memory) and the
  * statistics to stats_out (may be NULL).  Synchronises the stream. */
@@ -407,7 +422,8 @@ int sim_born_sample(const void* amps_dev, uint64_t count, int n_qubits, uint64_t
 typedef struct sim_batch_s* sim_batch;
 
 /* Batch options (NULL: defaults; zero fields mean the default).
- *   contraction  SIM_SPLIT_BF16 (default) or SIM_SPLIT_FP16
+ *   contraction  SIM_SPLIT_BF16 (default; refused with SIM_EUNSUPPORTED at
+ *                creation if a circuit has fewer than 16 copies) or SIM_SPLIT_FP16
  *   autotune     0: fixed choices (fused-pass width 13, CTA-pair contraction with
  *                raster groups of 32); 1: for each circuit shape (rows, cols, cut
  *                row, cut CZs c), time fuse widths 10..13 and three contraction tile

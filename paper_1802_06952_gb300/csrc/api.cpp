@@ -673,6 +673,8 @@ int contract_impl(const void* lA, const void* lB, int64_t K, int64_t M, int64_t 
 // upper half's (Supplementary A, Eq. 8).
 int amplitudes_impl(sim_halves h, int contraction, int accumulate, void* out, cudaStream_t st,
                     double* st_acc = nullptr, unsigned long long* st_hist = nullptr) {
+  const int rc = check_split_bf16(contraction, (int64_t)h->cs.size(), false);
+  if (rc) return rc;
   return contract_impl(h->leafsel[1], h->leafsel[0], (int64_t)h->cs.size(), h->nsel[1], h->nsel[0], h->precision,
                        contraction, accumulate, out, st, h->plan->circ.n, st_acc, st_hist, h->out_code[1],
                        h->out_code[0]);
@@ -739,6 +741,19 @@ bool halves_view(const sim_halves_s* h, HalvesView* v) {
 }
 
 int set_error(int code, const std::string& msg) { return fail(code, msg); }
+
+int check_split_bf16(int contraction, int64_t copies, bool chained) {
+  if (contraction != SIM_SPLIT_BF16) return SIM_OK;
+  if (chained)
+    return fail(SIM_EUNSUPPORTED,
+                "split-bf16 is not offered for chained contractions (three or more parts): their roundings add up "
+                "past 1e-5 of max|A|; use SIM_SPLIT_FP16");
+  if (copies < kBf16MinCopies)
+    return fail(SIM_EUNSUPPORTED, "split-bf16 needs at least " + std::to_string(kBf16MinCopies) +
+                                      " copies in one contraction to stay within 1e-5 of max|A| (this one sums " +
+                                      std::to_string(copies) + "); use SIM_SPLIT_FP16");
+  return SIM_OK;
+}
 
 void note_launches(int phase, int count) {
   Profiler& P = prof();
@@ -1155,9 +1170,9 @@ int sim_sample(sim_cut_plan plan, uint64_t n_u, uint64_t n_l, uint64_t seed, uin
   rc = sim_evolve_halves(plan, SIM_C64, 0, 1ull << P.c, sel_u_out, uu, sel_l_out, ll, opts, stream, &h);
   if (rc) return rc;
   if (stats_out)
-    rc = sim_amplitudes_stats(h, SIM_SPLIT_BF16, 0, amps_dev_out, stats_out, nullptr, stream);
+    rc = sim_amplitudes_stats(h, SIM_SPLIT_FP16, 0, amps_dev_out, stats_out, nullptr, stream);
   else
-    rc = sim_amplitudes(h, SIM_SPLIT_BF16, 0, amps_dev_out, stream);
+    rc = sim_amplitudes(h, SIM_SPLIT_FP16, 0, amps_dev_out, stream);
   sim_destroy_halves(h);
   if (rc) return rc;
   return sim_status(stream);
@@ -1294,6 +1309,10 @@ int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, co
     M = np;
   }
   const int t = M.t;
+  {
+    const int rc = check_split_bf16(contraction, t > 1 ? (int64_t)1 << M.c[1] : 1, t > 2);
+    if (rc) return rc;
+  }
   // every copy of every part is listed and evolved: keep the lists (and the host
   // memory behind them) bounded, before any work starts
   for (int p = 0; p < t; ++p)

@@ -344,6 +344,10 @@ int sim_batch_create(const sim_circuit_desc* descs, int n_circuits, const uint64
       it.N = (int64_t)1 << it.plan.n_u;
       it.K = (int64_t)1 << it.plan.c;
       it.kpad = ((2 * it.K + 63) / 64) * 64;
+      {
+        const int rc = check_split_bf16(contraction, it.K, false);
+        if (rc) return set_error(rc, "circuit " + std::to_string(i) + ": " + sim_last_error());
+      }
       if (it.n > 34) return set_error(SIM_EUNSUPPORTED, "a batch evaluates full vectors of at most 34 qubits");
       for (uint64_t j = 0; j < subset_n; ++j)
         if (subset_idx[(size_t)i * subset_n + j] >> it.n)

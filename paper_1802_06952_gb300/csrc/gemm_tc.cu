@@ -569,13 +569,15 @@ cudaError_t launch_tc_gemm_single(const TcGemmArgs& a, cudaStream_t s) {
   k.w_scale = a.w_scale;
   k.st_acc = a.st_acc;
   k.st_hist = a.st_hist;
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+  static DeviceOnce attr;
+  {
+    cudaError_t e = attr.run([](int&) {
+      cudaError_t r = cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      if (r == cudaSuccess)
+        r = cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+      return r;
+    });
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   int grid = a.num_sms > 0 ? a.num_sms : 148;
   if ((int64_t)grid > k.num_tiles) grid = (int)k.num_tiles;

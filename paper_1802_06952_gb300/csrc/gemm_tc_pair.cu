@@ -674,23 +674,29 @@ cudaError_t launch_variant(const CUtensorMap (&maps)[4], const CUtensorMap& mapC
                            int num_sms, cudaStream_t s) {
   constexpr int SMEM = PairSmem<STG, SW, NBUF, EW>::BYTES;
   constexpr int THREADS = 32 * (2 + EW);
-  static int max_pairs = 0;
-  if (max_pairs == 0) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
-    if (e != cudaSuccess) return e;
-    // one resident pair per SM pair: as many clusters as can be co-scheduled at once
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * (unsigned)(num_sms / 2), 1, 1);
-    cfg.blockDim = dim3(THREADS, 1, 1);
-    cfg.dynamicSmemBytes = SMEM;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW>, &cfg) != cudaSuccess || n < 1) {
-      cudaGetLastError();
-      n = num_sms / 2;
-    }
-    max_pairs = n;
-  }
+  static DeviceOnce setup;
+  int max_pairs = 0;
+  cudaError_t e = setup.run(
+      [&](int& n) {
+        cudaError_t r = cudaFuncSetAttribute(tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (r != cudaSuccess) return r;
+        // one resident pair per SM pair: as many clusters as can be co-scheduled at once
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * (unsigned)(num_sms / 2), 1, 1);
+        cfg.blockDim = dim3(THREADS, 1, 1);
+        cfg.dynamicSmemBytes = SMEM;
+        n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW>, &cfg) !=
+                cudaSuccess ||
+            n < 1) {
+          cudaGetLastError();
+          n = num_sms / 2;
+        }
+        return cudaSuccess;
+      },
+      &max_pairs);
+  if (e != cudaSuccess) return e;
   int pairs = max_pairs;
   if ((int64_t)pairs > k.num_tiles) pairs = (int)k.num_tiles;
   if (pairs < 1) pairs = 1;

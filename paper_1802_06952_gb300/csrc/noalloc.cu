@@ -64,11 +64,25 @@ extern "C" int sim_amplitudes_noalloc(sim_halves h, int contraction, int accumul
   if (contraction != SIM_SPLIT_BF16 && contraction != SIM_SPLIT_FP16)
     return set_error(SIM_EINVAL, "sim_amplitudes_noalloc supports SIM_SPLIT_BF16 and SIM_SPLIT_FP16 only");
   if (v.precision != SIM_C64) return set_error(SIM_EINVAL, "split contractions need complex64 halves (SIM_C64)");
+  {
+    const int rc = check_split_bf16(contraction, (int64_t)v.K, false);
+    if (rc) return rc;
+  }
   cudaPointerAttributes pa;
   if (cudaPointerGetAttributes(&pa, out_dev) != cudaSuccess ||
       (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged)) {
     cudaGetLastError();
     return set_error(SIM_EINVAL, "sim_amplitudes_noalloc writes device memory only (out_dev is not device memory)");
+  }
+  if (pa.type == cudaMemoryTypeDevice) {
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(SIM_ECUDA, "sim_amplitudes_noalloc: cudaGetDevice failed");
+    }
+    if (pa.device != cur)
+      return set_error(SIM_EINVAL, "sim_amplitudes_noalloc: out_dev is memory of device " + std::to_string(pa.device) +
+                                       ", not of the current device " + std::to_string(cur));
   }
   const int64_t M = v.nsel[1], N = v.nsel[0];
   const int64_t K = (int64_t)v.K;

@@ -4,12 +4,42 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 #include <vector>
 
 struct sim_halves_s;
 
 namespace sim {
+
+// One-time set-up per device.  Function attributes (the dynamic shared-memory
+// opt-in) and occupancy answers belong to a device's context, so a process that
+// launches on several devices sets each one up with that device current.
+// run(fn) calls fn(value) once per device ordinal under a lock and caches the int
+// it writes; later calls on that device return the cached value.
+constexpr int kMaxDeviceSlots = 64;
+struct DeviceOnce {
+  std::mutex mu;
+  bool done[kMaxDeviceSlots] = {};
+  int value[kMaxDeviceSlots] = {};
+  template <class F>
+  cudaError_t run(F&& fn, int* value_out = nullptr) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDeviceSlots) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!done[dev]) {
+      int v = 0;
+      e = fn(v);
+      if (e != cudaSuccess) return e;
+      value[dev] = v;
+      done[dev] = true;
+    }
+    if (value_out) *value_out = value[dev];
+    return cudaSuccess;
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Circuit IR (Supplementary A, Eq. 3: layers of single-qubit gates and CZ edges)
@@ -202,6 +232,16 @@ struct HalvesView {
 bool halves_view(const sim_halves_s* h, HalvesView* v);
 // Sets the thread's last-error text and returns code.
 int set_error(int code, const std::string& msg);
+
+// Accuracy rule of the split-bf16 contraction.  Each bf16 hi/lo pair keeps a
+// residual of up to 2^-17 of its value, so one product U_k L_k can be off by
+// 3 * 2^-16 |U_k| |L_k| (4.6e-5 relative): only a sum over many copies, whose
+// rounding errors do not line up, stays within 1e-5 of max |A|.  Split-bf16 is
+// therefore refused (SIM_EUNSUPPORTED, naming SIM_SPLIT_FP16, whose residual is
+// 2^-22) for fewer than kBf16MinCopies copies in one contraction and for chained
+// contractions (multi-part sums of three or more parts), whose roundings add up.
+constexpr int64_t kBf16MinCopies = 16;
+int check_split_bf16(int contraction, int64_t copies, bool chained);
 
 // Phase profiler hooks (api.cpp): kernel launch and host<->device byte counters.
 void note_launches(int phase, int count);

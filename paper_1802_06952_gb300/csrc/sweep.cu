@@ -289,12 +289,13 @@ cudaError_t launch_sweep_c64(const SweepLaunch& L, cudaStream_t s) {
   a.init_val = (float)ldexp(1.0, -(L.n / 2)) * ((L.n & 1) ? 0.70710678118654752f : 1.f);
   const int threads = L.threads > 0 ? L.threads : 256;
   const size_t smem = sizeof(float2) << L.k;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_c64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(float2) << 13));
+  static DeviceOnce attr;
+  {
+    cudaError_t e = attr.run([](int&) {
+      return cudaFuncSetAttribute(sweep_c64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(float2) << 13));
+    });
     if (e != cudaSuccess) return e;
-    attr_set = true;
   }
   const uint64_t bps = 1ull << (L.n - L.k);
   // keep each launch below 2^30 blocks

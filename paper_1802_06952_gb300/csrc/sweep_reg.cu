@@ -508,12 +508,13 @@ template <int R>
 cudaError_t launch_r(const RegArgs& a, int64_t nslots, int use_smem, cudaStream_t s) {
   const uint32_t xs_bytes = use_smem ? (uint32_t)(sizeof(float2) << (8 + R)) : 0u;
   const size_t smem = xs_bytes + (size_t)a.op_count * sizeof(OpRec);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(sweep_reg_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)((sizeof(float2) << (8 + R)) + kMaxPassOps * sizeof(OpRec)));
+  static DeviceOnce attr;
+  {
+    cudaError_t e = attr.run([](int&) {
+      return cudaFuncSetAttribute(sweep_reg_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)((sizeof(float2) << (8 + R)) + kMaxPassOps * sizeof(OpRec)));
+    });
     if (e != cudaSuccess) return e;
-    attr = true;
   }
   const uint64_t bps = 1ull << (a.n - a.k);
   const int64_t max_slots = (int64_t)((1ull << 30) / bps) > 0 ? (int64_t)((1ull << 30) / bps) : 1;

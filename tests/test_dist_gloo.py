@@ -24,6 +24,41 @@ def test_copy_ranges_partition():
             assert max(sizes) - min(sizes) <= 1
 
 
+def test_copy_lists_partition():
+    for c in (0, 3, 8, 14):
+        for world in (1, 2, 3, 8):
+            ls = sdist.copy_lists(c, world)
+            allk = np.sort(np.concatenate(ls))
+            assert np.array_equal(allk, np.arange(1 << c, dtype=np.uint64))
+            sizes = [x.size for x in ls]
+            assert max(sizes) - min(sizes) <= 1
+
+
+def test_copy_lists_are_subtrees_of_the_copy_tree():
+    """The 64-qubit circuit's copy tree (8x8, depth 22, c = 16, levels fixing 4, 8,
+    12 and 16 copy bits, read from the library's plan): dealt out by copy_lists, the
+    ranks' tree nodes add up to the full tree's at every level (no node evolved
+    twice), while contiguous ranges of k make every rank evolve every node of the
+    early levels."""
+    import paper_1802_06952_gb300 as sim
+    circ = sim.sim_build_circuit(8, 8, 22, 0, 4)
+    plan, c, copies, nu, nl = sim.sim_cut(circ, 4)
+    try:
+        for half in (0, 1):
+            bits = [int(b1) for (_, _, b1, _) in sim.sim_plan_levels(plan, half)]
+            assert bits[-1] == c == 16
+            full = [1 << b for b in bits]
+            for world in (2, 4, 8, 16):
+                nodes = np.array([sdist.tree_nodes(lst, bits) for lst in sdist.copy_lists(c, world)])
+                assert list(nodes.sum(axis=0)) == [max(f, world) if f < world else f for f in full]
+                ranged = np.array([sdist.tree_nodes(np.arange(b, e, dtype=np.uint64), bits)
+                                   for b, e in sdist.copy_ranges(copies, world)])
+                assert ranged[:, 0].sum() == world * full[0]
+    finally:
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(circ)
+
+
 def _free_port():
     s = socket.socket()
     s.bind(("127.0.0.1", 0))

@@ -2,9 +2,9 @@
 circuit seeds, cut rows, fuse widths, sweep kernels, pass formations and the
 output-phase option, each full vector against the oracle's uncut state vector.
 
-Tolerances: split fp16 <= 1e-5 everywhere; split bf16 <= 1e-5 only with 16 or more
-copies (fewer copies average the bf16 split's per-product error 3 * 2^-16 too
-little); FP64 plain <= 1e-12."""
+Tolerances: split fp16 and split bf16 <= 1e-5, FP64 plain <= 1e-12.  Split bf16 is
+refused (SIM_EUNSUPPORTED) below 16 copies, where too few products average its
+per-product error 3 * 2^-16 below 1e-5; that refusal is checked too."""
 import numpy as np
 import pytest
 
@@ -57,14 +57,19 @@ def test_random_circuit_full_vector(R, C, d, seed, b, fuse, kernel, order, phase
     try:
         for prec, kind in ((sim.SIM_C64, sim.SIM_SPLIT_FP16), (sim.SIM_C64, sim.SIM_SPLIT_BF16),
                            (sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN)):
-            if kind == sim.SIM_SPLIT_BF16 and copies < 16:
-                continue
             h = sim.sim_evolve_halves(plan, prec, 0, copies, opts=opts)
             dt = torch.complex128 if kind == sim.SIM_FP64_PLAIN else torch.complex64
             out = torch.zeros((1 << nl, 1 << nu), dtype=dt, device="cuda")
-            sim.sim_amplitudes(h, kind, False, out)
-            sim.sim_status()
-            sim.sim_destroy_halves(h)
+            try:
+                if kind == sim.SIM_SPLIT_BF16 and copies < 16:
+                    with pytest.raises(sim.SimError) as ei:
+                        sim.sim_amplitudes(h, kind, False, out)
+                    assert ei.value.code == sim.SIM_EUNSUPPORTED
+                    continue
+                sim.sim_amplitudes(h, kind, False, out)
+                sim.sim_status()
+            finally:
+                sim.sim_destroy_halves(h)
             tol = 1e-12 if kind == sim.SIM_FP64_PLAIN else 1e-5
             assert rel_err(out.cpu().numpy(), ref) <= tol, (kind, c)
     finally:

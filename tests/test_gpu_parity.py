@@ -142,7 +142,9 @@ def test_selection_and_copy_ranges(R, C, d, seed, nsu, nsl, k0, k1):
     r = Run(R, C, d, seed)
     try:
         h = r.evolve(sim.SIM_C64, k0, k1v, su, sl)
-        got = amplitudes(h, sim.SIM_SPLIT_BF16, nsl, nsu).cpu().numpy()
+        # split-bf16 is offered from 16 copies on; fewer take the fp16 split
+        split = sim.SIM_SPLIT_BF16 if k1v - k0 >= 16 else sim.SIM_SPLIT_FP16
+        got = amplitudes(h, split, nsl, nsu).cpu().numpy()
         assert rel_err(got, ref) <= TOL_SPLIT
         hp = r.evolve(sim.SIM_C128_PLAIN, k0, k1v, su, sl)
         gotp = amplitudes(hp, sim.SIM_FP64_PLAIN, nsl, nsu).cpu().numpy()
@@ -160,7 +162,7 @@ def test_accumulate_over_copy_batches():
         bounds = [0, 5, 6, 40, plan.copies]
         for a, b in zip(bounds[:-1], bounds[1:]):
             h = r.evolve(sim.SIM_C64, a, b)
-            sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, True, out)
+            sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, True, out)
         sim.sim_status()
         assert rel_err(out.cpu().numpy(), ref) <= TOL_SPLIT
     finally:
@@ -471,20 +473,20 @@ def test_controlled_x_cuts(seed):
             got = amplitudes(h, kind, 1 << nl, 1 << nu).cpu().numpy()
             sim.sim_destroy_halves(h)
             assert rel_err(got, ref) <= tol, (prec, kind)
-        # a copy list: the oracle's partial sum over those copies.  A sum of a few
-        # outer products has no averaging, so the split contraction is held to its
-        # per-product bound: each real component keeps a residual of 2^-16 of itself
-        # after hi + lo (bf16) and lo * lo is dropped, so a complex product is off by
-        # at most 3 * 2^-16 |U_k[x_u]| |L_k[x_l]|, plus the complex64 leaves' rounding.
+        # a copy list: the oracle's partial sum over those three copies.  A sum of
+        # three outer products has no averaging to bring the bf16 split's per-product
+        # error (3 * 2^-16) below 1e-5, so split-bf16 is refused and split-fp16 holds
+        # the plain 1e-5.
         gplan = oc.CutPlan(n, n_u, gates)
         lst = np.array([copies - 1, 0, copies // 2 + 1], dtype=np.uint64)
         part = sum(oracle.cut_amplitudes(gplan, None, None, int(k), int(k) + 1) for k in lst)
-        mag = sum(np.abs(oracle.half_state(gplan, 1, int(k)))[:, None] *
-                  np.abs(oracle.half_state(gplan, 0, int(k)))[None, :] for k in lst)
         h = sim.sim_evolve_halves_list(cp, sim.SIM_C64, lst)
-        got = amplitudes(h, sim.SIM_SPLIT_BF16, 1 << nl, 1 << nu).cpu().numpy()
+        with pytest.raises(sim.SimError) as ei:
+            amplitudes(h, sim.SIM_SPLIT_BF16, 1 << nl, 1 << nu)
+        assert ei.value.code == sim.SIM_EUNSUPPORTED
+        got = amplitudes(h, sim.SIM_SPLIT_FP16, 1 << nl, 1 << nu).cpu().numpy()
         sim.sim_destroy_halves(h)
-        assert np.all(np.abs(got - part) <= 3 * 2.0 ** -16 * mag + 1e-6 * mag.max())
+        assert rel_err(got, part) <= TOL_SPLIT
         h = sim.sim_evolve_halves_list(cp, sim.SIM_C128_PLAIN, lst)
         got = amplitudes(h, sim.SIM_FP64_PLAIN, 1 << nl, 1 << nu).cpu().numpy()
         sim.sim_destroy_halves(h)
@@ -506,16 +508,18 @@ class PhaseRun(Run):
 def test_output_phase_cuts_full_vector():
     """4x4 grid, depth 9: the two cut CZs of the last layer become output signs
     (c = 4 -> 2).  The rewrite is exact, so every contraction path gives the uncut
-    state vector: split bf16 / fp16 (CTA-pair kernel, sign in the epilogue) and FP64
-    plain (separate sign pass)."""
+    state vector: split fp16 (CTA-pair kernel, sign in the epilogue) and FP64 plain
+    (separate sign pass).  Four copies are too few for split-bf16, which is refused."""
     gates = oc.generate(4, 4, 9, 0, 2)
     ref = oracle.statevector(16, gates).reshape(256, 256)
     r = PhaseRun(4, 4, 9, 0, 2)
     try:
         assert r.c == 2 and len(sim.sim_cut_output_phases(r.plan)) == 2
         h = r.evolve(sim.SIM_C64)
-        for kind in (sim.SIM_SPLIT_BF16, sim.SIM_SPLIT_FP16):
-            assert rel_err(amplitudes(h, kind, 256, 256).cpu().numpy(), ref) <= TOL_SPLIT
+        with pytest.raises(sim.SimError) as ei:
+            amplitudes(h, sim.SIM_SPLIT_BF16, 256, 256)
+        assert ei.value.code == sim.SIM_EUNSUPPORTED
+        assert rel_err(amplitudes(h, sim.SIM_SPLIT_FP16, 256, 256).cpu().numpy(), ref) <= TOL_SPLIT
         hp = r.evolve(sim.SIM_C128_PLAIN)
         assert rel_err(amplitudes(hp, sim.SIM_FP64_PLAIN, 256, 256).cpu().numpy(), ref) <= TOL_PLAIN
     finally:
@@ -541,7 +545,7 @@ def test_output_phase_cuts_accumulate_and_selections(nsu):
         bounds = [0, 1, r.copies // 2, r.copies]
         for a, bnd in zip(bounds[:-1], bounds[1:]):
             h = r.evolve(sim.SIM_C64, a, bnd, su, sl)
-            sim.sim_amplitudes(h, sim.SIM_SPLIT_BF16, True, out)
+            sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, True, out)
             hp = r.evolve(sim.SIM_C128_PLAIN, a, bnd, su, sl)
             sim.sim_amplitudes(hp, sim.SIM_FP64_PLAIN, True, outp)
         sim.sim_status()
