@@ -33,7 +33,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "oracle.c")
 
-CODES = {"H": 0, "X2": 1, "Y2": 2, "T": 3, "CZ": 4, "P0": 5, "P1": 6, "Z": 7, "CX": 8, "X": 9}
+CODES = {"H": 0, "X2": 1, "Y2": 2, "T": 3, "CZ": 4, "P0": 5, "P1": 6, "Z": 7, "CX": 8, "X": 9, "CT": 10, "CY2": 11}
 
 
 def build(force=False):
@@ -80,8 +80,10 @@ def _encode(gates):
     rows = []
     for g in gates:
         name = g[1]
-        if name in ("CZ", "CX"):
+        if name in ("CZ", "CX", "CT", "CY2"):
             rows.append((CODES[name], g[2], g[3]))
+        elif name == "CUTU":
+            rows.append((-100 - CODES[g[4]], g[3], g[2]))
         elif name == "CUTP":
             rows.append((-1, g[3], g[2]))
         elif name == "CUTZ":

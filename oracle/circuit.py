@@ -133,11 +133,16 @@ def parse_text(text):
     gates = []
     for f in rows[1:]:
         t, name = int(f[0]), f[1]
-        if name in ("CZ", "CX"):
+        if name in TWO_QUBIT:
             gates.append((t, name, int(f[2]), int(f[3])))
         else:
             gates.append((t, name, int(f[2])))
     return R, C, depth, seed, gates
+
+
+# two-qubit gates of the gate lists; the controlled ones map to their U
+TWO_QUBIT = ("CZ", "CX", "CT", "CY2")
+CONTROLLED_U = {"CT": "T", "CY2": "Y2"}
 
 
 class CutPlan:
@@ -146,7 +151,9 @@ class CutPlan:
     half (the set E_int of its layer) is replaced by P_l on the upper endpoint and
     Q_l in {I, Z} on the lower endpoint, l being one bit l_m of the copy index.
     A controlled X across the cut (Supplementary A, Eq. 1 with U = X) is replaced
-    by P_l on its control and X^l on its target, whichever half each is in.
+    by P_l on its control and X^l on its target, whichever half each is in; a
+    controlled T or Y^1/2 (Eq. 1 with U = T or Y^1/2) likewise by P_l on its
+    control and U^l on its target (slot ('CUTU', m, q, U)).
     Bits are numbered by (layer, upper qubit) ascending; copy k = sum_m l_m 2^m.
     """
 
@@ -157,7 +164,7 @@ class CutPlan:
         self.lower = []         # gates on lower qubits (re-indexed); ('CUTZ', m, k-n_u)
         cz_cross = []
         for g in gates:
-            if g[1] in ("CZ", "CX"):
+            if g[1] in TWO_QUBIT:
                 a, c2 = min(g[2], g[3]), max(g[2], g[3])
                 if a < n_u <= c2:
                     cz_cross.append((g[0], a, c2))
@@ -189,6 +196,21 @@ class CutPlan:
                         self.lower.append((t, "CUTX", m, qt - n_u))
                     else:
                         self.upper.append((t, "CUTX", m, qt))
+                        self.lower.append((t, "CUTP", m, qc - n_u))
+            elif g[1] in CONTROLLED_U:
+                qc, qt = g[2], g[3]
+                u = CONTROLLED_U[g[1]]
+                if qc < n_u and qt < n_u:
+                    self.upper.append(g)
+                elif qc >= n_u and qt >= n_u:
+                    self.lower.append((t, g[1], qc - n_u, qt - n_u))
+                else:
+                    m = index[(t, min(qc, qt), max(qc, qt))]
+                    if qc < n_u:
+                        self.upper.append((t, "CUTP", m, qc))
+                        self.lower.append((t, "CUTU", m, qt - n_u, u))
+                    else:
+                        self.upper.append((t, "CUTU", m, qt, u))
                         self.lower.append((t, "CUTP", m, qc - n_u))
             else:
                 q = g[2]
@@ -225,6 +247,10 @@ class CutPlan:
                 bit = (k >> g[2]) & 1
                 if bit:
                     out.append((g[0], "X", g[3]))
+            elif g[1] == "CUTU":
+                bit = (k >> g[2]) & 1
+                if bit:
+                    out.append((g[0], g[4], g[3]))
             else:
                 out.append(g)
         return out

@@ -24,6 +24,8 @@
  *   P0  = diag(1, 0), P1 = diag(0, 1), Z = diag(1, -1)         (Eq. 1 right side)
  *   CX  = controlled X, control q1, target q2; X = [[0, 1], [1, 0]]
  *         (Supplementary A, Eq. 1 with U = X: CX = P0 (x) I + P1 (x) X)
+ *   CT, CY2 = controlled T and controlled Y^1/2, control q1, target q2
+ *         (Supplementary A, Eq. 1: P0 (x) I + P1 (x) U with U = T or Y^1/2)
  *
  * Gate encoding (three int32 per gate): {code, q1, q2}; q2 is used by CZ and CX.
  */
@@ -33,7 +35,8 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { OR_H = 0, OR_X2 = 1, OR_Y2 = 2, OR_T = 3, OR_CZ = 4, OR_P0 = 5, OR_P1 = 6, OR_Z = 7, OR_CX = 8, OR_X = 9 };
+enum { OR_H = 0, OR_X2 = 1, OR_Y2 = 2, OR_T = 3, OR_CZ = 4, OR_P0 = 5, OR_P1 = 6, OR_Z = 7, OR_CX = 8, OR_X = 9,
+       OR_CT = 10, OR_CY2 = 11 };
 
 typedef double complex cplx;
 
@@ -107,6 +110,20 @@ static void apply_cx(cplx* psi, int n, int qc, int qt) {
   }
 }
 
+/* P0 (x) I + P1 (x) U on (qc, qt): the pairs of the target with the control bit
+ * set get U, the others are left alone (Supplementary A, Eq. 1). */
+static void apply_cu(cplx* psi, int n, int qc, int qt, const cplx m[4]) {
+  const int64_t dim = (int64_t)1 << n;
+  const int64_t c = (int64_t)1 << qc, t = (int64_t)1 << qt;
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < dim; ++i) {
+    if (!(i & c) || (i & t)) continue;
+    cplx a0 = psi[i], a1 = psi[i | t];
+    psi[i] = m[0] * a0 + m[1] * a1;
+    psi[i | t] = m[2] * a0 + m[3] * a1;
+  }
+}
+
 void or_evolve(int n, const int32_t* ops, int nops, double* psi_d, int init_zero) {
   cplx* psi = (cplx*)psi_d;
   const int64_t dim = (int64_t)1 << n;
@@ -120,6 +137,10 @@ void or_evolve(int n, const int32_t* ops, int nops, double* psi_d, int init_zero
       apply_cz(psi, n, q1, q2);
     } else if (code == OR_CX) {
       apply_cx(psi, n, q1, q2);
+    } else if (code == OR_CT || code == OR_CY2) {
+      cplx m[4];
+      gate_matrix(code == OR_CT ? OR_T : OR_Y2, m);
+      apply_cu(psi, n, q1, q2, m);
     } else {
       cplx m[4];
       gate_matrix(code, m);
@@ -133,8 +154,9 @@ void or_evolve(int n, const int32_t* ops, int nops, double* psi_d, int init_zero
  *   out[i_l * n_sel_u + i_u] (+)= sum_k U_k[sel_u[i_u]] * L_k[sel_l[i_l]]
  * The half gate lists carry cut slots: code -1 means "P_{l_m} on q1" (the control
  * side, m = q2), code -2 means "Z^{l_m} on q1" and code -3 "X^{l_m} on q1" (the
- * target side of a cut CZ or CX), with l_m = bit m of k (Supplementary A,
- * Eqs. 1, 7-8).  If accumulate is 0 the output is
+ * target side of a cut CZ or CX), code -100 - u "U^{l_m} on q1" with U the gate of
+ * code u (the target side of a cut controlled T or Y^1/2), with l_m = bit m of k
+ * (Supplementary A, Eqs. 1, 7-8).  If accumulate is 0 the output is
  * cleared first.  The sum over k is taken in ascending k for every output.
  */
 static int resolve(const int32_t* tmpl, int ntmpl, uint64_t k, int32_t* out) {
@@ -148,6 +170,8 @@ static int resolve(const int32_t* tmpl, int ntmpl, uint64_t k, int32_t* out) {
       if ((k >> q2) & 1u) { out[3 * n] = OR_Z; out[3 * n + 1] = q1; out[3 * n + 2] = 0; ++n; }
     } else if (code == -3) {
       if ((k >> q2) & 1u) { out[3 * n] = OR_X; out[3 * n + 1] = q1; out[3 * n + 2] = 0; ++n; }
+    } else if (code <= -100) {
+      if ((k >> q2) & 1u) { out[3 * n] = -100 - code; out[3 * n + 1] = q1; out[3 * n + 2] = 0; ++n; }
     } else {
       out[3 * n] = code; out[3 * n + 1] = q1; out[3 * n + 2] = q2; ++n;
     }

@@ -4,9 +4,9 @@ import numpy as np
 from oracle import circuit as oc
 
 
-def cx_cut_circuit(seed):
-    """4x4 grid: H layer, CZ patterns, random single-qubit gates, and controlled X
-    gates across the cut (rows 1 | 2) in both directions."""
+def cx_cut_circuit(seed, name="CX"):
+    """4x4 grid: H layer, CZ patterns, random single-qubit gates, and controlled
+    gates (name: CX, CT or CY2) across the cut (rows 1 | 2) in both directions."""
     R, C, b, depth = 4, 4, 2, 10
     base = oc.generate(R, C, depth, seed, b)
     rng = np.random.default_rng(seed)
@@ -22,7 +22,7 @@ def cx_cut_circuit(seed):
         lo = [q for q in free if q >= b * C]
         if up and lo:
             qa, qb = int(rng.choice(up)), int(rng.choice(lo))
-            extra.append((t, "CX", qa, qb) if t % 2 else (t, "CX", qb, qa))
+            extra.append((t, name, qa, qb) if t % 2 else (t, name, qb, qa))
             busy.setdefault(t, set()).update((qa, qb))
     gates = sorted(gates + extra, key=lambda g: (g[0], g[2]))
     return R, C, b, depth, gates
