@@ -77,8 +77,9 @@ typedef struct sim_multi_s* sim_multi_plan;
  *   seed         splitmix64 seed of the X^1/2 / Y^1/2 draws
  *   cut_row      b, the row the CZ patterns 7 and 8 straddle (0 => rows / 2)
  *   gate_list    optional canonical gate-list text ("circuit R C depth seed" then
- *                one "t NAME q [q2]" line per gate, NAME in H X2 Y2 T CZ CX; CX is
- *                "t CX control target"); when not NULL it replaces the generator.
+ *                one "t NAME q [q2]" line per gate, NAME in H X2 Y2 T CZ CX CT CY2;
+ *                the controlled X, T and Y^1/2 gates are "t CX control target"
+ *                etc.); when not NULL it replaces the generator.
  *   rule_t_in_pool  0: a qubit's first gate after H is T and later ones are X^1/2
  *                or Y^1/2 (top bit of the next splitmix64 output); 1: later ones are
  *                uniform over {X^1/2, Y^1/2, T} ((output >> 32) mod 3), a variant
@@ -137,11 +138,15 @@ int sim_circuit_text(sim_circuit circ, char* buf, size_t cap, size_t* len_out);
 /* Cut the circuit between rows cut_row-1 and cut_row (Section 2.1; Supplementary A,
  * Eqs. 6-8): find E_int, number the cut CZs, split the gates into two half-circuits,
  * build the copy tree (one level per layer holding cuts) and the fused pass
- * schedule.  A controlled X (explicit gate lists, "t CX control target") across the
- * cut is cut the same way with U = X (Supplementary A, Eq. 1): P_l on the control,
- * X^l on the target.  Outputs (any may be NULL): c, 2^c, qubits per half.  Host only.
- * SIM_EUNSUPPORTED if a controlled X lies inside one half, a half exceeds 32 qubits
- * or c exceeds 40. */
+ * schedule.  A controlled gate across the cut (explicit gate lists: controlled X,
+ * controlled T, controlled Y^1/2) is cut the same way, Supplementary A, Eq. 1 with
+ * U = X, T or Y^1/2: P_l on the control and U^l on the target, whichever half each
+ * is in.  The fused complex64 sweeps write U^l with copy-independent gates around
+ * one diagonal slot w^{b l x} on the target (w = e^{i pi/4}): X^l = H Z^l H (b = 4),
+ * T^l (b = 1), (Y^1/2)^l = X^1/2 X^1/2 X^1/2 S^l X^1/2 (b = 2, in time order); the
+ * plain complex128 path applies U in the copies with l = 1.  Outputs (any may be
+ * NULL): c, 2^c, qubits per half.  Host only.  SIM_EUNSUPPORTED if a controlled
+ * gate lies inside one half, a half exceeds 32 qubits or c exceeds 40. */
 int sim_cut(sim_circuit circ, int cut_row, sim_cut_plan* out, int* c_out,
             uint64_t* copies_out, int* n_upper_out, int* n_lower_out);
 
@@ -179,7 +184,7 @@ int sim_cut_output_phases(sim_cut_plan plan, int32_t* pairs_out, int cap, int* n
  * l each; the amplitude is the sum over all boundary bits of the products of the
  * t part states.  Outputs (any may be NULL): t, the cut CZs per boundary
  * (c_out[j-1] for boundary j, n_cut_rows values) and the qubits per part (nq_out,
- * t values).  Host only.  SIM_EUNSUPPORTED if the circuit holds a controlled X, a
+ * t values).  Host only.  SIM_EUNSUPPORTED if the circuit holds a controlled gate, a
  * part exceeds 32 qubits or its copy bits exceed 40. */
 int sim_cut_multi(sim_circuit circ, int n_cut_rows, const int* cut_rows, sim_multi_plan* out, int* parts_out,
                   int* c_out, int* nq_out);

@@ -53,7 +53,7 @@ def up_to_date():
     if not os.path.exists(OUT):
         return False
     t = os.path.getmtime(OUT)
-    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
     deps = sources() + headers + [os.path.join(ROOT, "include", "sim.h"), __file__]
     return all(os.path.getmtime(d) <= t for d in deps)
 

@@ -11,6 +11,7 @@
 
 #include "../../include/sim.h"
 #include "sim_internal.h"
+#include "stream_c64.cuh"
 
 namespace sim {
 namespace {
@@ -103,27 +104,31 @@ __global__ void __launch_bounds__(256) stats_kernel(const void* amps, uint64_t c
   double sp = 0.0, sl = 0.0, nz = 0.0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   if (!C128) {
-    const float2* a = (const float2*)amps;
+    // fp32 per element, the two running sums compensated (Kahan: the rounding of
+    // each add is carried in c and fed back), the count an integer; FP64 only once
+    // per thread at the end (GB300's FP64 pipe retires two operations per clock
+    // per SM, so no FP64 instruction may sit on the per-element path)
     const float sc = ldexpf(1.f, nq);
-    float fp = 0.f, fl = 0.f, fn = 0.f;
-    int cnt = 0;
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count; i += stride) {
-      const float2 v = a[i];
+    float fp = 0.f, cp = 0.f, fl = 0.f, cl = 0.f;
+    uint32_t cnt = 0;
+    auto kahan = [](float& sum, float& c, float x) {
+      const float y = x - c;
+      const float t = sum + y;
+      c = (t - sum) - y;
+      sum = t;
+    };
+    for_each_c64((const float2*)amps, count, [&](float2 v) {
       const float p = fmaf(v.x, v.x, v.y * v.y);
       const float w = p * sc;
-      fp += p;
-      if (w > 0.f) {
-        fl += __logf(w);
-        fn += 1.f;
-      }
+      kahan(fp, cp, p);
+      const bool pos = w > 0.f;
+      kahan(fl, cl, pos ? __logf(w) : 0.f);
+      cnt += pos ? 1u : 0u;
       atomicAdd(&sh[u_bin(w)], 1u);
-      if (++cnt == 32) {
-        sp += fp; sl += fl; nz += fn;
-        fp = fl = fn = 0.f;
-        cnt = 0;
-      }
-    }
-    sp += fp; sl += fl; nz += fn;
+    });
+    sp = (double)fp - (double)cp;
+    sl = (double)fl - (double)cl;
+    nz = (double)cnt;
   } else {
     const double2* a = (const double2*)amps;
     const double sc = ldexp(1.0, nq);
@@ -179,8 +184,11 @@ cudaError_t launch_stats(const void* amps, int is_c128, uint64_t count, int nq, 
   e = cudaMemsetAsync(hist_dev, 0, SIM_KS_BINS * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   if (count == 0) return cudaSuccess;
+  // four resident blocks per SM (16 KB histogram each), as many as the block needs
+  int dev = 0, sms = 148;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   uint64_t blocks = (count + 255) / 256;
-  if (blocks > 2048) blocks = 2048;
+  if (blocks > (uint64_t)sms * 4) blocks = (uint64_t)sms * 4;
   if (is_c128)
     stats_kernel<true><<<(unsigned)blocks, 256, 0, s>>>(amps, count, nq, acc_dev, hist_dev);
   else

@@ -4,10 +4,13 @@
 //
 // Each CTA of the pair holds 128 rows of the A tile and 128 of the 256 rows of the
 // B tile (one half of the output columns) in its own shared memory, and 128 rows x
-// 256 columns of the fp32 accumulator in its own tensor memory.  Per 64-wide k-block
-// each SM therefore moves 32 KB through shared memory twice (TMA write, MMA read)
-// instead of 48 KB for the single-CTA M=128 x N=256 MMA, which is what lets the
-// tensor pipe run closer to its peak.
+// 256 columns of the fp32 accumulator in its own tensor memory.  A stage holds one
+// 64-wide k-block of both split parts of both operands (A hi, A lo, B hi, B lo) and
+// the MMA issuer takes the three split products hi*hi, hi*lo, lo*hi from them, so
+// each operand tile crosses shared memory once per k-block: 64 KB written and 96 KB
+// read per SM for three k-block products, against 96 + 96 KB when every product
+// loads its own pair of tiles.  Shared-memory bandwidth, not the tensor pipe, is
+// what bounds this kernel.
 //
 // Roles (both CTAs run the same warps):
 //   warp 0     TMA loads of the CTA's own A and B halves into its own stage ring.
@@ -47,6 +50,7 @@ constexpr int BK = 64;
 constexpr int UMMA_K = 16;
 constexpr int A_BYTES = BM * BK * 2;   // 16 KB
 constexpr int B_BYTES = BNH * BK * 2;  // 16 KB
+constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);  // hi and lo tiles of both operands
 constexpr int ACC_COLS = BN;
 constexpr int TMEM_COLS = 2 * ACC_COLS;
 constexpr int HIST_BYTES = SIM_KS_BINS * 4;
@@ -55,7 +59,7 @@ constexpr int HIST_BYTES = SIM_KS_BINS * 4;
 template <int STG, int SW, int NBUF, int EW>
 struct PairSmem {
   static constexpr int EPI_BYTES = EW * NBUF * 32 * SW * 4;
-  static constexpr int BYTES = 1024 + STG * (A_BYTES + B_BYTES) + EPI_BYTES + 512 + HIST_BYTES;
+  static constexpr int BYTES = 1024 + STG * STAGE_BYTES + EPI_BYTES + 512 + HIST_BYTES;
   static_assert(BYTES <= 232448, "shared memory above the 227 KB per-block limit");
 };
 constexpr unsigned long long kWaitNs = 2000000000ull;
@@ -275,16 +279,11 @@ struct PairArgs {
   unsigned long long* st_hist;
   const uint32_t* out_lcode;  // output-phase codes of the rows and complex columns (NULL: none)
   const uint32_t* out_ucode;
+  // k-blocks of chunk c (each one stage: the three split products of one k-block)
   __device__ int chunk_kblocks(int c) const {
     const int b0 = c * ckb;
     const int b1 = b0 + ckb < nkb ? b0 + ckb : nkb;
-    return 3 * (b1 - b0);
-  }
-  __device__ void kblock(int c, int i, int& seg, int& kx) const {
-    const int b0 = c * ckb;
-    const int per = (b0 + ckb < nkb ? b0 + ckb : nkb) - b0;
-    seg = i / per;
-    kx = (b0 + i % per) * BK;
+    return b1 - b0;
   }
 };
 
@@ -301,9 +300,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
   constexpr int COLS = BN / (EW / 4);  // accumulator columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  // stage s: A hi, A lo at sA + s * 2 A_BYTES; B hi, B lo at sB + s * 2 B_BYTES
   uint8_t* sA = smem;
-  uint8_t* sB = smem + STG * A_BYTES;
-  float* sEpi = (float*)(sB + STG * B_BYTES);
+  uint8_t* sB = smem + STG * 2 * A_BYTES;
+  float* sEpi = (float*)(sB + STG * 2 * B_BYTES);
   uint64_t* bars = (uint64_t*)((uint8_t*)sEpi + L::EPI_BYTES);
   uint64_t* full = bars;                  // leader: both halves landed  (count 1 + tx)
   uint64_t* empty = bars + STG;           // leader's MMAs done          (count 1, multicast commit)
@@ -372,14 +372,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
               ok = false;
               break;
             }
-            int seg, kx;
-            args.kblock(c, i, seg, kx);
-            const CUtensorMap* ma = seg == 2 ? &mapA_lo : &mapA_hi;
-            const CUtensorMap* mbp = seg == 1 ? &mapB_lo : &mapB_hi;
+            const int kx = (c * args.ckb + i) * BK;
             const uint32_t fb = full0 + (uint32_t)(stage * sizeof(uint64_t));
-            if (leader) mbar_arrive_expect_tx(smem_u32(&full[stage]), 2 * (A_BYTES + B_BYTES));
-            tma_load_2d_pair(smem_u32(sA + stage * A_BYTES), ma, fb, kx, arow);
-            tma_load_2d_pair(smem_u32(sB + stage * B_BYTES), mbp, fb, kx, brow);
+            // both CTAs' four tiles complete on the leader's barrier
+            if (leader) mbar_arrive_expect_tx(smem_u32(&full[stage]), 2 * STAGE_BYTES);
+            uint8_t* a_st = sA + stage * 2 * A_BYTES;
+            uint8_t* b_st = sB + stage * 2 * B_BYTES;
+            tma_load_2d_pair(smem_u32(a_st), &mapA_hi, fb, kx, arow);
+            tma_load_2d_pair(smem_u32(a_st + A_BYTES), &mapA_lo, fb, kx, arow);
+            tma_load_2d_pair(smem_u32(b_st), &mapB_hi, fb, kx, brow);
+            tma_load_2d_pair(smem_u32(b_st + B_BYTES), &mapB_lo, fb, kx, brow);
             issued_parity[stage] = (int)phase;
             if (++stage == STG) {
               stage = 0;
@@ -421,12 +423,16 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
               break;
             }
             tc_fence_after();
-            const uint32_t a0 = smem_u32(sA + stage * A_BYTES);
-            const uint32_t b0 = smem_u32(sB + stage * B_BYTES);
+            const uint32_t ah = smem_u32(sA + stage * 2 * A_BYTES), al = ah + A_BYTES;
+            const uint32_t bh = smem_u32(sB + stage * 2 * B_BYTES), bl = bh + B_BYTES;
+            // the three split products of this k-block into the same accumulator
 #pragma unroll
-            for (int kk = 0; kk < BK / UMMA_K; ++kk)
-              umma_pair(d_tmem, smem_desc(a0 + kk * UMMA_K * 2), smem_desc(b0 + kk * UMMA_K * 2), idesc,
-                        (kb > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < BK / UMMA_K; ++kk) {
+              const uint32_t o = kk * UMMA_K * 2;
+              umma_pair(d_tmem, smem_desc(ah + o), smem_desc(bh + o), idesc, (kb > 0 || kk > 0) ? 1u : 0u);
+              umma_pair(d_tmem, smem_desc(ah + o), smem_desc(bl + o), idesc, 1u);
+              umma_pair(d_tmem, smem_desc(al + o), smem_desc(bh + o), idesc, 1u);
+            }
             umma_commit_both(smem_u32(&empty[stage]));
             if (++stage == STG) {
               stage = 0;
@@ -773,15 +779,14 @@ cudaError_t launch_tc_gemm_pair(const TcGemmArgs& a, cudaStream_t s) {
   const bool sign = k.out_lcode != nullptr;
   // Epilogue shape by the length of a tile's main loop: with few k-blocks per tile
   // (K <= 128 copies) the epilogue is the bound and 16 epilogue warps hide its
-  // latency (5 operand stages, 214,528 bytes of shared memory); otherwise 6 stages
-  // and 8 epilogue warps (230,912 bytes).  Measured on the 2^30-amplitude workload:
-  // K = 32: 3.16 ms against 4.97 ms with 8 warps; K = 256: 4.32 against 4.31 ms.
+  // latency (2 operand stages of 64 KB, 181,760 bytes of shared memory); otherwise 3
+  // stages and 8 epilogue warps (230,912 bytes).
 #define LV(G, E)                                                                                          \
   (stats ? (sign ? launch_variant<true, true, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s)                 \
                  : launch_variant<true, false, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s))               \
          : (sign ? launch_variant<false, true, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s)                \
                  : launch_variant<false, false, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s)))
-  cudaError_t e = k.nkb <= 4 ? LV(5, 16) : LV(6, 8);
+  cudaError_t e = k.nkb <= 4 ? LV(2, 16) : LV(3, 8);
 #undef LV
   note_launches(SIM_PHASE_CONTRACT, 1);
   return e;

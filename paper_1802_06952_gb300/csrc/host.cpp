@@ -25,7 +25,8 @@ uint64_t splitmix64_next(uint64_t& state) {
   return z ^ (z >> 31);
 }
 
-static const char* kGateName[] = {"H", "X2", "Y2", "T", "CZ", "CX", "X"};
+static const char* kGateName[] = {"H", "X2", "Y2", "T", "CZ", "CX", "X", "CT", "CY2"};
+constexpr int kNumGateNames = 9;
 
 // CZ couplers of pattern p (1..8) on an R x C grid whose cut lies above row b.
 // Patterns 1-4: horizontal (r,c)-(r,c+1) with (r%2, c%2) = (0,0), (1,1), (0,1), (1,0).
@@ -109,7 +110,7 @@ std::string circuit_text(const Circuit& c) {
   snprintf(buf, sizeof buf, "circuit %d %d %d %llu\n", c.R, c.C, c.depth, (unsigned long long)c.seed);
   s += buf;
   for (const Gate& g : c.gates) {
-    if (g.code == G_CZ || g.code == G_CX)
+    if (is_two_qubit(g.code))
       snprintf(buf, sizeof buf, "%d %s %d %d\n", g.t, kGateName[g.code], g.q1, g.q2);
     else
       snprintf(buf, sizeof buf, "%d %s %d\n", g.t, kGateName[g.code], g.q1);
@@ -145,10 +146,10 @@ std::string parse_circuit(const char* text, Circuit& out) {
     std::string nm;
     if (!(ls >> t >> nm >> q1)) return "malformed gate line: " + line;
     int code = -1;
-    for (int i = 0; i < 6; ++i)
-      if (nm == kGateName[i]) code = i;
+    for (int i = 0; i < kNumGateNames; ++i)
+      if (i != G_X && nm == kGateName[i]) code = i;
     if (code < 0) return "unknown gate name: " + nm;
-    const bool two = code == G_CZ || code == G_CX;
+    const bool two = is_two_qubit(code);
     if (two && !(ls >> q2)) return nm + " needs two qubits: " + line;
     if (t < 0 || t >= out.depth) return "gate layer out of range: " + line;
     if (t < last_t) return "gates must be ordered by layer";
@@ -159,7 +160,7 @@ std::string parse_circuit(const char* text, Circuit& out) {
     used_at[q1] = (int)t;
     if (two) used_at[q2] = (int)t;
     Gate g{(int)t, code, (int)q1, (int)(two ? q2 : -1)};
-    if (code == G_CZ && g.q2 < g.q1) std::swap(g.q1, g.q2);  // a CX keeps (control, target)
+    if (code == G_CZ && g.q2 < g.q1) std::swap(g.q1, g.q2);  // a controlled gate keeps (control, target)
     out.gates.push_back(g);
   }
   if (!have_head) return "empty gate list";
@@ -193,22 +194,28 @@ void select_indices(int nq, uint64_t count, uint64_t& state, std::vector<uint64_
 // ---------------------------------------------------------------------------
 namespace {
 
-// A diagonal cut slot on half-local qubit q for copy bit m: P_l (z = false: the
-// upper end of a cut CZ, or the control of a cut controlled X in either half) or
-// Z^l (z = true: the lower end of a cut CZ).
+// A diagonal cut slot on half-local qubit q for copy bit m: P_l (w = 0: the upper
+// end of a cut CZ, or the control of a cut controlled gate in either half) or the
+// phase w^{w l x_q} (w = 4: Z^l on the lower end of a cut CZ; 1: T^l on the target
+// of a cut controlled T).
 struct CutSlot {
   int q, m;
-  bool z;
+  int w;
+};
+
+// The U^l slot on the target q of a cut controlled gate (code G_CX, G_CT, G_CY2)
+struct UCut {
+  int q, m, code;
 };
 
 struct HalfGateLists {
   // per layer: non-diagonal gates (qubit, code), T qubits, CZ pairs, diagonal cut
-  // slots, and X^l slots (q, m) on the target of a cut controlled X
+  // slots, and U^l slots on the targets of cut controlled gates
   std::vector<std::vector<std::pair<int, int>>> nondiag;
   std::vector<uint32_t> tmask;
   std::vector<std::vector<std::pair<int, int>>> cz;
   std::vector<std::vector<CutSlot>> cuts;
-  std::vector<std::vector<std::pair<int, int>>> xcuts;
+  std::vector<std::vector<UCut>> ucuts;
 };
 
 void gate_matrix(int code, double m[8]) {
@@ -232,6 +239,11 @@ void gate_matrix(int code, double m[8]) {
     }
     case G_X: {  // [[0, 1], [1, 0]]
       double v[8] = {0, 0, 1, 0, 1, 0, 0, 0};
+      memcpy(m, v, sizeof v);
+      break;
+    }
+    case G_T: {  // diag(1, (1+i)/sqrt2): the T^l slot of the plain path
+      double v[8] = {1, 0, 0, 0, 0, 0, s, s};
       memcpy(m, v, sizeof v);
       break;
     }
@@ -284,7 +296,10 @@ void make_diags(uint32_t tmask, const std::vector<std::pair<int, int>>& cz, cons
     while (si < cuts.size() && o.ncut < kMaxCutSlots) {
       o.cutq[o.ncut] = (uint8_t)cuts[si].q;
       o.cutm[o.ncut] = (uint8_t)cuts[si].m;
-      if (cuts[si].z) o.cutz |= 1u << o.ncut;
+      if (cuts[si].w) {
+        o.cutz |= 1u << o.ncut;
+        o.cutw[o.ncut] = (uint8_t)(cuts[si].w & 7);
+      }
       ++o.ncut;
       ++si;
     }
@@ -634,7 +649,14 @@ void split_passes(int n, int kmax, const std::vector<SeqItem>& items, int first_
           ++p.general_gates;
       } else {
         if (R > 0) fill_diag_tables(o);
-        p.phase_op = (int)(ops.size() - (size_t)p.op_begin);
+        // exponents all 0 or 4 (CZ terms, Z^l and P_l slots only): a sign flip
+        bool sign_only = o.tmask == 0;
+        for (int i = 0; i < o.ncut; ++i)
+          if (((o.cutz >> i) & 1u) && o.cutw[i] != 4) sign_only = false;
+        o.sign_only = sign_only ? 1 : 0;
+        // the pass's phase w^(n_xy) goes into the last op that takes general
+        // phases anyway, so that the sign-only ops stay sign-only
+        if (!sign_only) p.phase_op = (int)(ops.size() - (size_t)p.op_begin);
       }
       ops.push_back(o);
     }
@@ -645,6 +667,11 @@ void split_passes(int n, int kmax, const std::vector<SeqItem>& items, int first_
     p.scale = (float)std::ldexp(n_xy + n_h == 0 ? 1.0 : ((n_xy + n_h) & 1 ? 0.70710678118654752440 : 1.0),
                                 -((n_xy + n_h) / 2));
     p.phase_e = n_xy & 7;
+    // without such an op the store applies the phase; w^4 = -1 is the scale's sign
+    if (p.phase_op < 0 && p.phase_e == 4) {
+      p.scale = -p.scale;
+      p.phase_e = 0;
+    }
     passes.push_back(p);
     first = false;
   }
@@ -662,7 +689,7 @@ void build_half(const Circuit& c, const HalfGateLists& H, int n, const std::vect
   // holding any diagonal gate (T, CZ, or cut slot)
   int plain = 0;
   for (int t = 0; t < c.depth; ++t) {
-    plain += (int)H.nondiag[t].size() + (int)H.xcuts[t].size();
+    plain += (int)H.nondiag[t].size() + (int)H.ucuts[t].size();
     if (H.tmask[t] || !H.cz[t].empty() || !H.cuts[t].empty()) ++plain;
   }
   S.plain_passes = plain;
@@ -687,18 +714,27 @@ void build_half(const Circuit& c, const HalfGateLists& H, int n, const std::vect
     for (int t = t_begin; t <= t_end; ++t) {
       const bool own_cut_layer = (j > 0 && t == t_begin);
       if (own_cut_layer) {
-        // this level applies only the cut slots of its branch layer here.  An X^l
-        // slot becomes H Z^l H (H Z H = X, H H = I): the fused passes need no
-        // copy-dependent gate, only the diagonal slot Z^l between two H gates,
-        // whose common factor 1/2 is the same in every copy.  The X^l slots act on
-        // qubits no other gate of the layer touches.
+        // this level applies only the cut slots of its branch layer here.  A U^l
+        // slot is written as copy-independent gates around one diagonal phase slot
+        // w^{b l x_q}, so the fused passes need no copy-dependent gate:
+        //   X^l        = H Z^l H                       (H Z H = X, H H = I; b = 4)
+        //   T^l        = diag(1, w^l)                  (b = 1)
+        //   (Y^1/2)^l  = X^1/2 X^1/2 X^1/2 S^l X^1/2   (X^-1/2 S X^1/2 = Y^1/2 and
+        //                (X^1/2)^4 = I; b = 2), gates listed in time order below
+        // Their common factors are the same in every copy.  The slots act on qubits
+        // no other gate of the layer touches.
         std::vector<CutSlot> slots = H.cuts[t];
-        for (auto& p : H.xcuts[t]) {
-          seq.push_back(gate_item(make_gate(G_H, p.first)));
-          slots.push_back({p.first, p.second, true});
+        for (const UCut& u : H.ucuts[t]) {
+          if (u.code == G_CX) seq.push_back(gate_item(make_gate(G_H, u.q)));
+          if (u.code == G_CY2) seq.push_back(gate_item(make_gate(G_X2, u.q)));
+          slots.push_back({u.q, u.m, u.code == G_CX ? 4 : u.code == G_CT ? 1 : 2});
         }
         seq.push_back(diag_item(0, {}, slots));
-        for (auto& p : H.xcuts[t]) seq.push_back(gate_item(make_gate(G_H, p.first)));
+        for (const UCut& u : H.ucuts[t]) {
+          if (u.code == G_CX) seq.push_back(gate_item(make_gate(G_H, u.q)));
+          if (u.code == G_CY2)
+            for (int r = 0; r < 3; ++r) seq.push_back(gate_item(make_gate(G_X2, u.q)));
+        }
         continue;
       }
       if (!(j == 0 && t == 0 && uniform))
@@ -717,7 +753,10 @@ void build_half(const Circuit& c, const HalfGateLists& H, int n, const std::vect
   plain_layers.assign(c.depth, PlainLayer());
   for (int t = 0; t < c.depth; ++t) {
     for (auto& p : H.nondiag[t]) plain_layers[t].gates.push_back(make_gate(p.second, p.first));
-    for (auto& p : H.xcuts[t]) plain_layers[t].gates.push_back(make_gate(G_X, p.first, p.second));
+    // the plain path applies U on the target in the copies with l_m = 1
+    for (const UCut& u : H.ucuts[t])
+      plain_layers[t].gates.push_back(
+          make_gate(u.code == G_CX ? G_X : u.code == G_CT ? G_T : G_Y2, u.q, u.m));
     make_diags(H.tmask[t], H.cz[t], H.cuts[t], plain_layers[t].diags);
   }
 }
@@ -762,10 +801,12 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
       }
       plan.cuts.push_back({g.t, g.q1, g.q2, 0});
     }
-    if (g.code == G_CX) {
+    if (is_controlled_u(g.code)) {
       const int a = std::min(g.q1, g.q2), b2 = std::max(g.q1, g.q2);
-      if (!(a < nu && b2 >= nu)) return "a controlled X inside one half is not supported (only across the cut)";
-      plan.cuts.push_back({g.t, a, b2, g.q1 < nu ? 1 : 2});
+      if (!(a < nu && b2 >= nu))
+        return std::string("a controlled gate (") + kGateName[g.code] +
+               ") inside one half is not supported (only across the cut)";
+      plan.cuts.push_back({g.t, a, b2, g.q1 < nu ? 1 : 2, g.code});
     }
   }
   std::sort(plan.cuts.begin(), plan.cuts.end(), [](const CutCZ& a, const CutCZ& b2) {
@@ -782,7 +823,7 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
     hl[h].tmask.assign(c.depth, 0);
     hl[h].cz.assign(c.depth, {});
     hl[h].cuts.assign(c.depth, {});
-    hl[h].xcuts.assign(c.depth, {});
+    hl[h].ucuts.assign(c.depth, {});
   }
   for (const Gate& g : c.gates) {
     if (g.code == G_CZ) {
@@ -792,15 +833,15 @@ std::string build_cut_plan(const Circuit& c, int cut_row, int fuse_qubits, CutPl
         hl[1].cz[g.t].emplace_back(g.q1 - nu, g.q2 - nu);
       } else if (!out_keys.count({g.t, g.q1})) {
         int m = cut_index[{g.t, g.q1}];
-        hl[0].cuts[g.t].push_back({g.q1, m, false});
-        hl[1].cuts[g.t].push_back({g.q2 - nu, m, true});
+        hl[0].cuts[g.t].push_back({g.q1, m, 0});
+        hl[1].cuts[g.t].push_back({g.q2 - nu, m, 4});
       }
-    } else if (g.code == G_CX) {
+    } else if (is_controlled_u(g.code)) {
       const int a = std::min(g.q1, g.q2);
       const int m = cut_index[{g.t, a}];
       const int hc = g.q1 < nu ? 0 : 1;  // half of the control
-      hl[hc].cuts[g.t].push_back({hc ? g.q1 - nu : g.q1, m, false});
-      hl[1 - hc].xcuts[g.t].emplace_back(hc ? g.q2 : g.q2 - nu, m);
+      hl[hc].cuts[g.t].push_back({hc ? g.q1 - nu : g.q1, m, 0});
+      hl[1 - hc].ucuts[g.t].push_back({hc ? g.q2 : g.q2 - nu, m, g.code});
     } else {
       int h = g.q1 < nu ? 0 : 1;
       int q = h ? g.q1 - nu : g.q1;
@@ -851,7 +892,7 @@ std::string build_multi_plan(const Circuit& c, const std::vector<int>& cut_rows,
   // cut CZs per boundary, numbered by (layer, upper qubit)
   std::vector<std::vector<CutCZ>> cuts(mp.t);
   for (const Gate& g : c.gates) {
-    if (g.code == G_CX || g.code == G_X) return "multi-part cuts take H, X^1/2, Y^1/2, T and CZ gates only";
+    if (is_controlled_u(g.code) || g.code == G_X) return "multi-part cuts take H, X^1/2, Y^1/2, T and CZ gates only";
     if (g.code != G_CZ) continue;
     const int pa = part_of[g.q1], pb = part_of[g.q2];  // q1 < q2
     if (pb - pa > 1) return "a CZ crosses more than one boundary";
@@ -888,7 +929,7 @@ std::string build_multi_plan(const Circuit& c, const std::vector<int>& cut_rows,
     H.tmask.assign(c.depth, 0);
     H.cz.assign(c.depth, {});
     H.cuts.assign(c.depth, {});
-    H.xcuts.assign(c.depth, {});
+    H.ucuts.assign(c.depth, {});
   }
   for (const Gate& g : c.gates) {
     const int p = part_of[g.q1];
@@ -899,8 +940,8 @@ std::string build_multi_plan(const Circuit& c, const std::vector<int>& cut_rows,
         hl[p].cz[g.t].emplace_back(g.q1 - o, g.q2 - o);
       } else {
         const auto jb = where[{g.t, g.q1}];
-        hl[p].cuts[g.t].push_back({g.q1 - o, local[p][jb], false});                    // P_l above the boundary
-        hl[pb].cuts[g.t].push_back({g.q2 - mp.offset[pb], local[pb][jb], true});      // Z^l below it
+        hl[p].cuts[g.t].push_back({g.q1 - o, local[p][jb], 0});                    // P_l above the boundary
+        hl[pb].cuts[g.t].push_back({g.q2 - mp.offset[pb], local[pb][jb], 4});      // Z^l below it
       }
     } else if (g.code == G_T) {
       hl[p].tmask[g.t] |= 1u << (g.q1 - o);

@@ -24,6 +24,7 @@
 #include "../../include/sim.h"
 #include "runtime.h"
 #include "sim_internal.h"
+#include "stream_c64.cuh"
 
 using namespace sim;
 
@@ -59,18 +60,24 @@ __device__ __forceinline__ bool decide(const float2* amps, uint64_t count, uint6
 // stays below (1 - 2^-20) times the largest FP32 value this thread has seen cannot
 // exceed the FP64 maximum it holds.  Only the others are computed in FP64, so the
 // pass runs at the speed of its loads instead of GB300's FP64 rate.
+// The rare FP64 update sits in a call of its own so that it is a branch taken by
+// the few candidates, not a predicated sequence on every element (GB300's FP64
+// pipe is slow); its arithmetic is prob()'s, on the loaded floats.
+__device__ __noinline__ double max_prob(double m, float x, float y) {
+  return fmax(m, (double)x * (double)x + (double)y * (double)y);
+}
+
+// The values are streamed 32 bytes at a time (stream_c64.cuh).
 __global__ void pmax_kernel(const float2* amps, uint64_t count, double* block_max) {
   double m = 0.0;
   float thr = 0.f;
-  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < count;
-       i += (uint64_t)gridDim.x * blockDim.x) {
-    const float2 a = amps[i];
+  for_each_c64(amps, count, [&](float2 a) {
     const float p32 = fmaf(a.x, a.x, a.y * a.y);
     if (p32 >= thr) {
-      m = fmax(m, prob(amps, i));
+      m = max_prob(m, a.x, a.y);
       thr = fmaxf(thr, p32 * (1.f - 9.5367431640625e-07f));
     }
-  }
+  });
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   __shared__ double sm[32];
   if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;

@@ -44,10 +44,13 @@ struct DeviceOnce {
 // ---------------------------------------------------------------------------
 // Circuit IR (Supplementary A, Eq. 3: layers of single-qubit gates and CZ edges)
 // ---------------------------------------------------------------------------
-// G_CX: controlled X, q1 control, q2 target (only across the cut, where it becomes
-// P_l on the control and X^l on the target: Supplementary A, Eq. 1 with U = X);
-// G_X: the X of such a slot (not a gate of the circuit text)
-enum GateCode : int { G_H = 0, G_X2 = 1, G_Y2 = 2, G_T = 3, G_CZ = 4, G_CX = 5, G_X = 6 };
+// G_CX, G_CT, G_CY2: controlled X, T and Y^1/2, q1 control, q2 target (only across
+// the cut, where each becomes P_l on the control and U^l on the target:
+// Supplementary A, Eq. 1 with U = X, T, Y^1/2); G_X: the X of a controlled-X slot
+// (not a gate of the circuit text)
+enum GateCode : int { G_H = 0, G_X2 = 1, G_Y2 = 2, G_T = 3, G_CZ = 4, G_CX = 5, G_X = 6, G_CT = 7, G_CY2 = 8 };
+inline bool is_two_qubit(int code) { return code == G_CZ || code == G_CX || code == G_CT || code == G_CY2; }
+inline bool is_controlled_u(int code) { return code == G_CX || code == G_CT || code == G_CY2; }
 
 struct Gate {
   int t, code, q1, q2;
@@ -74,10 +77,12 @@ constexpr int kMaxCutSlots = 16;
 // path) or on qubit `q` (plain path).  A DIAG is the combined diagonal of one
 // layer (Section 2.4, Eqs. 4 and 6) plus the copy-dependent cut slots:
 //   phase(x) = w^{popc(x & tmask)} * (-1)^{sum_s popc(x & (x >> sh_d[s]) & sh_m[s])}
-//   slot i with bit i of cutz clear:  * [bit cutq[i] of x == bit cutm[i] of the copy id]   (P_l)
-//   slot i with bit i of cutz set:    * (-1)^{bit cutq[i] of x * bit cutm[i] of the copy id} (Z^l)
+//   slot i with bit i of cutz clear:  * [bit cutq[i] of x == bit cutm[i] of the copy id]    (P_l)
+//   slot i with bit i of cutz set:    * w^{cutw[i] * bit cutq[i] of x * bit cutm[i] of the copy id}
 // with w = e^{i pi / 4}.  P_l sits on the upper end of a cut CZ and on the control
-// of a cut controlled X (in either half), Z^l on the lower end of a cut CZ.
+// of a cut controlled gate (in either half); the phase slots on the lower end of a
+// cut CZ (cutw = 4: Z^l) and on the target of a cut controlled T (1: T^l), and
+// between the copy-independent gates that write X^l (4) and (Y^1/2)^l (2).
 struct OpRec {
   int32_t type;
   int32_t lq;
@@ -93,6 +98,7 @@ struct OpRec {
   uint32_t sh_m[kMaxShift];
   uint8_t cutq[kMaxCutSlots];
   uint8_t cutm[kMaxCutSlots];
+  uint8_t cutw[kMaxCutSlots];  // phase slots: exponent weight of w (1..7)
   float m[8];
   double md[8];
   // DIAG in the register-blocked sweep (set per pass by the scheduler): with x the
@@ -111,6 +117,10 @@ struct OpRec {
   uint32_t regmask;
   uint8_t rq[8];
   uint8_t tq[8];
+  // DIAG: 1 when every exponent of the op is 0 or 4 (no T, no phase slot of weight
+  // other than 4): the register-blocked sweep then flips signs instead of
+  // multiplying by w^e
+  int32_t sign_only;
 };
 
 // At most this many ops per fused pass (the register-blocked sweep copies a pass's
@@ -180,7 +190,8 @@ struct PlainLayer {
 
 struct CutCZ {
   int t, h, k;  // layer, upper qubit, lower qubit (global indices)
-  int kind = 0;  // 0 CZ; 1 CX with the control in the upper half; 2 control in the lower half
+  int kind = 0;  // 0 CZ; 1 controlled gate with the control in the upper half; 2 control in the lower half
+  int code = G_CZ;  // gate code (G_CZ, G_CX, G_CT, G_CY2)
 };
 
 struct CutPlan {

@@ -35,13 +35,15 @@ __constant__ double2 kOmegaD[8] = {
     {0.70710678118654752440, -0.70710678118654752440}};
 
 struct DiagState {
-  uint32_t tmask, pmask, pval, zmask;
+  uint32_t tmask, pmask, pval, zmask, w1mask, w2mask;
   int nsh;
   uint32_t sh_d[kMaxShift], sh_m[kMaxShift];
 };
 
 // Resolve a DIAG op for one copy-tree node: the cut slots become a projector
-// (P_l slots: bits cutq must equal the copy bits cutm) or a Z mask (Z^l slots).
+// (P_l slots: bits cutq must equal the copy bits cutm) and, for the phase slots
+// whose copy bit is 1, masks of the qubits whose weight has bit 1, 2 or 4 set
+// (Z^l: weight 4; T^l: 1; S^l: 2).
 __device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, DiagState& d) {
   d.tmask = __ldg(&op->tmask);
   d.nsh = __ldg(&op->nsh);
@@ -51,7 +53,7 @@ __device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, Dia
   }
   const int ncut = __ldg(&op->ncut);
   const uint32_t cutz = __ldg(&op->cutz);
-  d.pmask = d.pval = d.zmask = 0;
+  d.pmask = d.pval = d.zmask = d.w1mask = d.w2mask = 0;
   for (int i = 0; i < ncut; ++i) {
     const uint32_t qb = 1u << op->cutq[i];
     const uint32_t l = (uint32_t)((node_id >> op->cutm[i]) & 1ull);
@@ -59,14 +61,17 @@ __device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, Dia
       d.pmask |= qb;
       if (l) d.pval |= qb;
     } else if (l) {
-      d.zmask |= qb;
+      const uint32_t w = op->cutw[i];
+      if (w & 4u) d.zmask |= qb;
+      if (w & 2u) d.w2mask |= qb;
+      if (w & 1u) d.w1mask |= qb;
     }
   }
 }
 
 // exponent of w (mod 8) and the projector test for index x
 __device__ __forceinline__ int diag_exp(const DiagState& d, uint32_t x, bool& keep) {
-  int e = __popc(x & d.tmask);
+  int e = __popc(x & d.tmask) + __popc(x & d.w1mask) + 2 * __popc(x & d.w2mask);
   int s2 = __popc(x & d.zmask);
 #pragma unroll
   for (int s = 0; s < kMaxShift; ++s)

@@ -172,7 +172,7 @@ __device__ __forceinline__ void smem_gate_k(float2 (&v)[1 << R], float2* xs, int
 }
 
 struct Diag {
-  uint32_t tmask, pmask, pval, zmask;
+  uint32_t tmask, pmask, pval, zmask, w1mask, w2mask;
   int nsh;
   uint32_t sh_d[kMaxShift], sh_m[kMaxShift];
 };
@@ -187,7 +187,7 @@ __device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, Dia
   }
   const int ncut = op->ncut;
   const uint32_t cutz = op->cutz;
-  d.pmask = d.pval = d.zmask = 0;
+  d.pmask = d.pval = d.zmask = d.w1mask = d.w2mask = 0;
   for (int i = 0; i < ncut; ++i) {
     const uint32_t qb = 1u << op->cutq[i];
     const uint32_t l = (uint32_t)((node_id >> op->cutm[i]) & 1ull);
@@ -195,7 +195,11 @@ __device__ __forceinline__ void load_diag(const OpRec* op, uint64_t node_id, Dia
       d.pmask |= qb;
       if (l) d.pval |= qb;
     } else if (l) {
-      d.zmask |= qb;
+      // phase slot w^{cutw l x}: weight bits 4 (Z^l), 2 and 1
+      const uint32_t w = op->cutw[i];
+      if (w & 4u) d.zmask |= qb;
+      if (w & 2u) d.w2mask |= qb;
+      if (w & 1u) d.w1mask |= qb;
     }
   }
 }
@@ -418,14 +422,17 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
       // same way
       bool proj = false, keep_t = true;
       uint32_t pm_r = 0, pv_r = 0;
+      uint32_t wreg = 0;  // weights 1 and 2 of phase slots on register ranks, 2 bits per rank
       if (op->ncut) {
         Diag d;
         load_diag(op, ne.node_id, d);
-        et += 4 * __popc(xt & d.zmask);
+        et += 4 * __popc(xt & d.zmask) + __popc(xt & d.w1mask) + 2 * __popc(xt & d.w2mask);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
           const uint32_t qb = 1u << op->rq[r];
           if (d.zmask & qb) B ^= 1u << r;
+          if (d.w1mask & qb) wreg |= 1u << (2 * r);
+          if (d.w2mask & qb) wreg |= 2u << (2 * r);
           if (d.pmask & qb) {
             pm_r |= 1u << r;
             if (d.pval & qb) pv_r |= 1u << r;
@@ -457,6 +464,23 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
           ew[w4] = 0u;
         }
       }
+      if (wreg) {
+        // weights 1..3 of phase slots on register rank r: + w_r in the fields of the
+        // elements j with bit r set.  Each add follows a reduction of every field to
+        // its value mod 8 (fields stay below 16, no carries between fields).
+        constexpr uint32_t kAdd[3] = {0x10101010u, 0x11001100u, 0x11110000u};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t wr = (wreg >> (2 * r)) & 3u;
+          if (!wr) continue;
+#pragma unroll
+          for (int w4 = 0; w4 < 4; ++w4) {
+            if (w4 * 8 >= NE) continue;
+            const uint32_t pat = r < 3 ? kAdd[r] : (((w4 >> (r - 3)) & 1) ? 0x11111111u : 0u);
+            ew[w4] = (ew[w4] & 0x77777777u) + wr * pat;
+          }
+        }
+      }
       // projector: the elements j with (j & pm_r) == pv_r, as a bit mask over j
       uint32_t kmask = 0xFFFFFFFFu;
       if (proj) {
@@ -473,7 +497,25 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
         const uint32_t off = (i == 0 ? (w << 3) : (w >> (4 * i - 3))) & 0x38u;
         return *(const float2*)((const char*)s_omega + off);
       };
-      if (proj) {
+      if (op->sign_only) {
+        // every exponent is 0 or 4 mod 8: flip the sign where bit 2 of the field is
+        // set (field i of a word at bits 4i .. 4i+3, so bit 2 moves up by 29 - 4i)
+        auto flip = [&](int j) {
+          const uint32_t sm = (ew[j >> 3] << (29 - 4 * (j & 7))) & 0x80000000u;
+          v[j] = make_float2(__uint_as_float(__float_as_uint(v[j].x) ^ sm),
+                             __uint_as_float(__float_as_uint(v[j].y) ^ sm));
+        };
+        if (proj) {
+#pragma unroll
+          for (int j = 0; j < NE; ++j) {
+            flip(j);
+            if (!((kmask >> j) & 1u)) v[j] = make_float2(0.f, 0.f);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NE; ++j) flip(j);
+        }
+      } else if (proj) {
 #pragma unroll
         for (int j = 0; j < NE; ++j) {
           v[j] = cmul(v[j], omega_at(j));

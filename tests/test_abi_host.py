@@ -158,11 +158,14 @@ def test_plan_levels_cover_the_copy_bits(R, C, d, b):
         sim.sim_destroy_circuit(circ)
 
 
-def test_controlled_x_cuts_on_the_host():
-    """Controlled X gates across the cut count as cuts (P_l on the control, X^l on the
-    target); the cut list equals the oracle's; one inside a half is unsupported."""
+@pytest.mark.parametrize("name", ["CX", "CT", "CY2"])
+def test_controlled_gate_cuts_on_the_host(name):
+    """Controlled X, T and Y^1/2 gates across the cut count as cuts (P_l on the
+    control, U^l on the target, Supplementary A, Eq. 1); the gate list round-trips
+    through the library's parser; the cut list equals the oracle's; a controlled
+    gate inside one half is unsupported, and so are multi-part cuts of them."""
     from circuits import cx_cut_circuit
-    R, C, b, depth, gates = cx_cut_circuit(1)
+    R, C, b, depth, gates = cx_cut_circuit(1, name)
     txt = oc.to_text(R, C, depth, 0, gates)
     c = sim.sim_build_circuit(gate_list=txt)
     try:
@@ -173,11 +176,18 @@ def test_controlled_x_cuts_on_the_host():
         sim.sim_destroy_cut(plan)
     finally:
         sim.sim_destroy_circuit(c)
-    bad = oc.to_text(4, 4, 3, 0, [(0, "H", 0), (1, "CX", 0, 1)])
+    bad = oc.to_text(4, 4, 3, 0, [(0, "H", 0), (1, name, 0, 1)])
     c = sim.sim_build_circuit(gate_list=bad)
     try:
         with pytest.raises(sim.SimError) as e:
             sim.sim_cut(c, 2)
+        assert e.value.code == sim.SIM_EUNSUPPORTED
+    finally:
+        sim.sim_destroy_circuit(c)
+    c = sim.sim_build_circuit(gate_list=txt)
+    try:
+        with pytest.raises(sim.SimError) as e:
+            sim.sim_cut_multi(c, [1, 3])
         assert e.value.code == sim.SIM_EUNSUPPORTED
     finally:
         sim.sim_destroy_circuit(c)

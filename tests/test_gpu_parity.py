@@ -496,6 +496,45 @@ def test_controlled_x_cuts(seed):
         sim.sim_destroy_circuit(circ)
 
 
+@pytest.mark.parametrize("name,seed", [("CT", 0), ("CT", 1), ("CY2", 0), ("CY2", 2)])
+def test_controlled_u_cuts(name, seed):
+    """Controlled T (diagonal U) and controlled Y^1/2 (non-diagonal U) across the cut
+    (Supplementary A, Eq. 1: P_l on the control, U^l on the target, in either half).
+    The fused sweeps write U^l as copy-independent gates around a phase slot
+    w^{b l x} (T^l: b = 1; (Y^1/2)^l = (X^1/2)^3 S^l X^1/2: b = 2); the plain path
+    applies U in the copies with l = 1.  Full 16-qubit vectors through both sweep
+    kernels and the plain FP64 path, and a copy list, against the oracle."""
+    from circuits import cx_cut_circuit
+    R, C, b, depth, gates = cx_cut_circuit(seed, name)
+    n, n_u = R * C, b * C
+    ref = oracle.statevector(n, gates).reshape(1 << (n - n_u), 1 << n_u)
+    circ = sim.sim_build_circuit(gate_list=oc.to_text(R, C, depth, 0, gates))
+    cp, c, copies, nu, nl = sim.sim_cut(circ, b)
+    try:
+        assert copies >= 16
+        runs = [(sim.SIM_C64, sim.SIM_SPLIT_BF16, TOL_SPLIT, {"sweep_kernel": 2}),
+                (sim.SIM_C64, sim.SIM_SPLIT_FP16, TOL_SPLIT, {"sweep_kernel": 2, "fuse_qubits": 8}),
+                (sim.SIM_C64, sim.SIM_SPLIT_FP16, TOL_SPLIT, {"sweep_kernel": 1, "fuse_qubits": 5}),
+                (sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN, TOL_PLAIN, None)]
+        for prec, kind, tol, opts in runs:
+            h = sim.sim_evolve_halves(cp, prec, 0, copies, None, None, opts)
+            got = amplitudes(h, kind, 1 << nl, 1 << nu).cpu().numpy()
+            sim.sim_destroy_halves(h)
+            assert rel_err(got, ref) <= tol, (prec, kind, opts)
+        gplan = oc.CutPlan(n, n_u, gates)
+        lst = np.array([copies - 1, 0, copies // 2 + 1], dtype=np.uint64)
+        part = sum(oracle.cut_amplitudes(gplan, None, None, int(k), int(k) + 1) for k in lst)
+        for prec, kind, tol in ((sim.SIM_C64, sim.SIM_SPLIT_FP16, TOL_SPLIT),
+                                (sim.SIM_C128_PLAIN, sim.SIM_FP64_PLAIN, TOL_PLAIN)):
+            h = sim.sim_evolve_halves_list(cp, prec, lst)
+            got = amplitudes(h, kind, 1 << nl, 1 << nu).cpu().numpy()
+            sim.sim_destroy_halves(h)
+            assert rel_err(got, part) <= tol, (prec, kind)
+    finally:
+        sim.sim_destroy_cut(cp)
+        sim.sim_destroy_circuit(circ)
+
+
 class PhaseRun(Run):
     """Run whose cut applies the last cut layers as output signs (sim_cut_ex)."""
 
