@@ -290,7 +290,7 @@ struct PairArgs {
 // STATS: fuse the FP64 statistics of the final amplitudes into the epilogue.
 // STG: operand stages.  SW: accumulator columns per epilogue step (8 or 16), which
 // sets the staging box (32 rows x SW floats, 32- or 64-byte TMA swizzle).
-template <bool STATS, bool SIGN, int STG, int SW, int NBUF, int UNR, int EW>
+template <bool STATS, bool SIGN, int STG, int SW, int NBUF, int UNR, int EW, bool DIRECT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constant__ CUtensorMap mapA_lo,
                         const __grid_constant__ CUtensorMap mapB_hi, const __grid_constant__ CUtensorMap mapB_lo,
@@ -481,6 +481,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
         const bool last = kc == args.nchunks - 1;
         // final values of a read-modify-write pass are formed in registers when they
         // feed the statistics; otherwise the TMA reduce-add accumulates them in L2
+        // (direct launches never read back: one chunk, no accumulation)
         const bool rmw_regs = STATS && last && rmw;
         const int acc = it & 1;
         const uint32_t acc_phase = (uint32_t)(it >> 1) & 1u;
@@ -492,8 +493,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
         }
         tc_fence_after();
         // an earlier chunk of this tile was written by this warp: its writes must be
-        // complete before they are added to or read back
-        if (kc > 0) {
+        // complete before they are added to or read back (direct stores: the same
+        // thread wrote them, in program order)
+        if (!DIRECT && kc > 0) {
           if (lane == 0) bulk_wait_all();
           __syncwarp();
         }
@@ -556,6 +558,23 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
               if (okv) atomicAdd(&s_hist[min(max(bin, 0), SIM_KS_BINS - 1)], 1u);
             }
           }
+          if constexpr (DIRECT) {
+            // each lane writes its row's SW floats as SW / 8 full 32-byte sectors
+            // (256-bit stores): the sectors a TMA box store writes, without the
+            // shared-memory staging
+            if (rowok) {
+              float* dst = args.C + grow * args.N2 + gcol0;
+#pragma unroll
+              for (int j = 0; j < SW / 8; ++j)
+                if (gcol0 + 8 * j < args.N2)
+                  asm volatile("st.global.L1::no_allocate.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(
+                                   dst + 8 * j),
+                               "f"(v[8 * j]), "f"(v[8 * j + 1]), "f"(v[8 * j + 2]), "f"(v[8 * j + 3]), "f"(v[8 * j + 4]),
+                               "f"(v[8 * j + 5]), "f"(v[8 * j + 6]), "f"(v[8 * j + 7])
+                               : "memory");
+            }
+            return;
+          }
           float* buf = bufs + sbuf * (32 * SW);
           if (lane == 0) {
             if (NBUF == 2)
@@ -605,8 +624,10 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
         }
       }
     // all output writes of this warp complete (and its staging buffers free) before exit
-    if (lane == 0) bulk_wait_all();
-    __syncwarp();
+    if (!DIRECT) {
+      if (lane == 0) bulk_wait_all();
+      __syncwarp();
+    }
     if (STATS) {
       for (int o = 16; o > 0; o >>= 1) {
         st_p += __shfl_xor_sync(0xffffffffu, st_p, o);
@@ -675,7 +696,7 @@ bool make_output_map(CUtensorMap* map, float* C, int64_t M, int64_t N2, int sw) 
   return r == CUDA_SUCCESS;
 }
 
-template <bool STATS, bool SIGN, int STG, int SW, int NBUF, int UNR, int EW>
+template <bool STATS, bool SIGN, int STG, int SW, int NBUF, int UNR, int EW, bool DIRECT>
 cudaError_t launch_variant(const CUtensorMap (&maps)[4], const CUtensorMap& mapC, const PairArgs& k, uint32_t idesc,
                            int num_sms, cudaStream_t s) {
   constexpr int SMEM = PairSmem<STG, SW, NBUF, EW>::BYTES;
@@ -684,7 +705,7 @@ cudaError_t launch_variant(const CUtensorMap (&maps)[4], const CUtensorMap& mapC
   int max_pairs = 0;
   cudaError_t e = setup.run(
       [&](int& n) {
-        cudaError_t r = cudaFuncSetAttribute(tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW>,
+        cudaError_t r = cudaFuncSetAttribute(tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW, DIRECT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (r != cudaSuccess) return r;
         // one resident pair per SM pair: as many clusters as can be co-scheduled at once
@@ -693,7 +714,7 @@ cudaError_t launch_variant(const CUtensorMap (&maps)[4], const CUtensorMap& mapC
         cfg.blockDim = dim3(THREADS, 1, 1);
         cfg.dynamicSmemBytes = SMEM;
         n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW>, &cfg) !=
+        if (cudaOccupancyMaxActiveClusters(&n, tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW, DIRECT>, &cfg) !=
                 cudaSuccess ||
             n < 1) {
           cudaGetLastError();
@@ -706,7 +727,7 @@ cudaError_t launch_variant(const CUtensorMap (&maps)[4], const CUtensorMap& mapC
   int pairs = max_pairs;
   if ((int64_t)pairs > k.num_tiles) pairs = (int)k.num_tiles;
   if (pairs < 1) pairs = 1;
-  tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW><<<2 * pairs, THREADS, SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], mapC, k,
+  tc_gemm_pair_kernel<STATS, SIGN, STG, SW, NBUF, UNR, EW, DIRECT><<<2 * pairs, THREADS, SMEM, s>>>(maps[0], maps[1], maps[2], maps[3], mapC, k,
                                                                       idesc);
   return cudaGetLastError();
 }
@@ -759,7 +780,12 @@ cudaError_t launch_tc_gemm_pair(const TcGemmArgs& a, cudaStream_t s) {
   k.tm.num_nb = (a.N2 + BN - 1) / BN;
   // 32 pair tiles (8192 rows of A, 16 MB of split operands) per raster group stay in
   // L2 while the group sweeps B, which is then read from DRAM once per group
-  k.tm.group = a.group_m > 0 ? a.group_m : 32;
+  // (SIM_GEMM_GROUP in the environment overrides the default, for comparisons)
+  static const int env_group = [] {
+    const char* e = getenv("SIM_GEMM_GROUP");
+    return e ? atoi(e) : 0;
+  }();
+  k.tm.group = a.group_m > 0 ? a.group_m : (env_group > 0 ? env_group : 32);
   k.num_tiles = k.tm.num_mb * k.tm.num_nb;
   k.scale_a = a.scale_a;
   k.scale_b = a.scale_b;
@@ -781,13 +807,30 @@ cudaError_t launch_tc_gemm_pair(const TcGemmArgs& a, cudaStream_t s) {
   // (K <= 128 copies) the epilogue is the bound and 16 epilogue warps hide its
   // latency (2 operand stages of 64 KB, 181,760 bytes of shared memory); otherwise 3
   // stages and 8 epilogue warps (230,912 bytes).
-#define LV(G, E)                                                                                          \
-  (stats ? (sign ? launch_variant<true, true, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s)                 \
-                 : launch_variant<true, false, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s))               \
-         : (sign ? launch_variant<false, true, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s)                \
-                 : launch_variant<false, false, G, 16, 1, 2, E>(maps, mapC, k, idesc, nsm, s)))
+  // Direct epilogue stores (each lane writes full 32-byte sectors of its row from
+  // registers, no shared-memory staging) when the contraction writes each output
+  // once: one copy chunk and no accumulation, 32-byte aligned rows.  Measured on the
+  // 2^30-amplitude workload (K = 256): 3.86 ms against 4.22 ms with TMA box stores
+  // from staging, whose shared-memory traffic competed with the operand stages.
+  // Contractions that add chunks into the output keep the staging path, whose TMA
+  // reduce-adds accumulate in L2 (the 42-qubit contraction, 64 chunks: 72 ms against
+  // 115 ms when every chunk reads the block back through the SMs).
+  // SIM_EPI_DIRECT=0 selects the staging path everywhere, for comparisons.
+  static const bool direct_ok = [] {
+    const char* e = getenv("SIM_EPI_DIRECT");
+    return !(e && e[0] == '0');
+  }();
+  const bool direct = direct_ok && k.nchunks == 1 && !a.accumulate && ((((uintptr_t)a.C) & 31u) == 0) &&
+                      (a.N2 % 8) == 0;
+#define LV2(G, E, D)                                                                                     \
+  (stats ? (sign ? launch_variant<true, true, G, 16, 1, 2, E, D>(maps, mapC, k, idesc, nsm, s)             \
+                 : launch_variant<true, false, G, 16, 1, 2, E, D>(maps, mapC, k, idesc, nsm, s))           \
+         : (sign ? launch_variant<false, true, G, 16, 1, 2, E, D>(maps, mapC, k, idesc, nsm, s)            \
+                 : launch_variant<false, false, G, 16, 1, 2, E, D>(maps, mapC, k, idesc, nsm, s)))
+#define LV(G, E) (direct ? LV2(G, E, true) : LV2(G, E, false))
   cudaError_t e = k.nkb <= 4 ? LV(2, 16) : LV(3, 8);
 #undef LV
+#undef LV2
   note_launches(SIM_PHASE_CONTRACT, 1);
   return e;
 }

@@ -6,10 +6,11 @@
                     on 4096 seeded entries each, against the oracle's gate-by-gate
                     FP64 half-states (Supplementary A, Eqs. 4-5 per half), and the
                     4096 x 4096 amplitude block of that copy (Eq. 8 with one term)
-  64-qubit halves   the same for one seeded copy of the 8x8, depth-22 circuit (two
-                    32-qubit halves, 64 GB each in FP64 on the host).  The oracle
-                    takes many minutes per half, so this case runs only when
-                    SIM_LONG_TESTS=1 is set
+  64-qubit halves   one seeded copy of the 8x8, depth-22 circuit: the upper
+                    32-qubit leaf (64 GB in FP64 on the host, about four minutes of
+                    oracle time) against the oracle, and the split block against the
+                    plain FP64 path's; with SIM_LONG_TESTS=1 both leaves and the
+                    block against the oracle
   Born sampling     2^16 Born-rule samples of the full 2^30-amplitude vector of the
                     30-qubit 6x5 depth-16 circuit: proposals bit-exact against the
                     oracle's stream, decisions against the oracle's on its own FP64
@@ -59,22 +60,26 @@ def leaf(h, half, k, n, dt):
     return buf.cpu().numpy().astype(np.complex128)
 
 
-def halves_case(R, C, d, seed, b, nsel, copy_seed):
+def halves_case(R, C, d, seed, b, nsel, copy_seed, halves=(0, 1)):
     """One seeded copy of the circuit: GPU leaves (complex64 fused sweeps in both
     pass formations, complex128 plain path) on nsel seeded entries per half and the
-    split-fp16 / FP64 contractions of that copy, each against the oracle."""
+    split-fp16 / FP64 contractions of that copy, against the oracle's half-states
+    of `halves` (the block against the oracle when both are given, else the split
+    block against the plain FP64 path's block)."""
     gates, oplan = oc.grid_cut(R, C, d, seed, b)
     rng = np.random.default_rng(copy_seed)
     k = int(rng.integers(0, oplan.copies))
     su = np.sort(rng.choice(1 << oplan.n_u, nsel, replace=False)).astype(np.uint64)
     sl = np.sort(rng.choice(1 << oplan.n_l, nsel, replace=False)).astype(np.uint64)
     # the oracle's half-states, one at a time (2^n complex128 each), at the selections
-    want = []
+    want = [None, None]
     for half, sel in ((0, su), (1, sl)):
-        hs = oracle.half_state(oplan, half, k)
-        want.append(hs[sel.astype(np.int64)].copy())
-        del hs
-    outer = want[1][:, None] * want[0][None, :]
+        if half in halves:
+            hs = oracle.half_state(oplan, half, k)
+            want[half] = hs[sel.astype(np.int64)].copy()
+            del hs
+    outer = want[1][:, None] * want[0][None, :] if len(halves) == 2 else None
+    blocks = {}
     circ = sim.sim_build_circuit(R, C, d, seed, b)
     plan, c, copies, nu, nl = sim.sim_cut(circ, b)
     try:
@@ -84,12 +89,15 @@ def halves_case(R, C, d, seed, b, nsel, copy_seed):
             h = sim.sim_evolve_halves_list(plan, sim.SIM_C64, lst, su, sl, opts={"pass_order": order})
             try:
                 for half, n in ((0, su.size), (1, sl.size)):
-                    got = leaf(h, half, k, n, torch.complex64)
-                    assert rel_err(got, want[half]) <= TOL_SPLIT, (order, half)
+                    if want[half] is not None:
+                        got = leaf(h, half, k, n, torch.complex64)
+                        assert rel_err(got, want[half]) <= TOL_SPLIT, (order, half)
                 out = torch.zeros((sl.size, su.size), dtype=torch.complex64, device="cuda")
                 sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, False, out)
                 sim.sim_status()
-                assert rel_err(out.cpu().numpy(), outer) <= TOL_SPLIT, order
+                blocks[order] = out.cpu().numpy()
+                if outer is not None:
+                    assert rel_err(blocks[order], outer) <= TOL_SPLIT, order
                 del out
             finally:
                 sim.sim_destroy_halves(h)
@@ -97,11 +105,17 @@ def halves_case(R, C, d, seed, b, nsel, copy_seed):
         hp = sim.sim_evolve_halves_list(plan, sim.SIM_C128_PLAIN, lst, su, sl)
         try:
             for half, n in ((0, su.size), (1, sl.size)):
-                assert rel_err(leaf(hp, half, k, n, torch.complex128), want[half]) <= TOL_PLAIN, half
+                if want[half] is not None:
+                    assert rel_err(leaf(hp, half, k, n, torch.complex128), want[half]) <= TOL_PLAIN, half
             outp = torch.zeros((sl.size, su.size), dtype=torch.complex128, device="cuda")
             sim.sim_amplitudes(hp, sim.SIM_FP64_PLAIN, False, outp)
             sim.sim_status()
-            assert rel_err(outp.cpu().numpy(), outer) <= TOL_PLAIN
+            plain = outp.cpu().numpy()
+            if outer is not None:
+                assert rel_err(plain, outer) <= TOL_PLAIN
+            else:
+                for order, blk in blocks.items():
+                    assert rel_err(blk, plain) <= TOL_SPLIT, order
         finally:
             sim.sim_destroy_halves(hp)
     finally:
@@ -114,9 +128,10 @@ def test_30q_halves_match_oracle():
     halves_case(6, 10, 16, 0, 3, 4096, 30)
 
 
-@pytest.mark.skipif(not LONG, reason="the FP64 oracle takes many minutes per 32-qubit half (SIM_LONG_TESTS=1)")
 def test_64q_halves_match_oracle():
-    halves_case(8, 8, 22, 0, 4, 4096, 64)
+    """The upper 32-qubit leaf against the oracle (about four minutes of oracle time
+    on 16 cores); both leaves and the block with SIM_LONG_TESTS=1 (about eight)."""
+    halves_case(8, 8, 22, 0, 4, 4096, 64, halves=(0, 1) if LONG else (0,))
 
 
 def test_born_samples_2to30_match_oracle():

@@ -1,6 +1,8 @@
 """Randomized GPU parity (fixed seed, so deterministic): random small grids, depths,
 circuit seeds, cut rows, fuse widths, sweep kernels, pass formations and the
-output-phase option, each full vector against the oracle's uncut state vector.
+output-phase option, half of them with controlled X, T and Y^1/2 gates across the
+cut added (Supplementary A, Eq. 1), each full vector against the oracle's uncut
+state vector.
 
 Tolerances: split fp16 and split bf16 <= 1e-5, FP64 plain <= 1e-12.  Split bf16 is
 refused (SIM_EUNSUPPORTED) below 16 copies, where too few products average its
@@ -43,15 +45,20 @@ def cases(count=120, seed=2024):
         b = int(rng.integers(1, R))
         d = int(rng.integers(3, 26))
         out.append((R, C, d, int(rng.integers(0, 10 ** 6)), b, int(rng.integers(4, 14)), int(rng.integers(0, 3)),
-                    int(rng.integers(0, 2)), bool(rng.integers(0, 2))))
+                    int(rng.integers(0, 2)), bool(rng.integers(0, 2)), bool(rng.integers(0, 2))))
     return out
 
 
-@pytest.mark.parametrize("R,C,d,seed,b,fuse,kernel,order,phase", cases())
-def test_random_circuit_full_vector(R, C, d, seed, b, fuse, kernel, order, phase):
-    gates = oc.generate(R, C, d, seed, b)
+@pytest.mark.parametrize("R,C,d,seed,b,fuse,kernel,order,phase,cu", cases())
+def test_random_circuit_full_vector(R, C, d, seed, b, fuse, kernel, order, phase, cu):
+    if cu:
+        from circuits import with_cross_controlled
+        gates = with_cross_controlled(R, C, d, seed, b, np.random.default_rng(seed))
+        circ = sim.sim_build_circuit(gate_list=oc.to_text(R, C, d, seed, gates))
+    else:
+        gates = oc.generate(R, C, d, seed, b)
+        circ = sim.sim_build_circuit(R, C, d, seed, b)
     ref = oracle.statevector(R * C, gates).reshape(1 << ((R - b) * C), 1 << (b * C))
-    circ = sim.sim_build_circuit(R, C, d, seed, b)
     plan, c, copies, nu, nl = sim.sim_cut_ex(circ, b, output_phase_cuts=phase)
     opts = {"fuse_qubits": fuse, "sweep_kernel": kernel, "pass_order": order}
     try:
