@@ -67,14 +67,26 @@ int fail(int code, const std::string& msg) {
   } while (0)
 
 // ---------------------------------------------------------------------------
-// Device memory pool: cudaMalloc'd blocks cached by (device, rounded size) and
-// reused in stream order.  Sizes are rounded up to 2 MiB above 1 MiB and to a
-// power of two below.
+// Device memory pool: cudaMalloc'd blocks cached by (device, rounded size).  Sizes
+// are rounded up to 2 MiB above 1 MiB and to a power of two below.
+// Reuse is stream-ordered.  A block freed with a stream carries an event recorded
+// on that stream at the free, after all the work that used it.  A later request on
+// the same stream reuses it at once (stream order already puts the new work after
+// the old); a request on another stream takes a block whose event has completed,
+// or else makes its stream wait for the event (cudaStreamWaitEvent, no host wait).
+// So buffers can go back to the pool while kernels still use them, and callers on
+// several streams never share a block across in-flight work.
 // ---------------------------------------------------------------------------
 struct Pool {
+  struct Blk {
+    void* p;
+    cudaEvent_t ev;   // recorded on st at the free (null: the block was idle)
+    cudaStream_t st;
+  };
   std::mutex mu;
-  std::map<std::pair<int, size_t>, std::vector<void*>> free_blocks;
+  std::map<std::pair<int, size_t>, std::vector<Blk>> free_blocks;
   std::unordered_map<void*, std::pair<int, size_t>> owner;
+  std::map<int, std::vector<cudaEvent_t>> spare_ev;  // per device
 
   static size_t round(size_t n) {
     if (n <= 256) return 256;
@@ -87,7 +99,24 @@ struct Pool {
     return (n + g - 1) / g * g;
   }
 
-  cudaError_t alloc(void** p, size_t n) {
+  // (mu held) an event of the current device
+  cudaEvent_t take_event(int dev) {
+    auto& v = spare_ev[dev];
+    if (!v.empty()) {
+      cudaEvent_t e = v.back();
+      v.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return e;
+  }
+
+  // n bytes for work on stream st
+  cudaError_t alloc(void** p, size_t n, cudaStream_t st) {
     int dev = 0;
     cudaGetDevice(&dev);
     const size_t r = round(n);
@@ -95,10 +124,29 @@ struct Pool {
       std::lock_guard<std::mutex> lk(mu);
       auto it = free_blocks.find({dev, r});
       if (it != free_blocks.end() && !it->second.empty()) {
-        *p = it->second.back();
-        it->second.pop_back();
-        owner[*p] = {dev, r};
-        return cudaSuccess;
+        std::vector<Blk>& v = it->second;
+        // an idle block, else the latest freed on this stream, else the latest;
+        // a block still in use orders st after its free (stream identity alone is
+        // not trusted: a destroyed stream's handle can come back for a new one)
+        int pick = -1, same = -1;
+        for (int i = (int)v.size() - 1; i >= 0 && pick < 0; --i) {
+          if (!v[i].ev || cudaEventQuery(v[i].ev) == cudaSuccess) pick = i;
+          else if (same < 0 && v[i].st == st) same = i;
+        }
+        cudaGetLastError();  // a not-ready query
+        cudaError_t e = cudaSuccess;
+        if (pick < 0) {
+          pick = same >= 0 ? same : (int)v.size() - 1;
+          e = cudaStreamWaitEvent(st, v[pick].ev, 0);
+        }
+        if (e == cudaSuccess) {
+          *p = v[pick].p;
+          if (v[pick].ev) spare_ev[dev].push_back(v[pick].ev);
+          v.erase(v.begin() + pick);
+          owner[*p] = {dev, r};
+          return cudaSuccess;
+        }
+        cudaGetLastError();
       }
     }
     cudaError_t e = cudaMalloc(p, r);
@@ -116,12 +164,31 @@ struct Pool {
     return cudaSuccess;
   }
 
-  void free(void* p) {
+  // back to the pool after the work enqueued so far on st (ordered), or at once
+  // (the caller has waited for every use of the block)
+  void free(void* p, cudaStream_t st, bool ordered) {
     if (!p) return;
     std::lock_guard<std::mutex> lk(mu);
     auto it = owner.find(p);
     if (it == owner.end()) return;
-    free_blocks[it->second].push_back(p);
+    Blk b{p, nullptr, st};
+    if (ordered) {
+      // the event belongs to the block's device, whichever device is current
+      const int dev = it->second.first;
+      int cur = dev;
+      cudaGetDevice(&cur);
+      if (cur != dev) cudaSetDevice(dev);
+      b.ev = take_event(dev);
+      if (!b.ev || cudaEventRecord(b.ev, st) != cudaSuccess) {
+        cudaGetLastError();
+        if (b.ev) spare_ev[dev].push_back(b.ev);
+        b.ev = nullptr;
+        cudaStreamSynchronize(st);  // no event: wait instead
+        cudaGetLastError();
+      }
+      if (cur != dev) cudaSetDevice(cur);
+    }
+    free_blocks[it->second].push_back(b);
     owner.erase(it);
   }
 
@@ -129,7 +196,13 @@ struct Pool {
     std::lock_guard<std::mutex> lk(mu);
     for (auto& kv : free_blocks) {
       if (dev >= 0 && kv.first.first != dev) continue;
-      for (void* p : kv.second) cudaFree(p);
+      for (const Blk& b : kv.second) {
+        if (b.ev) {
+          cudaEventSynchronize(b.ev);
+          spare_ev[kv.first.first].push_back(b.ev);
+        }
+        cudaFree(b.p);
+      }
       kv.second.clear();
     }
   }
@@ -140,16 +213,20 @@ Pool& pool() {
   return *p;
 }
 
+// A pool block for work on one stream, returned to the pool (stream-ordered) when
+// the DevBuf goes out of scope, with its kernels possibly still running.
 struct DevBuf {
   void* p = nullptr;
+  cudaStream_t st = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  ~DevBuf() { pool().free(p); }
-  cudaError_t alloc(size_t n) {
-    pool().free(p);
+  ~DevBuf() { pool().free(p, st, true); }
+  cudaError_t alloc(size_t n, cudaStream_t s) {
+    pool().free(p, st, true);
     p = nullptr;
-    return pool().alloc(&p, n ? n : 1);
+    st = s;
+    return pool().alloc(&p, n ? n : 1, s);
   }
   template <typename T>
   T* as() const {
@@ -249,9 +326,11 @@ int device_info(DeviceInfo** out) {
 // Op tables of a plan live in pool memory, uploaded on the caller's stream the
 // first time the plan is evolved on a device.
 void free_plan_ops(CutPlan& P) {
+  // after the work enqueued so far on the last stream that used them
+  const cudaStream_t st = (cudaStream_t)P.ops_stream;
   for (int h = 0; h < 2; ++h) {
-    pool().free(P.d_ops[h]);
-    pool().free(P.d_plain_ops[h]);
+    pool().free(P.d_ops[h], st, true);
+    pool().free(P.d_plain_ops[h], st, true);
     P.d_ops[h] = P.d_plain_ops[h] = nullptr;
   }
   P.device = -1;
@@ -260,12 +339,25 @@ void free_plan_ops(CutPlan& P) {
 int upload_plan_ops(CutPlan& P, cudaStream_t st) {
   int dev = 0;
   CK(cudaGetDevice(&dev));
-  if (P.device == dev && P.d_ops[0]) return SIM_OK;
+  if (P.device == dev && P.d_ops[0]) {
+    // another stream now uses the tables: order it after their upload
+    if ((cudaStream_t)P.ops_stream != st) {
+      cudaEvent_t ev = nullptr;
+      CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      cudaError_t e = cudaEventRecord(ev, (cudaStream_t)P.ops_stream);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev, 0);
+      cudaEventDestroy(ev);
+      CK(e);
+      P.ops_stream = st;
+    }
+    return SIM_OK;
+  }
   free_plan_ops(P);
+  P.ops_stream = st;
   for (int h = 0; h < 2; ++h) {
     const auto& ops = P.sched[h].ops;
     void* p = nullptr;
-    CK(pool().alloc(&p, sizeof(OpRec) * (ops.size() + 1)));
+    CK(pool().alloc(&p, sizeof(OpRec) * (ops.size() + 1), st));
     P.d_ops[h] = (OpRec*)p;
     if (!ops.empty())
       CK(cudaMemcpyAsync(P.d_ops[h], ops.data(), sizeof(OpRec) * ops.size(), cudaMemcpyHostToDevice, st));
@@ -278,7 +370,7 @@ int upload_plan_ops(CutPlan& P, cudaStream_t st) {
       flat.insert(flat.end(), L.gates.begin(), L.gates.end());
       flat.insert(flat.end(), L.diags.begin(), L.diags.end());
     }
-    CK(pool().alloc(&p, sizeof(OpRec) * (flat.size() + 1)));
+    CK(pool().alloc(&p, sizeof(OpRec) * (flat.size() + 1), st));
     P.d_plain_ops[h] = (OpRec*)p;
     if (!flat.empty())
       CK(cudaMemcpyAsync(P.d_plain_ops[h], flat.data(), sizeof(OpRec) * flat.size(), cudaMemcpyHostToDevice, st));
@@ -501,17 +593,17 @@ int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel,
       }
       CK(cudaHostGetDevicePointer(&lp[j], hlvl[j].p, 0));
     } else {
-      CK(lvl[j].alloc(bytes));
+      CK(lvl[j].alloc(bytes, st));
       lp[j] = lvl[j].p;
     }
   }
   DevBuf table;
-  CK(table.alloc(sizeof(NodeEntry) * (prog.table.size() + 1)));
+  CK(table.alloc(sizeof(NodeEntry) * (prog.table.size() + 1), st));
   CK(cudaMemcpyAsync(table.p, prog.table.data(), sizeof(NodeEntry) * prog.table.size(), cudaMemcpyHostToDevice, st));
   note_bytes(sizeof(NodeEntry) * prog.table.size(), 0);
-  // the pool may hand the device buffers to the next call on this stream only
-  // after the launches are enqueued, which keeps reuse stream-ordered; host level
-  // buffers are released after the stream has finished with them
+  // the device buffers go back to the pool (stream-ordered, behind these launches)
+  // when this function returns; host level buffers only after the stream has
+  // finished with them
   const int rc = enqueue_tree(P, h, prog, lp.data(), table.as<NodeEntry>(), d_sel, nsel, leafsel, st,
                               opts ? opts->sweep_kernel : 0,
                               (opts && opts->sweep_threads > 0) ? opts->sweep_threads : 256);
@@ -534,9 +626,9 @@ int evolve_plain_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_se
   if (cap < 1) cap = 1;
   const uint64_t batch = std::min(K, cap);
   DevBuf work, ids, table;
-  if (!full) CK(work.alloc(state_bytes * batch));
-  CK(ids.alloc(sizeof(uint64_t) * batch));
-  CK(table.alloc(sizeof(NodeEntry) * batch));
+  if (!full) CK(work.alloc(state_bytes * batch, st));
+  CK(ids.alloc(sizeof(uint64_t) * batch, st));
+  CK(table.alloc(sizeof(NodeEntry) * batch, st));
   std::vector<uint64_t> hid(batch);
   std::vector<NodeEntry> htab(batch);
   PhaseScope ps(SIM_PHASE_PLAIN, st);
@@ -631,16 +723,16 @@ int contract_impl(const void* lA, const void* lB, int64_t K, int64_t M, int64_t 
   const int64_t kpad = ((2 * K + 63) / 64) * 64;
   const int64_t N2 = 2 * N;
   DevBuf ahi, alo, bhi, blo, sc;
-  CK(ahi.alloc((size_t)M * kpad * 2));
-  CK(alo.alloc((size_t)M * kpad * 2));
-  CK(bhi.alloc((size_t)N2 * kpad * 2));
-  CK(blo.alloc((size_t)N2 * kpad * 2));
+  CK(ahi.alloc((size_t)M * kpad * 2, st));
+  CK(alo.alloc((size_t)M * kpad * 2, st));
+  CK(bhi.alloc((size_t)N2 * kpad * 2, st));
+  CK(blo.alloc((size_t)N2 * kpad * 2, st));
   const float* sa = nullptr;
   const float* sb = nullptr;
   {
   PhaseScope ps(SIM_PHASE_PACK, st);
   if (fp16) {
-    CK(sc.alloc(4 * sizeof(float)));
+    CK(sc.alloc(4 * sizeof(float), st));
     CK(launch_absmax_c64(lA, K * M, sc.as<float>(), st));
     CK(launch_absmax_c64(lB, K * N, sc.as<float>() + 2, st));
     sa = sc.as<float>() + 1;
@@ -711,8 +803,8 @@ int rt_enqueue_tree(const CutPlan& P, int half, const TreeProgram& prog, void* c
                     int threads) {
   return enqueue_tree(P, half, prog, lvl, table, d_sel, nsel, leafsel, st, kernel_choice, threads);
 }
-cudaError_t rt_alloc(void** p, size_t n) { return pool().alloc(p, n); }
-void rt_free(void* p) { pool().free(p); }
+cudaError_t rt_alloc(void** p, size_t n, cudaStream_t st) { return pool().alloc(p, n, st); }
+void rt_free(void* p, cudaStream_t st) { pool().free(p, st, true); }
 int rt_device(int** d_status, int* num_sms) {
   DeviceInfo* di = nullptr;
   const int rc = device_info(&di);
@@ -977,14 +1069,14 @@ int evolve_halves_impl(sim_cut_plan plan, int precision, CopySet&& cs, const uin
     h->full[hh] = sels[hh] == nullptr;
     h->nsel[hh] = h->full[hh] ? (int64_t)1 << nq[hh] : (int64_t)nreq[hh];
     const size_t bytes = esz * (size_t)K * (size_t)h->nsel[hh];
-    cudaError_t e = pool().alloc(&h->leafsel[hh], bytes);
+    cudaError_t e = pool().alloc(&h->leafsel[hh], bytes, st);
     if (e != cudaSuccess) {
       cleanup();
       return fail(e == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA,
                   "cannot allocate the leaf buffers of the evolved halves");
     }
     if (!h->full[hh]) {
-      e = pool().alloc(&h->d_sel[hh], sizeof(uint64_t) * h->nsel[hh]);
+      e = pool().alloc(&h->d_sel[hh], sizeof(uint64_t) * h->nsel[hh], st);
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->d_sel[hh], sels[hh], sizeof(uint64_t) * h->nsel[hh], cudaMemcpyHostToDevice, st);
       note_bytes(sizeof(uint64_t) * h->nsel[hh], 0);
@@ -999,7 +1091,7 @@ int evolve_halves_impl(sim_cut_plan plan, int precision, CopySet&& cs, const uin
     for (int hh = 0; hh < 2; ++hh) {
       std::vector<int> qs;
       for (const auto& pr : P.out_cz) qs.push_back(hh == 0 ? pr.first : pr.second - P.n_u);
-      cudaError_t e = pool().alloc((void**)&h->out_code[hh], sizeof(uint32_t) * h->nsel[hh]);
+      cudaError_t e = pool().alloc((void**)&h->out_code[hh], sizeof(uint32_t) * h->nsel[hh], st);
       if (e == cudaSuccess)
         e = launch_out_codes((const uint64_t*)h->d_sel[hh], h->nsel[hh], qs.data(), (int)qs.size(), h->out_code[hh],
                              st);
@@ -1085,7 +1177,7 @@ int sim_amplitudes(sim_halves h, int contraction, int accumulate, void* out, voi
   const size_t esz = contraction == SIM_FP64_PLAIN ? 16 : 8;
   const size_t bytes = esz * (size_t)h->nsel[0] * (size_t)h->nsel[1];
   DevBuf stage;
-  CK(stage.alloc(bytes));
+  CK(stage.alloc(bytes, st));
   if (accumulate) CK(cudaMemcpyAsync(stage.p, out, bytes, cudaMemcpyHostToDevice, st));
   note_bytes(accumulate ? bytes : 0, bytes);
   int rc = amplitudes_impl(h, contraction, accumulate, stage.p, st);
@@ -1102,8 +1194,8 @@ int sim_stats(const void* amps, int is_c128, uint64_t count, int n_qubits, doubl
   if (!amps || !stats_out) return fail(SIM_EINVAL, "amps and stats_out must not be NULL");
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf acc, hist;
-  CK(acc.alloc(4 * sizeof(double)));
-  CK(hist.alloc(SIM_KS_BINS * sizeof(unsigned long long)));
+  CK(acc.alloc(4 * sizeof(double), st));
+  CK(hist.alloc(SIM_KS_BINS * sizeof(unsigned long long), st));
   {
     PhaseScope ps(SIM_PHASE_STATS, st);
     CK(launch_stats(amps, is_c128, count, n_qubits, acc.as<double>(), hist.as<unsigned long long>(), st));
@@ -1126,8 +1218,8 @@ int sim_amplitudes_stats(sim_halves h, int contraction, int accumulate, void* ou
   if (!is_device_ptr(out_dev)) return fail(SIM_EINVAL, "sim_amplitudes_stats writes device memory only");
   cudaStream_t st = (cudaStream_t)stream;
   DevBuf acc, hist;
-  CK(acc.alloc(4 * sizeof(double)));
-  CK(hist.alloc(SIM_KS_BINS * sizeof(unsigned long long)));
+  CK(acc.alloc(4 * sizeof(double), st));
+  CK(hist.alloc(SIM_KS_BINS * sizeof(unsigned long long), st));
   CK(cudaMemsetAsync(acc.p, 0, 3 * sizeof(double), st));
   CK(cudaMemsetAsync(hist.p, 0, SIM_KS_BINS * sizeof(unsigned long long), st));
   int rc = amplitudes_impl(h, contraction, accumulate, out_dev, st, acc.as<double>(), hist.as<unsigned long long>());
@@ -1328,7 +1420,7 @@ int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, co
       if (n[p] == 0) return fail(SIM_EINVAL, "empty selection");
       for (int64_t i = 0; i < n[p]; ++i)
         if (sels[p][i] >> M.nq[p]) return fail(SIM_EINVAL, "selected index out of range for its part");
-      CK(dsel[p].alloc(sizeof(uint64_t) * n[p]));
+      CK(dsel[p].alloc(sizeof(uint64_t) * n[p], st));
       CK(cudaMemcpyAsync(dsel[p].p, sels[p], sizeof(uint64_t) * n[p], cudaMemcpyHostToDevice, st));
       note_bytes(sizeof(uint64_t) * n[p], 0);
     }
@@ -1350,7 +1442,7 @@ int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, co
       }
     int rc = upload_plan_ops(M.part[p], st);
     if (rc) return rc;
-    CK(leaves[p].alloc(esz * cs.size() * (size_t)n[p]));
+    CK(leaves[p].alloc(esz * cs.size() * (size_t)n[p], st));
     rc = precision == SIM_C64
              ? evolve_c64_half(M.part[p], 0, cs, (const uint64_t*)dsel[p].p, n[p], full, leaves[p].p, st, opts)
              : evolve_plain_half(M.part[p], 0, cs, (const uint64_t*)dsel[p].p, n[p], full, leaves[p].p, st);
@@ -1367,7 +1459,7 @@ int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, co
     const int64_t rows = (p + 1 < t ? ((int64_t)1 << M.c[p + 1]) : 1) * n[p];
     void* dst = out_dev;
     if (p + 1 < t) {
-      CK(tb[p & 1].alloc(esz * (size_t)rows * (size_t)ncols));
+      CK(tb[p & 1].alloc(esz * (size_t)rows * (size_t)ncols, st));
       dst = tb[p & 1].p;
     }
     int rc = contract_impl(leaves[p].p, right, K, rows, ncols, precision, contraction, 0, dst, st, M.circ.n);
@@ -1388,12 +1480,12 @@ void sim_destroy_multi(sim_multi_plan plan) {
 
 void sim_destroy_halves(sim_halves h) {
   if (!h) return;
-  // buffers go back to the pool for reuse in stream order
-  if (h->stream) cudaStreamSynchronize(h->stream);
+  // the buffers go back to the pool after the work enqueued so far on the halves'
+  // stream (stream-ordered: no host wait)
   for (int i = 0; i < 2; ++i) {
-    pool().free(h->leafsel[i]);
-    pool().free(h->d_sel[i]);
-    pool().free(h->out_code[i]);
+    pool().free(h->leafsel[i], h->stream, true);
+    pool().free(h->d_sel[i], h->stream, true);
+    pool().free(h->out_code[i], h->stream, true);
   }
   delete h;
 }

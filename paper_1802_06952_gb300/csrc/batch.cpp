@@ -101,16 +101,20 @@ struct sim_batch_s {
   cudaGraphExec_t exec = nullptr;
   cudaStream_t cap_stream = nullptr;  // the capture runs here; the graph launches on the caller's stream
 
+  cudaStream_t create_stream = nullptr;  // the stream sim_batch_create works on
   cudaError_t alloc(void** p, size_t bytes) {
-    cudaError_t e = rt_alloc(p, bytes > 0 ? bytes : 256);
+    cudaError_t e = rt_alloc(p, bytes > 0 ? bytes : 256, create_stream);
     if (e == cudaSuccess) owned.push_back(*p);
     return e;
   }
   ~sim_batch_s() {
+    // runs may still be in flight on the caller's streams: the blocks go back to the
+    // pool once the device is idle
+    cudaDeviceSynchronize();
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
-    for (void* p : owned) rt_free(p);
+    for (void* p : owned) rt_free(p, nullptr);
     for (Item& it : items) rt_free_plan(it.plan);
   }
 };
@@ -260,13 +264,13 @@ int autotune(sim_batch_s& B, size_t level_budget, cudaStream_t st) {
         tab.insert(tab.end(), it.prog[h].table.begin(), it.prog[h].table.end());
       }
       void* dt = nullptr;
-      BCK(rt_alloc(&dt, sizeof(NodeEntry) * (tab.size() + 1)));
+      BCK(rt_alloc(&dt, sizeof(NodeEntry) * (tab.size() + 1), st));
       cudaError_t e = cudaMemcpyAsync(dt, tab.data(), sizeof(NodeEntry) * tab.size(), cudaMemcpyHostToDevice, st);
       double ms = 0;
       int rc = e == cudaSuccess ? time_ms([&] { return enqueue_sweeps(B, it, (const NodeEntry*)dt, st); }, st, 3, &ms)
                                 : set_error(SIM_ECUDA, cudaGetErrorString(e));
       cudaStreamSynchronize(st);
-      rt_free(dt);
+      rt_free(dt, st);
       BRC(rc);
       if (ms < best_sweep) {
         best_sweep = ms;
@@ -286,11 +290,11 @@ int autotune(sim_batch_s& B, size_t level_budget, cudaStream_t st) {
         tab.insert(tab.end(), it.prog[h].table.begin(), it.prog[h].table.end());
       }
       void* dt = nullptr;
-      BCK(rt_alloc(&dt, sizeof(NodeEntry) * (tab.size() + 1)));
+      BCK(rt_alloc(&dt, sizeof(NodeEntry) * (tab.size() + 1), st));
       cudaError_t e = cudaMemcpyAsync(dt, tab.data(), sizeof(NodeEntry) * tab.size(), cudaMemcpyHostToDevice, st);
       int rc = e == cudaSuccess ? enqueue_sweeps(B, it, (const NodeEntry*)dt, st) : set_error(SIM_ECUDA, "table");
       cudaStreamSynchronize(st);
-      rt_free(dt);
+      rt_free(dt, st);
       BRC(rc);
     }
     double best_gemm = 1e300;
@@ -324,6 +328,7 @@ int sim_batch_create(const sim_circuit_desc* descs, int n_circuits, const uint64
       return set_error(SIM_EINVAL, "a batch contracts with SIM_SPLIT_BF16 or SIM_SPLIT_FP16");
     cudaStream_t st = (cudaStream_t)stream;
     auto B = std::unique_ptr<sim_batch_s>(new sim_batch_s());
+    B->create_stream = st;
     B->contraction = contraction;
     B->use_graph = opts && opts->use_graph;
     B->subset_n = subset_n;

@@ -780,12 +780,7 @@ cudaError_t launch_tc_gemm_pair(const TcGemmArgs& a, cudaStream_t s) {
   k.tm.num_nb = (a.N2 + BN - 1) / BN;
   // 32 pair tiles (8192 rows of A, 16 MB of split operands) per raster group stay in
   // L2 while the group sweeps B, which is then read from DRAM once per group
-  // (SIM_GEMM_GROUP in the environment overrides the default, for comparisons)
-  static const int env_group = [] {
-    const char* e = getenv("SIM_GEMM_GROUP");
-    return e ? atoi(e) : 0;
-  }();
-  k.tm.group = a.group_m > 0 ? a.group_m : (env_group > 0 ? env_group : 32);
+  k.tm.group = a.group_m > 0 ? a.group_m : 32;
   k.num_tiles = k.tm.num_mb * k.tm.num_nb;
   k.scale_a = a.scale_a;
   k.scale_b = a.scale_b;

@@ -55,8 +55,10 @@ int rt_enqueue_tree(const CutPlan& P, int half, const TreeProgram& prog, void* c
 
 // Stream-ordered caching pool of device memory (blocks stay cached until
 // sim_release_cache or an allocation failure).
-cudaError_t rt_alloc(void** p, size_t n);
-void rt_free(void* p);
+// pool blocks for work on stream st; freed blocks return to the pool after the
+// work enqueued so far on st (stream-ordered reuse)
+cudaError_t rt_alloc(void** p, size_t n, cudaStream_t st);
+void rt_free(void* p, cudaStream_t st);
 
 // Device status word (timeouts of bounded device waits) and SM count of the
 // current device.

@@ -177,7 +177,7 @@ __global__ void xeb_kernel(const float2* amps, const uint64_t* idx, uint64_t n, 
     cudaError_t e_ = (x);                                                                       \
     if (e_ != cudaSuccess) {                                                                    \
       cudaGetLastError();                                                                       \
-      for (void* p_ : bufs) rt_free(p_);                                                        \
+      for (void* p_ : bufs) rt_free(p_, st);                                                    \
       return set_error(e_ == cudaErrorMemoryAllocation ? SIM_ENOMEM : SIM_ECUDA,                \
                        std::string(#x) + ": " + cudaGetErrorString(e_));                        \
     }                                                                                           \
@@ -194,7 +194,7 @@ int sim_born_sample(const void* amps_dev, uint64_t count, int n_qubits, uint64_t
   cudaStream_t st = (cudaStream_t)stream;
   std::vector<void*> bufs;
   auto alloc = [&](void** p, size_t n) {
-    cudaError_t e = rt_alloc(p, n);
+    cudaError_t e = rt_alloc(p, n, st);
     if (e == cudaSuccess) bufs.push_back(*p);
     return e;
   };
@@ -257,6 +257,6 @@ int sim_born_sample(const void* amps_dev, uint64_t count, int n_qubits, uint64_t
     xeb_out[2] = pmax * std::ldexp(1.0, n_qubits);
   }
   *n_out = got;
-  for (void* p : bufs) rt_free(p);
+  for (void* p : bufs) rt_free(p, st);
   return SIM_OK;
 }

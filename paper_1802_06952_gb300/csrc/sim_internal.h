@@ -209,6 +209,7 @@ struct CutPlan {
   // device copies of the op tables (uploaded lazily, freed with the plan)
   OpRec* d_ops[2] = {nullptr, nullptr};
   OpRec* d_plain_ops[2] = {nullptr, nullptr};
+  void* ops_stream = nullptr;  // cudaStream_t of the last evolve that used the tables
   std::vector<int> plain_op_offsets[2];  // per layer: first op index (gates then diags)
   std::vector<OpRec> plain_flat[2];       // host copy of the uploaded plain op table
   int device = -1;
