@@ -416,6 +416,60 @@ std::vector<std::vector<OpRec>> form_passes(int k, int low, std::vector<SeqItem>
   return out;
 }
 
+// Number of fused passes a level's sequence forms into.
+int count_passes(int n, int kmax, const std::vector<SeqItem>& items, bool in_order) {
+  if (items.empty()) return 1;
+  const int k = std::min(n, kmax);
+  const int low = k < n ? std::min(5, k - 1) : std::min(5, k);
+  return (int)form_passes(k, low, items, in_order).size();
+}
+
+// Ops of a child level that commute with everything the child must keep are
+// applied once per parent node instead of once per child (the shared prefixes of
+// Section 2.3.2, extended by commutation).  The child keeps its cut slots (the
+// copy-dependent items; all diagonal) and every op that does not commute past what
+// it keeps: a non-diagonal gate on a qubit a kept item touches, or a diagonal term
+// on a qubit a kept non-diagonal gate touches.  Hoisted ops keep their order and
+// follow the parent's own ops.  The move is made only if the passes it costs do not
+// outweigh those it saves, at 2^bits children per parent.
+void hoist_into_parent(int n, int kmax, bool in_order, std::vector<SeqItem>& parent, std::vector<SeqItem>& child,
+                       int bits) {
+  uint32_t kept_diag = 0, kept_gate = 0;  // qubits touched by kept diagonal terms / kept gates
+  std::vector<SeqItem> up, keep;
+  for (const SeqItem& it : child) {
+    if (it.is_gate) {
+      const uint32_t b = 1u << it.gate.q;
+      if ((kept_diag | kept_gate) & b) {
+        keep.push_back(it);
+        kept_gate |= b;
+      } else {
+        up.push_back(it);
+      }
+      continue;
+    }
+    SeqItem u, st;
+    st.cuts = it.cuts;
+    for (int q = 0; q < 32; ++q)
+      if ((it.tmask >> q) & 1u) ((kept_gate >> q) & 1u ? st.tmask : u.tmask) |= 1u << q;
+    for (const auto& pr : it.cz)
+      ((kept_gate >> pr.first) & 1u || (kept_gate >> pr.second) & 1u ? st.cz : u.cz).push_back(pr);
+    kept_diag |= st.tmask;
+    for (const auto& pr : st.cz) kept_diag |= (1u << pr.first) | (1u << pr.second);
+    for (const CutSlot& sl : st.cuts) kept_diag |= 1u << sl.q;
+    if (!u.empty_diag()) up.push_back(u);
+    if (!st.empty_diag()) keep.push_back(st);
+  }
+  if (up.empty()) return;
+  std::vector<SeqItem> parent2 = parent;
+  parent2.insert(parent2.end(), up.begin(), up.end());
+  const int64_t w = (int64_t)1 << std::min(bits, 40);
+  const int64_t before = count_passes(n, kmax, parent, in_order) + w * count_passes(n, kmax, child, in_order);
+  const int64_t after = count_passes(n, kmax, parent2, in_order) + w * count_passes(n, kmax, keep, in_order);
+  if (after > before) return;
+  parent.swap(parent2);
+  child.swap(keep);
+}
+
 // The passes of one copy-tree level: formed as above, then each given its rank
 // order (which staged qubit sits on which lane, warp and register bit).
 void split_passes(int n, int kmax, const std::vector<SeqItem>& items, int first_src, bool in_order,
@@ -702,6 +756,7 @@ void build_half(const Circuit& c, const HalfGateLists& H, int n, const std::vect
 
   const int nlev = (int)branch.size() + 1;
   int bits = 0;
+  std::vector<std::vector<SeqItem>> seqs;
   for (int j = 0; j < nlev; ++j) {
     Level L;
     L.branch_layer = j == 0 ? -1 : branch[j - 1];
@@ -743,9 +798,15 @@ void build_half(const Circuit& c, const HalfGateLists& H, int n, const std::vect
       SeqItem d = diag_item(H.tmask[t], H.cz[t], next_branch ? std::vector<CutSlot>() : H.cuts[t]);
       if (!d.empty_diag()) seq.push_back(d);
     }
-    int first_src = j == 0 ? (uniform ? SRC_UNIFORM : SRC_ZERO) : SRC_PARENT;
-    split_passes(n, fuse, seq, first_src, in_order, L.passes, S.ops);
     S.levels.push_back(L);
+    seqs.push_back(std::move(seq));
+  }
+  // copy-independent ops move up the tree where that saves work (bottom-up, so
+  // that an op can climb several levels)
+  for (int j = nlev - 1; j >= 1; --j) hoist_into_parent(n, fuse, in_order, seqs[j - 1], seqs[j], branch_bits[j - 1]);
+  for (int j = 0; j < nlev; ++j) {
+    const int first_src = j == 0 ? (uniform ? SRC_UNIFORM : SRC_ZERO) : SRC_PARENT;
+    split_passes(n, fuse, seqs[j], first_src, in_order, S.levels[j].passes, S.ops);
   }
 
   // plain complex128 path: per layer, one op per non-diagonal gate, then the

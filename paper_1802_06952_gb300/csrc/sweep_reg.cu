@@ -213,21 +213,13 @@ __device__ __forceinline__ uint32_t swz_thread(const RegArgs& a, uint32_t t) {
   return z;
 }
 
-template <int R>
-__global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArgs a) {
-  constexpr int NE = 1 << R;
-  extern __shared__ float2 xs[];  // 2^k slots (transposes, warp-rank gates), then the ops
-  __shared__ float2 s_omega[8];   // w^e, w = e^{i pi / 4}
-  const int t = threadIdx.x;
-  const int lane = t & 31;
-  // the pass's ops, read by every thread: one copy in shared memory per block
-  OpRec* s_ops = (OpRec*)((char*)xs + a.xs_bytes);
-  {
-    static_assert(sizeof(OpRec) % 8 == 0, "ops are copied in 8-byte words");
-    const int nw = a.op_count * (int)(sizeof(OpRec) / 8);
-    const uint2* g = (const uint2*)a.ops;
-    for (int i = t; i < nw; i += 256) ((uint2*)s_ops)[i] = __ldg(g + i);
-  }
+// Per block: the pass's ops (read by every thread) copied to shared memory, and
+// the table of w^e.
+__device__ __forceinline__ void block_setup(const RegArgs& a, OpRec* s_ops, float2* s_omega, int t) {
+  static_assert(sizeof(OpRec) % 8 == 0, "ops are copied in 8-byte words");
+  const int nw = a.op_count * (int)(sizeof(OpRec) / 8);
+  const uint2* g = (const uint2*)a.ops;
+  for (int i = t; i < nw; i += (int)blockDim.x) ((uint2*)s_ops)[i] = __ldg(g + i);
   if (t < 8) {
     // w^t: (+-1, 0), (0, +-1) for even t; (+-1/sqrt2, +-1/sqrt2) for odd t
     const int quad = t >> 1;
@@ -241,6 +233,208 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
     }
     s_omega[t] = make_float2(re, im);
   }
+}
+
+// The pass's ops on one block of 2^k amplitudes held in compute order: thread t
+// keeps elements j of v; base holds the block's non-local index bits and node_id
+// the copy-tree node (its cut-slot values).
+template <int R>
+__device__ __forceinline__ void run_ops(const RegArgs& a, float2 (&v)[1 << R], float2* xs, const OpRec* s_ops,
+                                        const float2* s_omega, int t, uint32_t base, uint64_t node_id) {
+  constexpr int NE = 1 << R;
+  const int lane = t & 31;
+  // compute-order global index bits for the diagonal ops
+  uint32_t xt = base;
+#pragma unroll
+  for (int r = 0; r < 8; ++r)
+    if ((t >> r) & 1) xt |= 1u << a.cpos[r];
+  for (int o = 0; o < a.op_count; ++o) {
+    const OpRec* op = s_ops + o;
+    if (op->type == OP_SWAP) {
+      // exchange warp ranks 5+m with register ranks 10+m (m < NSW): the element at
+      // (t, j) afterwards is the one at t with warp bits from j's bits 2.., and j
+      // with those bits from t's warp bits (reads conflict-free: for fixed j a
+      // warp reads 32 consecutive slots)
+      constexpr int NSW = R >= 5 ? 3 : 0;  // the planner exchanges only at k = 13
+      if constexpr (NSW > 0) {
+        constexpr int MS = (1 << NSW) - 1;
+#pragma unroll
+        for (int j = 0; j < NE; ++j) xs[j * 256 + t] = v[j];
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NE; ++j) {
+          const int old_t = (t & ~(MS << 5)) | (((j >> 2) & MS) << 5);
+          const int old_j = (j & ~(MS << 2)) | (((t >> 5) & MS) << 2);
+          v[j] = xs[old_j * 256 + old_t];
+        }
+        __syncthreads();
+        xt = base;
+#pragma unroll
+        for (int r = 0; r < 8; ++r)
+          if ((t >> r) & 1) xt |= 1u << op->tq[r];
+      }
+      continue;
+    }
+    if (op->type == OP_GATE) {
+      const int lq = op->lq;
+      const int kind = op->kind;
+      if (lq >= 8) {
+        reg_gate<R>(v, lq - 8, kind);
+      } else if (lq < 5) {
+        const float sg = ((lane >> lq) & 1) ? 1.f : -1.f;
+        const int mask = 1 << lq;
+        if (kind == 1)
+          lane_gate_k<R, 1>(v, mask, sg);
+        else if (kind == 2)
+          lane_gate_k<R, 2>(v, mask, sg);
+        else
+          lane_gate_k<R, 3>(v, mask, sg);
+      } else {
+        const float sg = ((t >> lq) & 1) ? 1.f : -1.f;
+        const int pt = t ^ (1 << lq);
+        if (kind == 1)
+          smem_gate_k<R, 1>(v, xs, t, pt, sg);
+        else if (kind == 2)
+          smem_gate_k<R, 2>(v, xs, t, pt, sg);
+        else
+          smem_gate_k<R, 3>(v, xs, t, pt, sg);
+      }
+    } else {
+      // exponent of w at x = xt | r(j): the thread part (T and CZ terms within xt)
+      // once per op, the register part from the op's table, and the CZ pairs between
+      // a register qubit and a thread or non-local qubit as 4 popc(j & B)
+      const uint32_t tmask = op->tmask;
+      const int nsh = op->nsh;
+      int s2 = 0;
+#pragma unroll 1
+      for (int s = 0; s < nsh; ++s) s2 += __popc(xt & (xt >> op->sh_d[s]) & op->sh_m[s]);
+      int et = __popc(xt & tmask) + 4 * s2 + (o == a.phase_op ? a.phase_e : 0);
+      uint32_t B = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const uint32_t pq = op->pq[r];
+        if (pq != 0xFFu && ((xt >> pq) & 1u)) B |= 1u << r;
+      }
+      // cut slots of this copy-tree node: Z^l signs and P_l projectors, split the
+      // same way
+      bool proj = false, keep_t = true;
+      uint32_t pm_r = 0, pv_r = 0;
+      uint32_t wreg = 0;  // weights 1 and 2 of phase slots on register ranks, 2 bits per rank
+      if (op->ncut) {
+        Diag d;
+        load_diag(op, node_id, d);
+        et += 4 * __popc(xt & d.zmask) + __popc(xt & d.w1mask) + 2 * __popc(xt & d.w2mask);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t qb = 1u << op->rq[r];
+          if (d.zmask & qb) B ^= 1u << r;
+          if (d.w1mask & qb) wreg |= 1u << (2 * r);
+          if (d.w2mask & qb) wreg |= 2u << (2 * r);
+          if (d.pmask & qb) {
+            pm_r |= 1u << r;
+            if (d.pval & qb) pv_r |= 1u << r;
+          }
+        }
+        if (d.pmask) {
+          proj = true;
+          keep_t = (xt & d.pmask & ~op->regmask) == (d.pval & ~op->regmask);
+        }
+      }
+      // Exponents of 8 elements at a time, one 4-bit field per element (element
+      // 8w + i in field i of word w): the register-part table plus et in every
+      // field (each field stays below 15, so no carries), then the cross-CZ sign
+      // 4 popc(B & j) mod 8 as an XOR of 4 into the fields with odd parity of
+      // B & j.  kPar[r]: the fields i (of 0..7) whose bit r is set.
+      constexpr uint32_t kPar[3] = {0x40404040u, 0x44004400u, 0x44440000u};
+      uint32_t par0 = 0;
+#pragma unroll
+      for (int r = 0; r < 3 && r < R; ++r)
+        if ((B >> r) & 1u) par0 ^= kPar[r];
+      const uint32_t et8 = (uint32_t)(et & 7) * 0x11111111u;
+      uint32_t ew[4];
+#pragma unroll
+      for (int w4 = 0; w4 < 4; ++w4) {
+        if (w4 * 8 < NE) {
+          const uint32_t hi = (uint32_t)__popc(B & (uint32_t)(w4 << 3)) & 1u;
+          ew[w4] = (op->ereg[w4] + et8) ^ par0 ^ (hi ? 0x44444444u : 0u);
+        } else {
+          ew[w4] = 0u;
+        }
+      }
+      if (wreg) {
+        // weights 1..3 of phase slots on register rank r: + w_r in the fields of the
+        // elements j with bit r set.  Each add follows a reduction of every field to
+        // its value mod 8 (fields stay below 16, no carries between fields).
+        constexpr uint32_t kAdd[3] = {0x10101010u, 0x11001100u, 0x11110000u};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const uint32_t wr = (wreg >> (2 * r)) & 3u;
+          if (!wr) continue;
+#pragma unroll
+          for (int w4 = 0; w4 < 4; ++w4) {
+            if (w4 * 8 >= NE) continue;
+            const uint32_t pat = r < 3 ? kAdd[r] : (((w4 >> (r - 3)) & 1) ? 0x11111111u : 0u);
+            ew[w4] = (ew[w4] & 0x77777777u) + wr * pat;
+          }
+        }
+      }
+      // projector: the elements j with (j & pm_r) == pv_r, as a bit mask over j
+      uint32_t kmask = 0xFFFFFFFFu;
+      if (proj) {
+        constexpr uint32_t kJ[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
+#pragma unroll
+        for (int r = 0; r < R; ++r)
+          if ((pm_r >> r) & 1u) kmask &= ((pv_r >> r) & 1u) ? kJ[r] : ~kJ[r];
+        if (!keep_t) kmask = 0u;
+      }
+      // field i of a word, as the byte offset 8 e of w^e in s_omega
+      auto omega_at = [&](int j) {
+        const uint32_t w = ew[j >> 3];
+        const int i = j & 7;
+        const uint32_t off = (i == 0 ? (w << 3) : (w >> (4 * i - 3))) & 0x38u;
+        return *(const float2*)((const char*)s_omega + off);
+      };
+      if (op->sign_only) {
+        // every exponent is 0 or 4 mod 8: flip the sign where bit 2 of the field is
+        // set (field i of a word at bits 4i .. 4i+3, so bit 2 moves up by 29 - 4i)
+        auto flip = [&](int j) {
+          const uint32_t sm = (ew[j >> 3] << (29 - 4 * (j & 7))) & 0x80000000u;
+          v[j] = make_float2(__uint_as_float(__float_as_uint(v[j].x) ^ sm),
+                             __uint_as_float(__float_as_uint(v[j].y) ^ sm));
+        };
+        if (proj) {
+#pragma unroll
+          for (int j = 0; j < NE; ++j) {
+            flip(j);
+            if (!((kmask >> j) & 1u)) v[j] = make_float2(0.f, 0.f);
+          }
+        } else {
+#pragma unroll
+          for (int j = 0; j < NE; ++j) flip(j);
+        }
+      } else if (proj) {
+#pragma unroll
+        for (int j = 0; j < NE; ++j) {
+          v[j] = cmul(v[j], omega_at(j));
+          if (!((kmask >> j) & 1u)) v[j] = make_float2(0.f, 0.f);
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < NE; ++j) v[j] = cmul(v[j], omega_at(j));
+      }
+    }
+  }
+}
+
+template <int R>
+__global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArgs a) {
+  constexpr int NE = 1 << R;
+  extern __shared__ float2 xs[];  // 2^k slots (transposes, warp-rank gates), then the ops
+  __shared__ float2 s_omega[8];   // w^e, w = e^{i pi / 4}
+  const int t = threadIdx.x;
+  // the pass's ops, read by every thread: one copy in shared memory per block
+  OpRec* s_ops = (OpRec*)((char*)xs + a.xs_bytes);
+  block_setup(a, s_ops, s_omega, t);
   const uint32_t nb_log = (uint32_t)(a.n - a.k);
   const uint64_t bid = blockIdx.x;
   const int64_t slot = a.slot_begin + (int64_t)(bid >> nb_log);
@@ -346,187 +540,7 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
   __syncthreads();  // s_omega, s_ops
   if constexpr (R < 2)
     if (a.transpose) transpose(true);
-  // compute-order global index bits for the diagonal ops
-  uint32_t xt = base;
-#pragma unroll
-  for (int r = 0; r < 8; ++r)
-    if ((t >> r) & 1) xt |= 1u << a.cpos[r];
-  for (int o = 0; o < a.op_count; ++o) {
-    const OpRec* op = s_ops + o;
-    if (op->type == OP_SWAP) {
-      // exchange warp ranks 5+m with register ranks 10+m (m < NSW): the element at
-      // (t, j) afterwards is the one at t with warp bits from j's bits 2.., and j
-      // with those bits from t's warp bits (reads conflict-free: for fixed j a
-      // warp reads 32 consecutive slots)
-      constexpr int NSW = R >= 5 ? 3 : 0;  // the planner exchanges only at k = 13
-      if constexpr (NSW > 0) {
-        constexpr int MS = (1 << NSW) - 1;
-#pragma unroll
-        for (int j = 0; j < NE; ++j) xs[j * 256 + t] = v[j];
-        __syncthreads();
-#pragma unroll
-        for (int j = 0; j < NE; ++j) {
-          const int old_t = (t & ~(MS << 5)) | (((j >> 2) & MS) << 5);
-          const int old_j = (j & ~(MS << 2)) | (((t >> 5) & MS) << 2);
-          v[j] = xs[old_j * 256 + old_t];
-        }
-        __syncthreads();
-        xt = base;
-#pragma unroll
-        for (int r = 0; r < 8; ++r)
-          if ((t >> r) & 1) xt |= 1u << op->tq[r];
-      }
-      continue;
-    }
-    if (op->type == OP_GATE) {
-      const int lq = op->lq;
-      const int kind = op->kind;
-      if (lq >= 8) {
-        reg_gate<R>(v, lq - 8, kind);
-      } else if (lq < 5) {
-        const float sg = ((lane >> lq) & 1) ? 1.f : -1.f;
-        const int mask = 1 << lq;
-        if (kind == 1)
-          lane_gate_k<R, 1>(v, mask, sg);
-        else if (kind == 2)
-          lane_gate_k<R, 2>(v, mask, sg);
-        else
-          lane_gate_k<R, 3>(v, mask, sg);
-      } else {
-        const float sg = ((t >> lq) & 1) ? 1.f : -1.f;
-        const int pt = t ^ (1 << lq);
-        if (kind == 1)
-          smem_gate_k<R, 1>(v, xs, t, pt, sg);
-        else if (kind == 2)
-          smem_gate_k<R, 2>(v, xs, t, pt, sg);
-        else
-          smem_gate_k<R, 3>(v, xs, t, pt, sg);
-      }
-    } else {
-      // exponent of w at x = xt | r(j): the thread part (T and CZ terms within xt)
-      // once per op, the register part from the op's table, and the CZ pairs between
-      // a register qubit and a thread or non-local qubit as 4 popc(j & B)
-      const uint32_t tmask = op->tmask;
-      const int nsh = op->nsh;
-      int s2 = 0;
-#pragma unroll 1
-      for (int s = 0; s < nsh; ++s) s2 += __popc(xt & (xt >> op->sh_d[s]) & op->sh_m[s]);
-      int et = __popc(xt & tmask) + 4 * s2 + (o == a.phase_op ? a.phase_e : 0);
-      uint32_t B = 0;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const uint32_t pq = op->pq[r];
-        if (pq != 0xFFu && ((xt >> pq) & 1u)) B |= 1u << r;
-      }
-      // cut slots of this copy-tree node: Z^l signs and P_l projectors, split the
-      // same way
-      bool proj = false, keep_t = true;
-      uint32_t pm_r = 0, pv_r = 0;
-      uint32_t wreg = 0;  // weights 1 and 2 of phase slots on register ranks, 2 bits per rank
-      if (op->ncut) {
-        Diag d;
-        load_diag(op, ne.node_id, d);
-        et += 4 * __popc(xt & d.zmask) + __popc(xt & d.w1mask) + 2 * __popc(xt & d.w2mask);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const uint32_t qb = 1u << op->rq[r];
-          if (d.zmask & qb) B ^= 1u << r;
-          if (d.w1mask & qb) wreg |= 1u << (2 * r);
-          if (d.w2mask & qb) wreg |= 2u << (2 * r);
-          if (d.pmask & qb) {
-            pm_r |= 1u << r;
-            if (d.pval & qb) pv_r |= 1u << r;
-          }
-        }
-        if (d.pmask) {
-          proj = true;
-          keep_t = (xt & d.pmask & ~op->regmask) == (d.pval & ~op->regmask);
-        }
-      }
-      // Exponents of 8 elements at a time, one 4-bit field per element (element
-      // 8w + i in field i of word w): the register-part table plus et in every
-      // field (each field stays below 15, so no carries), then the cross-CZ sign
-      // 4 popc(B & j) mod 8 as an XOR of 4 into the fields with odd parity of
-      // B & j.  kPar[r]: the fields i (of 0..7) whose bit r is set.
-      constexpr uint32_t kPar[3] = {0x40404040u, 0x44004400u, 0x44440000u};
-      uint32_t par0 = 0;
-#pragma unroll
-      for (int r = 0; r < 3 && r < R; ++r)
-        if ((B >> r) & 1u) par0 ^= kPar[r];
-      const uint32_t et8 = (uint32_t)(et & 7) * 0x11111111u;
-      uint32_t ew[4];
-#pragma unroll
-      for (int w4 = 0; w4 < 4; ++w4) {
-        if (w4 * 8 < NE) {
-          const uint32_t hi = (uint32_t)__popc(B & (uint32_t)(w4 << 3)) & 1u;
-          ew[w4] = (op->ereg[w4] + et8) ^ par0 ^ (hi ? 0x44444444u : 0u);
-        } else {
-          ew[w4] = 0u;
-        }
-      }
-      if (wreg) {
-        // weights 1..3 of phase slots on register rank r: + w_r in the fields of the
-        // elements j with bit r set.  Each add follows a reduction of every field to
-        // its value mod 8 (fields stay below 16, no carries between fields).
-        constexpr uint32_t kAdd[3] = {0x10101010u, 0x11001100u, 0x11110000u};
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const uint32_t wr = (wreg >> (2 * r)) & 3u;
-          if (!wr) continue;
-#pragma unroll
-          for (int w4 = 0; w4 < 4; ++w4) {
-            if (w4 * 8 >= NE) continue;
-            const uint32_t pat = r < 3 ? kAdd[r] : (((w4 >> (r - 3)) & 1) ? 0x11111111u : 0u);
-            ew[w4] = (ew[w4] & 0x77777777u) + wr * pat;
-          }
-        }
-      }
-      // projector: the elements j with (j & pm_r) == pv_r, as a bit mask over j
-      uint32_t kmask = 0xFFFFFFFFu;
-      if (proj) {
-        constexpr uint32_t kJ[5] = {0xAAAAAAAAu, 0xCCCCCCCCu, 0xF0F0F0F0u, 0xFF00FF00u, 0xFFFF0000u};
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-          if ((pm_r >> r) & 1u) kmask &= ((pv_r >> r) & 1u) ? kJ[r] : ~kJ[r];
-        if (!keep_t) kmask = 0u;
-      }
-      // field i of a word, as the byte offset 8 e of w^e in s_omega
-      auto omega_at = [&](int j) {
-        const uint32_t w = ew[j >> 3];
-        const int i = j & 7;
-        const uint32_t off = (i == 0 ? (w << 3) : (w >> (4 * i - 3))) & 0x38u;
-        return *(const float2*)((const char*)s_omega + off);
-      };
-      if (op->sign_only) {
-        // every exponent is 0 or 4 mod 8: flip the sign where bit 2 of the field is
-        // set (field i of a word at bits 4i .. 4i+3, so bit 2 moves up by 29 - 4i)
-        auto flip = [&](int j) {
-          const uint32_t sm = (ew[j >> 3] << (29 - 4 * (j & 7))) & 0x80000000u;
-          v[j] = make_float2(__uint_as_float(__float_as_uint(v[j].x) ^ sm),
-                             __uint_as_float(__float_as_uint(v[j].y) ^ sm));
-        };
-        if (proj) {
-#pragma unroll
-          for (int j = 0; j < NE; ++j) {
-            flip(j);
-            if (!((kmask >> j) & 1u)) v[j] = make_float2(0.f, 0.f);
-          }
-        } else {
-#pragma unroll
-          for (int j = 0; j < NE; ++j) flip(j);
-        }
-      } else if (proj) {
-#pragma unroll
-        for (int j = 0; j < NE; ++j) {
-          v[j] = cmul(v[j], omega_at(j));
-          if (!((kmask >> j) & 1u)) v[j] = make_float2(0.f, 0.f);
-        }
-      } else {
-#pragma unroll
-        for (int j = 0; j < NE; ++j) v[j] = cmul(v[j], omega_at(j));
-      }
-    }
-  }
+  run_ops<R>(a, v, xs, s_ops, s_omega, t, base, ne.node_id);
   if constexpr (R < 2)
     if (a.transpose) transpose(false);
   if (a.phase_op < 0 && a.phase_e != 0) {
@@ -545,6 +559,7 @@ __global__ void __launch_bounds__(256, (R >= 5 ? 2 : 3)) sweep_reg_kernel(RegArg
     for (int j = 0; j < NE; ++j) dst[st | sreg(j)] = __fmul2_rn(v[j], sc2);
   }
 }
+
 
 template <int R>
 cudaError_t launch_r(const RegArgs& a, int64_t nslots, int use_smem, cudaStream_t s) {
@@ -633,6 +648,7 @@ cudaError_t launch_sweep2_c64(const SweepLaunch& L, cudaStream_t s) {
   a.transpose = L.transpose;
   a.vec4 = L.vec4;
   const int use_smem = L.warp_gates > 0 || L.transpose;
+  // passes that read a state (not the first pass of a root) at k = 13 run persistent
   switch (L.k - 8) {
     case 0: return launch_r<0>(a, L.nslots, use_smem, s);
     case 1: return launch_r<1>(a, L.nslots, use_smem, s);

@@ -158,6 +158,27 @@ def test_plan_levels_cover_the_copy_bits(R, C, d, b):
         sim.sim_destroy_circuit(circ)
 
 
+
+@pytest.mark.parametrize("R,C,d,b,leaf_passes", [(6, 7, 22, 3, 1), (8, 8, 22, 4, 1)])
+def test_copy_independent_ops_climb_the_tree(R, C, d, b, leaf_passes):
+    """The cut slots are a level's only copy-dependent items and they are diagonal,
+    so the ops that commute past them run in the parent level (Sec. 2.3.2's shared
+    prefixes extended by commutation).  On the 42- and 64-qubit circuits the leaf
+    level (2^c nodes per half) keeps one fused pass, and the work weighted by node
+    count stays below the plain layer-by-layer tree's."""
+    circ = sim.sim_build_circuit(R, C, d, 0, b)
+    plan, c, copies, nu, nl = sim.sim_cut(circ, b)
+    try:
+        for half in (0, 1):
+            lv = sim.sim_plan_levels(plan, half)
+            assert lv[-1, 3] == leaf_passes
+            # node-passes of the full tree: passes x 2^(copy bits fixed by the level)
+            weighted = int(sum(int(p) << int(bits) for bits, p in zip(lv[:, 2], lv[:, 3])))
+            assert weighted <= (leaf_passes + 1) << c
+    finally:
+        sim.sim_destroy_cut(plan)
+        sim.sim_destroy_circuit(circ)
+
 @pytest.mark.parametrize("name", ["CX", "CT", "CY2"])
 def test_controlled_gate_cuts_on_the_host(name):
     """Controlled X, T and Y^1/2 gates across the cut count as cuts (P_l on the
