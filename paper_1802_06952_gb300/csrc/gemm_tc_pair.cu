@@ -54,11 +54,12 @@ constexpr int STAGE_BYTES = 2 * (A_BYTES + B_BYTES);  // hi and lo tiles of both
 constexpr int ACC_COLS = BN;
 constexpr int TMEM_COLS = 2 * ACC_COLS;
 constexpr int HIST_BYTES = SIM_KS_BINS * 4;
-// Shared memory of one CTA: STG operand stages, two output staging buffers of 32 rows
-// x SW floats per epilogue warp, barriers, histogram.
-template <int STG, int SW, int NBUF, int EW>
+// Shared memory of one CTA: STG operand stages, NBUF output staging buffers of 32 rows
+// x SW floats per epilogue warp (none for direct epilogues), barriers, histogram.
+template <int STG, int SW, int NBUF, int EW, bool DIRECT = false>
 struct PairSmem {
-  static constexpr int EPI_BYTES = EW * NBUF * 32 * SW * 4;
+  // direct epilogues store from registers: no staging buffers
+  static constexpr int EPI_BYTES = DIRECT ? 0 : EW * NBUF * 32 * SW * 4;
   static constexpr int BYTES = 1024 + STG * STAGE_BYTES + EPI_BYTES + 512 + HIST_BYTES;
   static_assert(BYTES <= 232448, "shared memory above the 227 KB per-block limit");
 };
@@ -295,7 +296,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(32 * (2 + EW), 1)
     tc_gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA_hi, const __grid_constant__ CUtensorMap mapA_lo,
                         const __grid_constant__ CUtensorMap mapB_hi, const __grid_constant__ CUtensorMap mapB_lo,
                         const __grid_constant__ CUtensorMap mapC, PairArgs args, uint32_t idesc) {
-  using L = PairSmem<STG, SW, NBUF, EW>;
+  using L = PairSmem<STG, SW, NBUF, EW, DIRECT>;
   constexpr int THREADS = 32 * (2 + EW);
   constexpr int COLS = BN / (EW / 4);  // accumulator columns per epilogue warp
   extern __shared__ uint8_t smem_raw[];
@@ -699,7 +700,7 @@ bool make_output_map(CUtensorMap* map, float* C, int64_t M, int64_t N2, int sw) 
 template <bool STATS, bool SIGN, int STG, int SW, int NBUF, int UNR, int EW, bool DIRECT>
 cudaError_t launch_variant(const CUtensorMap (&maps)[4], const CUtensorMap& mapC, const PairArgs& k, uint32_t idesc,
                            int num_sms, cudaStream_t s) {
-  constexpr int SMEM = PairSmem<STG, SW, NBUF, EW>::BYTES;
+  constexpr int SMEM = PairSmem<STG, SW, NBUF, EW, DIRECT>::BYTES;
   constexpr int THREADS = 32 * (2 + EW);
   static DeviceOnce setup;
   int max_pairs = 0;
@@ -800,8 +801,7 @@ cudaError_t launch_tc_gemm_pair(const TcGemmArgs& a, cudaStream_t s) {
   const bool sign = k.out_lcode != nullptr;
   // Epilogue shape by the length of a tile's main loop: with few k-blocks per tile
   // (K <= 128 copies) the epilogue is the bound and 16 epilogue warps hide its
-  // latency (2 operand stages of 64 KB, 181,760 bytes of shared memory); otherwise 3
-  // stages and 8 epilogue warps (230,912 bytes).
+  // latency (2 operand stages of 64 KB); longer main loops are set below.
   // Direct epilogue stores (each lane writes full 32-byte sectors of its row from
   // registers, no shared-memory staging) when the contraction writes each output
   // once: one copy chunk and no accumulation, 32-byte aligned rows.  Measured on the
@@ -823,7 +823,14 @@ cudaError_t launch_tc_gemm_pair(const TcGemmArgs& a, cudaStream_t s) {
          : (sign ? launch_variant<false, true, G, 16, 1, 2, E, D>(maps, mapC, k, idesc, nsm, s)            \
                  : launch_variant<false, false, G, 16, 1, 2, E, D>(maps, mapC, k, idesc, nsm, s)))
 #define LV(G, E) (direct ? LV2(G, E, true) : LV2(G, E, false))
-  cudaError_t e = k.nkb <= 4 ? LV(2, 16) : LV(3, 8);
+  // Longer main loops: 3 stages; 8 epilogue warps, or 16 when the statistics are
+  // fused into a direct epilogue (no staging buffers, 214,528 bytes of shared
+  // memory).  2^30 amplitudes, K = 256: with statistics 3.25 ms on 16 warps against
+  // 3.74 ms on 8; without them 3.02 ms on 8 against 3.26 ms on 16 (the extra warps
+  // take issue slots from the producer and MMA warps).
+  cudaError_t e = k.nkb <= 4             ? LV(2, 16)
+                  : (direct && stats) ? LV2(3, 16, true)
+                                      : LV(3, 8);
 #undef LV
 #undef LV2
   note_launches(SIM_PHASE_CONTRACT, 1);
