@@ -72,6 +72,8 @@ def parse():
                     help="replicas: one circuit per rank per step (weak scaling, no data-path collective); "
                          "copies: one circuit per step, its copies dealt out to the ranks as subtrees of the "
                          "copy tree, partial blocks summed by one all-reduce (strong scaling)")
+    ap.add_argument("--streams", type=int, default=2, choices=[1, 2],
+                    help="host threads and CUDA streams the timed steps alternate between")
     ap.add_argument("--select", type=int, default=0,
                     help="profiling case: contract only the first S upper x S lower indices (S*S amplitudes)")
     return ap.parse_args()
@@ -665,23 +667,31 @@ def run_ours(args):
         my_copies = sdist.rank_list(8, world, rank)
 
     # Host work of a step (rows a1-a3: build the circuit, cut it, plan the passes)
-    # for step i + 1 runs on a helper thread while step i's kernels run: the library
-    # releases the interpreter lock inside every call, and these calls touch no
-    # device state.  Every step still does all of its work.
+    # for a later step runs on a helper thread while this step's kernels run: the
+    # library releases the interpreter lock inside every call, and these calls touch
+    # no device state.  Every step still does all of its work.
     from concurrent.futures import ThreadPoolExecutor
-    prep_pool = ThreadPoolExecutor(max_workers=1)
+    prep_pool = ThreadPoolExecutor(max_workers=2)
     pending = {}
+    pending_mu = threading.Lock()
+    # The timed steps alternate between two host threads, each with its own CUDA
+    # stream and output block, so that one step's host work (the statistics'
+    # read-back, the next circuit's evolve set-up) overlaps the other's kernels.
+    nstreams = 1 if (shard or args.streams < 2) else 2
+    streams = [stream] + [torch.cuda.Stream() for _ in range(nstreams - 1)]
+    outs = [out] + [torch.empty_like(out) for _ in range(nstreams - 1)]
 
     def prepare(i):
         circ = sim.sim_build_circuit(R, C, DEPTH, step_seed(i), CUT_ROW)
         plan, c, copies, nu, nl = sim.sim_cut(circ, CUT_ROW)
         return circ, plan, copies
 
-    def step(i, target, split=sim.SIM_SPLIT_FP16):
-        fut = pending.pop(i, None)
+    def step(i, target, split=sim.SIM_SPLIT_FP16, stream=stream, ahead=1):
+        with pending_mu:
+            fut = pending.pop(i, None)
+            if i + ahead not in pending:
+                pending[i + ahead] = prep_pool.submit(prepare, i + ahead)
         circ, plan, copies = fut.result() if fut is not None else prepare(i)
-        if i + 1 not in pending:
-            pending[i + 1] = prep_pool.submit(prepare, i + 1)
         st = None
         if shard:
             # this rank's copies -> partial block on the device; one all-reduce sums the
@@ -749,13 +759,43 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     per = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     e0.record(stream)
-    stats = []
-    for i in range(args.steps):
-        per[i][0].record(stream)
-        stats.append(step(args.warmup + i, out))
-        per[i][1].record(stream)
+    stats = [None] * args.steps
+    if nstreams == 1:
+        for i in range(args.steps):
+            per[i][0].record(stream)
+            stats[i] = step(args.warmup + i, out)
+            per[i][1].record(stream)
+    else:
+        for sx in streams[1:]:
+            sx.wait_event(e0)
+        errs = []
+
+        def worker(p):
+            try:
+                torch.cuda.set_device(local)
+                for i in range(p, args.steps, nstreams):
+                    per[i][0].record(streams[p])
+                    stats[i] = step(args.warmup + i, outs[p], stream=streams[p], ahead=nstreams)
+                    per[i][1].record(streams[p])
+            except Exception as ex:  # re-raised below
+                errs.append(ex)
+
+        threads = [threading.Thread(target=worker, args=(p,)) for p in range(nstreams)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errs:
+            raise errs[0]
+        for sx in streams[1:]:
+            ej = torch.cuda.Event()
+            ej.record(sx)
+            stream.wait_event(ej)
     e1.record(stream)
     torch.cuda.synchronize()
+    # the last timed circuit's amplitudes (read by the legs below)
+    out = outs[(args.steps - 1) % nstreams]
+    del outs
     barrier()
     sim.sim_profile_enable(False)
     prof = sim.sim_profile_read(reset=True)
@@ -800,7 +840,11 @@ def run_ours(args):
                                    "all-reduce of the amplitude block per step" % world) if shard else
                                   ("one circuit per step per GPU (weak)" if world > 1 else "1 GPU"),
                    "l2": "each step writes 8.6 GB of amplitudes (> 129 MB L2); no data carried across steps",
-                   "step_ms_median": statistics.median(step_ms)},
+                   "host_threads": nstreams,
+                   "streams_note": ("the timed steps alternate between %d host threads, each with its own CUDA "
+                                    "stream and output block; every step does all of its work" % nstreams),
+                   # (with two streams a step's events also span the other stream's kernels)
+                   "step_ms_median": statistics.median(step_ms) if nstreams == 1 else None},
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": bf16, "unit": "TFLOP/s",
                      "frac": achieved / bf16, "traffic": traffic,
                      "kernel": ("tc_gemm_pair_kernel (split-fp16 contraction, CTA pairs)" if pair
@@ -816,6 +860,9 @@ def run_ours(args):
                      "issued_def": "24*M*N*K: the three split products (hi*hi, hi*lo, lo*hi) each issue the 8*M*N*K",
                      "launch_ms": gemm_ms},
         "phases": phases,
+        "phases_note": ("CUDA-event pairs on each step's stream" + (
+            "; with two streams a phase's pair also spans waits for the other stream's kernels (the "
+            "sweeps wait for the other step's contraction to free the SMs)" if nstreams > 1 else "")),
         "sweep": {"ms_per_step": sweep_ms, "note": "15-qubit halves are L2-resident; HBM fraction not meaningful here"},
         "gpu_launches": int(sum(launches)),
         "clocks": clocks,
