@@ -248,6 +248,45 @@ def test_host_output_buffer():
         r.close()
 
 
+def test_host_output_written_in_place_and_staged():
+    """Host output (pinned or pageable, overwritten or accumulated, full or ragged
+    selections) goes through the device staging copy and gives the device route's
+    bits."""
+    R, C, d, seed, b = 4, 5, 16, 3, 2
+    gates, plan = oc.grid_cut(R, C, d, seed, b)
+    full = oracle.statevector(R * C, gates).reshape(1 << plan.n_l, 1 << plan.n_u)
+    r = Run(R, C, d, seed, b)
+    try:
+        h = r.evolve(sim.SIM_C64)
+        shape = (1 << r.nl, 1 << r.nu)
+        dev = torch.zeros(shape, dtype=torch.complex64, device="cuda")
+        sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, False, dev)
+        sim.sim_status()
+        want = dev.cpu().numpy()
+        assert rel_err(want, full) <= TOL_SPLIT
+        pinned = torch.zeros(shape, dtype=torch.complex64).pin_memory()
+        sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, False, pinned)
+        assert np.array_equal(pinned.numpy(), want)
+        # accumulate: the block is read back from the host first
+        sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, True, pinned)
+        assert rel_err(pinned.numpy(), 2 * full) <= TOL_SPLIT
+        pageable = torch.zeros(shape, dtype=torch.complex64)
+        sim.sim_amplitudes(h, sim.SIM_SPLIT_FP16, False, pageable)
+        assert np.array_equal(pageable.numpy(), want)
+        # ragged selection (n_u not a multiple of 4)
+        su = np.sort(np.random.default_rng(5).choice(1 << r.nu, 301, replace=False)).astype(np.uint64)
+        sl = np.arange(0, 1 << r.nl, 3, dtype=np.uint64)
+        hs = r.evolve(sim.SIM_C64, sel_u=su, sel_l=sl)
+        dsel = torch.zeros((sl.size, su.size), dtype=torch.complex64, device="cuda")
+        sim.sim_amplitudes(hs, sim.SIM_SPLIT_FP16, False, dsel)
+        psel = torch.zeros((sl.size, su.size), dtype=torch.complex64).pin_memory()
+        sim.sim_amplitudes(hs, sim.SIM_SPLIT_FP16, False, psel)
+        assert np.array_equal(psel.numpy(), dsel.cpu().numpy())
+        assert rel_err(psel.numpy(), full[np.ix_(sl.astype(np.int64), su.astype(np.int64))]) <= TOL_SPLIT
+    finally:
+        r.close()
+
+
 def diag_circuit_text(R, C, depth, b):
     """H layer, CZ patterns, T on idle qubits of odd layers (closed form of Eqs. 4, 6)."""
     n = R * C
