@@ -476,7 +476,10 @@ def run_q64(sim, torch, stream, leaves, contraction_tflops):
     """8x8 grid, depth 22, cut between rows 3 and 4: c = 16, 65536 copies of two
     32-qubit halves.  A seeded list of copies (splitmix64(0)) is evolved with prefix
     sharing; the measured time per fused pass extrapolates to all copies by Eq. (2):
-    Time = sum over levels of (passes of the level) x (nodes of the level) x t."""
+    Time = sum over levels of (passes of the level) x (nodes of the level) x t.  A
+    half whose last level reads its selected entries from the parents (the library's
+    sparse leaves) runs no passes there; that work is timed with the gather and
+    scaled by the number of copies."""
     import numpy as np
     R, C, D, B = 8, 8, 22, 4
     circ = sim.sim_build_circuit(R, C, D, 0, B)
@@ -487,12 +490,18 @@ def run_q64(sim, torch, stream, leaves, contraction_tflops):
     timed_selection_run(sim, torch, stream, plan, lst[:1], su, sl, out)   # warm-up: one copy
     ms, phases, st, prof = timed_selection_run(sim, torch, stream, plan, lst, su, sl, out)
     run_passes, full_passes, levels = 0, 0, []
-    for half in (0, 1):
-        for (layer, b0, b1, npass) in sim.sim_plan_levels(plan, half):
+    sparse = []
+    for half, (n_h, n_sel) in enumerate(((nu, su.size), (nl, sl.size))):
+        # the library's automatic rule for sparse leaves (include/sim.h, sim_opts)
+        nq = sim.sim_plan_leaf_qubits(plan, half)
+        sparse.append(nq <= 10 and (n_sel << nq) <= (1 << n_h) >> 3)
+        lv = sim.sim_plan_levels(plan, half)
+        for j, (layer, b0, b1, npass) in enumerate(lv):
             nodes = len(np.unique(lst & np.uint64((1 << int(b1)) - 1)))
-            run_passes += nodes * int(npass)
-            full_passes += (1 << int(b1)) * int(npass)
-            levels.append([half, int(layer), int(b1), int(npass), nodes])
+            run = 0 if (sparse[half] and j == len(lv) - 1) else int(npass)
+            run_passes += nodes * run
+            full_passes += (1 << int(b1)) * run
+            levels.append([half, int(layer), int(b1), int(npass), run, nodes])
     sweep_ms = prof["ms"][sim.SIM_PHASE_SWEEP]
     t_pass = sweep_ms / run_passes
     gather_pack_ms = sum(prof["ms"][i] for i in (sim.SIM_PHASE_GATHER, sim.SIM_PHASE_PACK))
@@ -506,12 +515,15 @@ def run_q64(sim, torch, stream, leaves, contraction_tflops):
            "leaves_run": leaves, "leaf_sample": "splitmix64(0), distinct copy indices (Floyd)",
            "ms": ms, "phases_ms": phases, "stats_of_sample": st,
            "fused_passes_run": run_passes, "ms_per_fused_pass": t_pass,
-           "levels": {"columns": ["half", "branch_layer", "copy_bits_after", "passes", "nodes_run"], "rows": levels},
+           "sparse_leaves": sparse,
+           "levels": {"columns": ["half", "branch_layer", "copy_bits_after", "passes", "passes_run", "nodes_run"],
+                      "rows": levels},
            "eq2_full_run": {"fused_passes": full_passes, **est, "total_s": total,
                             "amplitudes_per_s": su.size * sl.size / total,
-                            "note": "Eq. (2) with n_i = fused passes per level, m = nodes per level (all copies), "
-                                    "t = measured ms per fused pass on 32-qubit states; contraction at the "
-                                    "30-qubit bench's measured tensor rate"}}
+                            "note": "Eq. (2) with n_i = fused passes run per level, m = nodes per level (all "
+                                    "copies), t = measured ms per fused pass on 32-qubit states; sparse leaves and "
+                                    "the pack timed per copy and scaled; contraction at the 30-qubit bench's "
+                                    "measured tensor rate"}}
     del out
     sim.sim_destroy_cut(plan)
     sim.sim_destroy_circuit(circ)

@@ -111,7 +111,16 @@ typedef struct {
  *                  is a quarter of the available host memory.  For halves whose
  *                  levels do not fit in device memory; each pass then runs at the
  *                  host link's bandwidth.  The leaves stay in device memory, and
- *                  the results are those of device-resident levels. */
+ *                  the results are those of device-resident levels.
+ *   sparse_leaves  selected entries of the complex64 leaves (a selection, not all
+ *                  indices) computed from their parent states instead of from
+ *                  whole leaf states (Section 2.3.1: only the selected entries are
+ *                  needed).  The last copy-tree level's ops act non-diagonally on
+ *                  a set Q of qubits; an entry then needs the 2^|Q| parent entries
+ *                  that agree with it outside Q.  0: where |Q| <= 10 and
+ *                  n_sel * 2^|Q| <= 2^n / 8; 1: wherever |Q| <= 10 (and the tree
+ *                  has more than one level); -1: never.  Same results up to
+ *                  rounding order. */
 typedef struct {
   int fuse_qubits;
   int sweep_threads;
@@ -119,7 +128,8 @@ typedef struct {
   int sweep_kernel;
   int pass_order;
   int host_levels;
-  int reserved[2];
+  int sparse_leaves;
+  int reserved[1];
 } sim_opts;
 
 /* Build a circuit (Supplementary A, Eq. 3 circuit model; gate rules of the random
@@ -239,6 +249,13 @@ int sim_cut_list(sim_cut_plan plan, int32_t* cuts_out, int* n_equiv_out);
  * level and m its node count).  Writes at most cap levels; *n_levels receives the
  * number of levels.  Host only. */
 int sim_plan_levels(sim_cut_plan plan, int half, int32_t* out, int cap, int* n_levels);
+
+/* Number of qubits on which the ops of a half's last copy-tree level act
+ * non-diagonally (0 when that level applies only diagonal terms): the |Q| of
+ * sim_opts.sparse_leaves, whose selected leaf entries each read 2^|Q| parent
+ * entries (Section 2.3.1; Supplementary A, Eq. 1: the cut slots are diagonal).
+ * Host only. */
+int sim_plan_leaf_qubits(sim_cut_plan plan, int half, int* nq_out);
 
 int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passes,
                       int* plain_passes);

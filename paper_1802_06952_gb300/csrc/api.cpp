@@ -387,6 +387,7 @@ struct TreeBuilder {
   const HalfSchedule& S;
   const CopySet& cs;
   bool direct;            // leaves written straight into leafsel rows (no selection)
+  bool sparse;            // selected leaf entries computed from the parents (no leaf states)
   std::vector<std::vector<uint64_t>> needed;  // sorted node ids per level
   TreeProgram& prog;
 
@@ -425,6 +426,26 @@ struct TreeBuilder {
     for (size_t c0 = 0; c0 < ids.size(); c0 += (size_t)cap) {
       const size_t c1 = std::min(ids.size(), c0 + (size_t)cap);
       const int64_t off = (int64_t)prog.table.size();
+      if (leaf && sparse) {
+        // one launch: parent slot and leaf row of each leaf
+        const uint64_t pmask = L.bits_before >= 63 ? ~0ull : ((1ull << L.bits_before) - 1);
+        for (size_t i = c0; i < c1; ++i) {
+          NodeEntry e;
+          e.node_id = ids[i];
+          e.parent_slot = parent_slot.at(ids[i] & pmask);
+          e.dst_row = cs.row_of(ids[i]);
+          prog.table.push_back(e);
+        }
+        LaunchRec r;
+        r.level = j;
+        r.pass = -2;
+        r.table_off = off;
+        r.nslots = (int64_t)(c1 - c0);
+        r.src_buf = j - 1;
+        r.dst_buf = -1;
+        prog.launches.push_back(r);
+        continue;
+      }
       std::unordered_map<uint64_t, int64_t> my_slot;
       for (size_t i = c0; i < c1; ++i) {
         NodeEntry e;
@@ -487,7 +508,7 @@ struct TreeBuilder {
   }
 };
 
-TreeProgram plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_t budget) {
+TreeProgram plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_t budget, bool sparse = false) {
   const size_t state_bytes = sizeof(float) * 2 * ((size_t)1 << S.n);
   const int J = (int)S.levels.size();
   TreeProgram prog;
@@ -498,9 +519,28 @@ TreeProgram plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_
     if (cap < 1) cap = 1;
     prog.level_cap.push_back(std::min<int64_t>(cap, std::max<int64_t>(need_nodes, 1)));
   }
-  TreeBuilder tb{S, cs, full, {}, prog};
+  TreeBuilder tb{S, cs, full, sparse && !full && S.levels.size() > 1, {}, prog};
   tb.build();
   return prog;
+}
+
+// The ops of a half's last copy-tree level (a contiguous run of S.ops) and the
+// qubits on which they act non-diagonally: the inputs of the sparse leaf
+// evaluation.
+struct LeafOps {
+  uint32_t qmask = 0;
+  int nq = 0, op_begin = 0, op_count = 0;
+};
+LeafOps leaf_ops(const HalfSchedule& S) {
+  LeafOps r;
+  if (S.levels.empty() || S.levels.back().passes.empty()) return r;
+  const Level& L = S.levels.back();
+  r.op_begin = L.passes.front().op_begin;
+  r.op_count = L.passes.back().op_begin + L.passes.back().op_count - r.op_begin;
+  for (int o = r.op_begin; o < r.op_begin + r.op_count; ++o)
+    if (S.ops[o].type == OP_GATE) r.qmask |= 1u << S.ops[o].q;
+  r.nq = __builtin_popcount(r.qmask);
+  return r;
 }
 
 int enqueue_tree(const CutPlan& P, int h, const TreeProgram& prog, void* const* lvl, const NodeEntry* table,
@@ -511,6 +551,26 @@ int enqueue_tree(const CutPlan& P, int h, const TreeProgram& prog, void* const* 
   for (const LaunchRec& r : prog.launches) {
     void* dstp = r.dst_buf < 0 ? leafsel : lvl[r.dst_buf];
     PhaseScope ps(r.pass < 0 ? SIM_PHASE_GATHER : SIM_PHASE_SWEEP, st);
+    if (r.pass == -2) {
+      const LeafOps lo = leaf_ops(S);
+      SparseLeafLaunch sl;
+      memset(&sl, 0, sizeof sl);
+      sl.n = n;
+      sl.nq = lo.nq;
+      int b = 0;
+      for (int q = 0; q < n && b < kMaxSparseQ; ++q)
+        if ((lo.qmask >> q) & 1u) sl.qpos[b++] = (uint8_t)q;
+      sl.ops = P.d_ops[h] + lo.op_begin;
+      sl.op_count = lo.op_count;
+      sl.nodes = table + r.table_off;
+      sl.nslots = r.nslots;
+      sl.parent_base = lvl[r.src_buf];
+      sl.sel = d_sel;
+      sl.nsel = nsel;
+      sl.leafsel = leafsel;
+      CK(launch_sparse_leaf(sl, st));
+      continue;
+    }
     if (r.pass < 0) {
       CK(launch_gather(lvl[r.src_buf], n, table + r.table_off, r.nslots, d_sel, nsel, leafsel, 0, st));
       continue;
@@ -578,13 +638,21 @@ int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel,
     CK(cudaMemGetInfo(&fr, &tot));
     budget = (size_t)(fr * 0.6);
   }
-  const TreeProgram prog = plan_tree(S, cs, full, budget);
+  // Selected leaf entries straight from the parents (no leaf states) where the
+  // selection is sparse: 2^nq parent reads per entry against a pass over the whole
+  // leaf (sim_opts.sparse_leaves: 1 wherever it applies, -1 never)
+  const LeafOps lo = leaf_ops(S);
+  const int sparse_mode = opts ? opts->sparse_leaves : 0;
+  bool sparse = false;
+  if (!full && J > 1 && sparse_mode >= 0 && lo.nq <= kMaxSparseQ && S.n <= 32)
+    sparse = sparse_mode == 1 || (((uint64_t)nsel << lo.nq) <= (((uint64_t)1 << S.n) >> 3));
+  const TreeProgram prog = plan_tree(S, cs, full, budget, sparse);
   std::vector<DevBuf> lvl(J);
   std::vector<HostBuf> hlvl(J);
   std::vector<void*> lp(J, nullptr);
   for (int j = 0; j < J; ++j) {
     const bool leaf = (j == J - 1);
-    if (leaf && full) continue;
+    if (leaf && (full || sparse)) continue;
     const size_t bytes = state_bytes * (size_t)prog.level_cap[j];
     if (host) {
       if (hlvl[j].alloc(bytes) != cudaSuccess) {
@@ -796,7 +864,7 @@ void finish_stats(const double a[3], const std::vector<unsigned long long>& hh, 
 
 namespace sim {
 TreeProgram rt_plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_t budget) {
-  return plan_tree(S, cs, full, budget);
+  return plan_tree(S, cs, full, budget, false);
 }
 int rt_enqueue_tree(const CutPlan& P, int half, const TreeProgram& prog, void* const* lvl, const NodeEntry* table,
                     const uint64_t* d_sel, int64_t nsel, void* leafsel, cudaStream_t st, int kernel_choice,
@@ -1010,6 +1078,12 @@ int sim_plan_levels(sim_cut_plan plan, int half, int32_t* out, int cap, int* n_l
   return SIM_OK;
 }
 
+int sim_plan_leaf_qubits(sim_cut_plan plan, int half, int* nq_out) {
+  if (!plan || half < 0 || half > 1 || !nq_out) return fail(SIM_EINVAL, "bad arguments");
+  *nq_out = leaf_ops(plan->p.sched[half]).nq;
+  return SIM_OK;
+}
+
 int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passes, int* plain_passes) {
   if (!plan || half < 0 || half > 1) return fail(SIM_EINVAL, "bad plan or half");
   const HalfSchedule& S = plan->p.sched[half];
@@ -1040,6 +1114,8 @@ int evolve_halves_impl(sim_cut_plan plan, int precision, CopySet&& cs, const uin
   }
   if (opts && opts->sweep_threads && (opts->sweep_threads < 64 || opts->sweep_threads > 256 || opts->sweep_threads % 32))
     return fail(SIM_EINVAL, "sweep_threads must be a multiple of 32 in 64..256");
+  if (opts && (opts->sparse_leaves < -1 || opts->sparse_leaves > 1))
+    return fail(SIM_EINVAL, "sparse_leaves must be -1, 0 or 1");
   // the copy tree's node table is built on the host: keep one call bounded
   if (cs.size() > (1ull << 26))
     return fail(SIM_EUNSUPPORTED, "more than 2^26 copies in one call: evolve copy ranges and accumulate");
@@ -1386,6 +1462,8 @@ int sim_multi_amplitudes(sim_multi_plan plan, int precision, int contraction, co
     return fail(SIM_EINVAL, "multi-part cuts take SIM_C64 with a split contraction or SIM_C128_PLAIN with SIM_FP64_PLAIN");
   if (opts && opts->sweep_threads && (opts->sweep_threads < 64 || opts->sweep_threads > 256 || opts->sweep_threads % 32))
     return fail(SIM_EINVAL, "sweep_threads must be a multiple of 32 in 64..256");
+  if (opts && (opts->sparse_leaves < -1 || opts->sparse_leaves > 1))
+    return fail(SIM_EINVAL, "sparse_leaves must be -1, 0 or 1");
   MultiPlan& M = plan->mp;
   cudaStream_t st = (cudaStream_t)stream;
   // re-plan for another fuse width or pass order

@@ -339,6 +339,26 @@ cudaError_t launch_absmax_c64(const void* x, int64_t count, float* out_dev, cuda
 // dst[i] = src[idx[i]] for n complex64 values (a flat-index gather of amplitudes)
 cudaError_t launch_gather_flat_c64(const void* src, const uint64_t* idx, int64_t n, void* dst, cudaStream_t s);
 
+// Selected entries of leaf half-states computed from their parents (the leaf level's
+// ops are non-diagonal on the nq qubits qpos only): for each leaf node and selected
+// index, the 2^nq parent entries that agree with it outside those qubits, the
+// level's ops on them, and the entry at its own bits; replaces the leaf level's
+// passes and the gather.
+constexpr int kMaxSparseQ = 10;
+struct SparseLeafLaunch {
+  int n, nq;
+  uint8_t qpos[kMaxSparseQ];
+  const OpRec* ops;           // device ops of the leaf level's passes, in order
+  int op_count;
+  const NodeEntry* nodes;     // node_id, parent_slot, dst_row = leaf row
+  int64_t nslots;
+  const void* parent_base;    // complex64 parent states, slot stride 2^n
+  const uint64_t* sel;        // device selection
+  int64_t nsel;
+  void* leafsel;              // complex64 [row][nsel]
+};
+cudaError_t launch_sparse_leaf(const SparseLeafLaunch& L, cudaStream_t s);
+
 // tcgen05 contraction: C[M][2N] fp32 (= complex64 [M][N]) (+)= sum over 3 split
 // segments of A_seg[M][kpad] * B_seg[2N][kpad]^T.
 struct TcGemmArgs {

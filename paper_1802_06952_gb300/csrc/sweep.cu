@@ -257,6 +257,100 @@ __global__ void gather_kernel(const T* src, int n, const NodeEntry* nodes, int64
   }
 }
 
+// Selected entries of leaf states computed from their parent states, without the
+// leaf states (Section 2.3.1's sampling needs only the selected entries).  The
+// ops of the leaf level act non-diagonally on the qubits Q alone (|Q| = nq), so
+// for a selected index x, with x_o its bits outside Q,
+//   leaf(x) = sum over y of <x| G |x_o + y> parent(x_o + y),  y over the 2^nq
+// settings of the Q bits: one warp loads those 2^nq parent entries into a small
+// vector (local bit b = qubit qpos[b]), applies the level's ops to it in order
+// (full gate matrices as in sweep_c64_kernel; diagonal terms evaluated at the full
+// index x_o + y), and keeps the entry at x's Q bits.
+struct SparseLeafArgs {
+  int n, nq;
+  uint32_t qmask;
+  uint8_t qpos[kMaxSparseQ];
+  uint8_t qrank[32];          // local bit of each qubit of Q
+  const OpRec* ops;
+  int op_count;
+  const NodeEntry* nodes;     // leaf nodes: node_id, parent_slot, dst_row = leaf row
+  int64_t nslots;
+  const float2* parent_base;  // parent level buffer (slot stride 2^n)
+  const uint64_t* sel;
+  int64_t nsel;
+  float2* leafsel;            // [row][nsel]
+};
+
+constexpr int kSparseWarps = 8;
+
+__global__ void __launch_bounds__(32 * kSparseWarps) sparse_leaf_kernel(SparseLeafArgs a) {
+  extern __shared__ float2 sv_all[];  // kSparseWarps vectors of 2^nq, then the offsets
+  const int size = 1 << a.nq;
+  uint32_t* scat = (uint32_t*)(sv_all + kSparseWarps * size);  // index bits of each local y
+  for (int e = threadIdx.x; e < size; e += blockDim.x) {
+    uint32_t off = 0;
+    for (int b = 0; b < a.nq; ++b)
+      if ((e >> b) & 1) off |= 1u << a.qpos[b];
+    scat[e] = off;
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* v = sv_all + w * size;
+  const uint64_t total = (uint64_t)a.nslots * (uint64_t)a.nsel;
+  for (uint64_t item = (uint64_t)blockIdx.x * kSparseWarps + w; item < total;
+       item += (uint64_t)gridDim.x * kSparseWarps) {
+    const uint64_t s = item / (uint64_t)a.nsel, i = item % (uint64_t)a.nsel;
+    const NodeEntry ne = a.nodes[s];
+    const uint32_t x = (uint32_t)a.sel[i];
+    const uint32_t xo = x & ~a.qmask;
+    const float2* par = a.parent_base + ((uint64_t)ne.parent_slot << a.n);
+    for (int e = lane; e < size; e += 32) v[e] = par[xo | scat[e]];
+    __syncwarp();
+    for (int o = 0; o < a.op_count; ++o) {
+      const OpRec* op = a.ops + o;
+      const int type = __ldg(&op->type);
+      if (type == OP_SWAP) continue;  // layout exchanges of the register-blocked sweep
+      if (type == OP_GATE) {
+        const int cond = __ldg(&op->cond);
+        if (cond >= 0 && !((ne.node_id >> cond) & 1ull)) continue;
+        const int lq = a.qrank[__ldg(&op->q)];
+        const float2 m00 = make_float2(__ldg(&op->m[0]), __ldg(&op->m[1]));
+        const float2 m01 = make_float2(__ldg(&op->m[2]), __ldg(&op->m[3]));
+        const float2 m10 = make_float2(__ldg(&op->m[4]), __ldg(&op->m[5]));
+        const float2 m11 = make_float2(__ldg(&op->m[6]), __ldg(&op->m[7]));
+        const int lo_mask = (1 << lq) - 1;
+        for (int p = lane; p < (size >> 1); p += 32) {
+          const int i0 = ((p & ~lo_mask) << 1) | (p & lo_mask);
+          const int i1 = i0 | (1 << lq);
+          const float2 a0 = v[i0], a1 = v[i1];
+          float2 r0 = cmul(m00, a0), r1 = cmul(m10, a0);
+          const float2 t0 = cmul(m01, a1), t1 = cmul(m11, a1);
+          r0.x += t0.x; r0.y += t0.y;
+          r1.x += t1.x; r1.y += t1.y;
+          v[i0] = r0;
+          v[i1] = r1;
+        }
+      } else {
+        DiagState d;
+        load_diag(op, ne.node_id, d);
+        for (int e = lane; e < size; e += 32) {
+          bool keep;
+          const int ex = diag_exp(d, xo | scat[e], keep);
+          v[e] = keep ? cmul(v[e], kOmegaF[ex]) : make_float2(0.f, 0.f);
+        }
+      }
+      __syncwarp();
+    }
+    if (lane == 0) {
+      uint32_t ex = 0;
+      for (int b = 0; b < a.nq; ++b)
+        if ((x >> a.qpos[b]) & 1u) ex |= 1u << b;
+      a.leafsel[(uint64_t)ne.dst_row * (uint64_t)a.nsel + i] = v[ex];
+    }
+    __syncwarp();
+  }
+}
+
 unsigned grid_for(uint64_t work, int threads) {
   uint64_t b = (work + threads - 1) / threads;
   if (b > (1u << 20)) b = 1u << 20;
@@ -348,6 +442,43 @@ cudaError_t launch_gather(const void* src, int n, const NodeEntry* nodes, int64_
   else
     gather_kernel<float2><<<grid_for(total, 256), 256, 0, s>>>((const float2*)src, n, nodes, nslots,
                                                                 sel, nsel, (float2*)dst);
+  note_launches(SIM_PHASE_GATHER, 1);
+  return cudaGetLastError();
+}
+
+
+cudaError_t launch_sparse_leaf(const SparseLeafLaunch& L, cudaStream_t s) {
+  if (L.nq < 0 || L.nq > kMaxSparseQ || L.n < 1 || L.n > 32) return cudaErrorInvalidValue;
+  const uint64_t total = (uint64_t)L.nslots * (uint64_t)L.nsel;
+  if (total == 0) return cudaSuccess;
+  SparseLeafArgs a;
+  memset(&a, 0, sizeof a);
+  a.n = L.n;
+  a.nq = L.nq;
+  a.qmask = 0;
+  for (int b = 0; b < L.nq; ++b) {
+    if (L.qpos[b] >= L.n || (a.qmask >> L.qpos[b]) & 1u) return cudaErrorInvalidValue;
+    a.qpos[b] = L.qpos[b];
+    a.qrank[L.qpos[b]] = (uint8_t)b;
+    a.qmask |= 1u << L.qpos[b];
+  }
+  a.ops = L.ops;
+  a.op_count = L.op_count;
+  a.nodes = L.nodes;
+  a.nslots = L.nslots;
+  a.parent_base = (const float2*)L.parent_base;
+  a.sel = L.sel;
+  a.nsel = L.nsel;
+  a.leafsel = (float2*)L.leafsel;
+  const size_t smem = ((size_t)kSparseWarps * sizeof(float2) + sizeof(uint32_t)) << L.nq;
+  static DeviceOnce attr;
+  cudaError_t e = attr.run([](int&) {
+    return cudaFuncSetAttribute(sparse_leaf_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(((size_t)kSparseWarps * sizeof(float2) + sizeof(uint32_t)) << kMaxSparseQ));
+  });
+  if (e != cudaSuccess) return e;
+  const uint64_t blocks = (total + kSparseWarps - 1) / kSparseWarps;
+  sparse_leaf_kernel<<<(unsigned)(blocks < (1u << 20) ? blocks : (1u << 20)), 32 * kSparseWarps, smem, s>>>(a);
   note_launches(SIM_PHASE_GATHER, 1);
   return cudaGetLastError();
 }
