@@ -492,13 +492,19 @@ def run_q64(sim, torch, stream, leaves, contraction_tflops):
     run_passes, full_passes, levels = 0, 0, []
     sparse = []
     for half, (n_h, n_sel) in enumerate(((nu, su.size), (nl, sl.size))):
-        # the library's automatic rule for sparse leaves (include/sim.h, sim_opts)
-        nq = sim.sim_plan_leaf_qubits(plan, half)
-        sparse.append(nq <= 10 and (n_sel << nq) <= (1 << n_h) >> 3)
         lv = sim.sim_plan_levels(plan, half)
+        # the library's automatic rule for sparse leaves (include/sim.h, sim_opts): the
+        # most trailing levels with |Q| <= 10 and n_sel 2^|Q| <= 2^n / 8 are not formed
+        depth = 0
+        for d in range(len(lv) - 1, 0, -1):
+            nq = sim.sim_plan_sparse_qubits(plan, half, d)
+            if nq <= 10 and (n_sel << nq) <= (1 << n_h) >> 3:
+                depth = d
+                break
+        sparse.append(depth)
         for j, (layer, b0, b1, npass) in enumerate(lv):
             nodes = len(np.unique(lst & np.uint64((1 << int(b1)) - 1)))
-            run = 0 if (sparse[half] and j == len(lv) - 1) else int(npass)
+            run = 0 if j >= len(lv) - depth else int(npass)
             run_passes += nodes * run
             full_passes += (1 << int(b1)) * run
             levels.append([half, int(layer), int(b1), int(npass), run, nodes])
@@ -515,7 +521,7 @@ def run_q64(sim, torch, stream, leaves, contraction_tflops):
            "leaves_run": leaves, "leaf_sample": "splitmix64(0), distinct copy indices (Floyd)",
            "ms": ms, "phases_ms": phases, "stats_of_sample": st,
            "fused_passes_run": run_passes, "ms_per_fused_pass": t_pass,
-           "sparse_leaves": sparse,
+           "sparse_levels": sparse,
            "levels": {"columns": ["half", "branch_layer", "copy_bits_after", "passes", "passes_run", "nodes_run"],
                       "rows": levels},
            "eq2_full_run": {"fused_passes": full_passes, **est, "total_s": total,

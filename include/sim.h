@@ -113,14 +113,16 @@ typedef struct {
  *                  host link's bandwidth.  The leaves stay in device memory, and
  *                  the results are those of device-resident levels.
  *   sparse_leaves  selected entries of the complex64 leaves (a selection, not all
- *                  indices) computed from their parent states instead of from
+ *                  indices) computed from an ancestor's state instead of from
  *                  whole leaf states (Section 2.3.1: only the selected entries are
- *                  needed).  The last copy-tree level's ops act non-diagonally on
- *                  a set Q of qubits; an entry then needs the 2^|Q| parent entries
- *                  that agree with it outside Q.  0: where |Q| <= 10 and
- *                  n_sel * 2^|Q| <= 2^n / 8; 1: wherever |Q| <= 10 (and the tree
- *                  has more than one level); -1: never.  Same results up to
- *                  rounding order. */
+ *                  needed).  The ops of the last d copy-tree levels act
+ *                  non-diagonally on a set Q of qubits (sim_plan_sparse_qubits); an
+ *                  entry then needs the 2^|Q| entries of its ancestor d levels up
+ *                  that agree with it outside Q, and those d levels are never
+ *                  formed.  d is the largest value below the number of levels with
+ *                  |Q| <= 10 and (0, the default) n_sel * 2^|Q| <= 2^n / 8, or
+ *                  (1) |Q| <= 10 alone; -1: never.  Same results up to rounding
+ *                  order. */
 typedef struct {
   int fuse_qubits;
   int sweep_threads;
@@ -250,12 +252,13 @@ int sim_cut_list(sim_cut_plan plan, int32_t* cuts_out, int* n_equiv_out);
  * number of levels.  Host only. */
 int sim_plan_levels(sim_cut_plan plan, int half, int32_t* out, int cap, int* n_levels);
 
-/* Number of qubits on which the ops of a half's last copy-tree level act
- * non-diagonally (0 when that level applies only diagonal terms): the |Q| of
- * sim_opts.sparse_leaves, whose selected leaf entries each read 2^|Q| parent
- * entries (Section 2.3.1; Supplementary A, Eq. 1: the cut slots are diagonal).
- * Host only. */
-int sim_plan_leaf_qubits(sim_cut_plan plan, int half, int* nq_out);
+/* Number of qubits on which the ops of a half's last `levels` copy-tree levels act
+ * non-diagonally (0 when they apply only diagonal terms): the |Q| of
+ * sim_opts.sparse_leaves, whose selected leaf entries are each computed from 2^|Q|
+ * entries of their ancestor `levels` levels up (Section 2.3.1; Supplementary A,
+ * Eq. 1: the cut slots are diagonal).  1 <= levels < number of levels
+ * (sim_plan_levels), else SIM_EINVAL.  Host only. */
+int sim_plan_sparse_qubits(sim_cut_plan plan, int half, int levels, int* nq_out);
 
 int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passes,
                       int* plain_passes);

@@ -34,7 +34,7 @@ EXPORTS = (
     "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc", "sim_amplitudes_stats",
     "sim_evolve_halves_list", "sim_plan_levels", "sim_batch_create", "sim_batch_run", "sim_batch_results",
     "sim_batch_info", "sim_destroy_batch", "sim_born_sample", "sim_cut_ex", "sim_cut_output_phases",
-    "sim_cut_multi", "sim_multi_amplitudes", "sim_destroy_multi", "sim_selftest_wait", "sim_plan_leaf_qubits",
+    "sim_cut_multi", "sim_multi_amplitudes", "sim_destroy_multi", "sim_selftest_wait", "sim_plan_sparse_qubits",
 )
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -96,7 +96,7 @@ def lib():
         "sim_selftest_wait": (ctypes.c_int, [ctypes.c_int, vp]),
         "sim_plan_schedule": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ip]),
         "sim_plan_levels": (ctypes.c_int, [vp, ctypes.c_int, i32p, ctypes.c_int, ip]),
-        "sim_plan_leaf_qubits": (ctypes.c_int, [vp, ctypes.c_int, ip]),
+        "sim_plan_sparse_qubits": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip]),
         "sim_evolve_halves": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u64p, u64, u64p, u64,
                                              ctypes.POINTER(SimOpts), vp, ctypes.POINTER(vp)]),
         "sim_evolve_halves_list": (ctypes.c_int, [vp, ctypes.c_int, u64p, u64, u64p, u64, u64p, u64,
@@ -283,9 +283,9 @@ def sim_plan_schedule(plan, half):
     return a.value, b.value, c.value
 
 
-def sim_plan_leaf_qubits(plan, half):
+def sim_plan_sparse_qubits(plan, half, levels):
     n = ctypes.c_int()
-    _check(lib().sim_plan_leaf_qubits(plan, half, ctypes.byref(n)))
+    _check(lib().sim_plan_sparse_qubits(plan, half, levels, ctypes.byref(n)))
     return n.value
 
 

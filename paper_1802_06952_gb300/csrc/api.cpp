@@ -387,7 +387,7 @@ struct TreeBuilder {
   const HalfSchedule& S;
   const CopySet& cs;
   bool direct;            // leaves written straight into leafsel rows (no selection)
-  bool sparse;            // selected leaf entries computed from the parents (no leaf states)
+  int sparse_d;           // > 0: the selected leaf entries come from the level sparse_d above the leaves
   std::vector<std::vector<uint64_t>> needed;  // sorted node ids per level
   TreeProgram& prog;
 
@@ -426,26 +426,6 @@ struct TreeBuilder {
     for (size_t c0 = 0; c0 < ids.size(); c0 += (size_t)cap) {
       const size_t c1 = std::min(ids.size(), c0 + (size_t)cap);
       const int64_t off = (int64_t)prog.table.size();
-      if (leaf && sparse) {
-        // one launch: parent slot and leaf row of each leaf
-        const uint64_t pmask = L.bits_before >= 63 ? ~0ull : ((1ull << L.bits_before) - 1);
-        for (size_t i = c0; i < c1; ++i) {
-          NodeEntry e;
-          e.node_id = ids[i];
-          e.parent_slot = parent_slot.at(ids[i] & pmask);
-          e.dst_row = cs.row_of(ids[i]);
-          prog.table.push_back(e);
-        }
-        LaunchRec r;
-        r.level = j;
-        r.pass = -2;
-        r.table_off = off;
-        r.nslots = (int64_t)(c1 - c0);
-        r.src_buf = j - 1;
-        r.dst_buf = -1;
-        prog.launches.push_back(r);
-        continue;
-      }
       std::unordered_map<uint64_t, int64_t> my_slot;
       for (size_t i = c0; i < c1; ++i) {
         NodeEntry e;
@@ -470,6 +450,30 @@ struct TreeBuilder {
         r.src_buf = (p == 0 && j > 0) ? j - 1 : dst;
         r.dst_buf = dst;
         prog.launches.push_back(r);
+      }
+      if (sparse_d > 0 && j == J - 1 - sparse_d) {
+        // the leaves under this chunk's nodes, read from them (one launch): ancestor
+        // slot and leaf row of each leaf; the levels below are never formed
+        const uint64_t amask = L.bits_total >= 63 ? ~0ull : ((1ull << L.bits_total) - 1);
+        const int64_t soff = (int64_t)prog.table.size();
+        for (uint64_t id : needed[J - 1]) {
+          const auto it = my_slot.find(id & amask);
+          if (it == my_slot.end()) continue;
+          NodeEntry e;
+          e.node_id = id;
+          e.parent_slot = it->second;
+          e.dst_row = cs.row_of(id);
+          prog.table.push_back(e);
+        }
+        LaunchRec r;
+        r.level = j;
+        r.pass = -2;
+        r.table_off = soff;
+        r.nslots = (int64_t)prog.table.size() - soff;
+        r.src_buf = j;
+        r.dst_buf = -1;
+        if (r.nslots > 0) prog.launches.push_back(r);
+        continue;
       }
       if (leaf) {
         if (!direct) {
@@ -508,7 +512,7 @@ struct TreeBuilder {
   }
 };
 
-TreeProgram plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_t budget, bool sparse = false) {
+TreeProgram plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_t budget, int sparse_d = 0) {
   const size_t state_bytes = sizeof(float) * 2 * ((size_t)1 << S.n);
   const int J = (int)S.levels.size();
   TreeProgram prog;
@@ -519,28 +523,43 @@ TreeProgram plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_
     if (cap < 1) cap = 1;
     prog.level_cap.push_back(std::min<int64_t>(cap, std::max<int64_t>(need_nodes, 1)));
   }
-  TreeBuilder tb{S, cs, full, sparse && !full && S.levels.size() > 1, {}, prog};
+  TreeBuilder tb{S, cs, full, full ? 0 : sparse_d, {}, prog};
   tb.build();
   return prog;
 }
 
-// The ops of a half's last copy-tree level (a contiguous run of S.ops) and the
-// qubits on which they act non-diagonally: the inputs of the sparse leaf
-// evaluation.
+// The ops of a half's last d copy-tree levels (a contiguous run of S.ops: levels
+// and their passes are laid out in order) and the qubits on which they act
+// non-diagonally: the inputs of the sparse leaf evaluation.
 struct LeafOps {
   uint32_t qmask = 0;
   int nq = 0, op_begin = 0, op_count = 0;
 };
-LeafOps leaf_ops(const HalfSchedule& S) {
+LeafOps leaf_ops(const HalfSchedule& S, int d) {
   LeafOps r;
-  if (S.levels.empty() || S.levels.back().passes.empty()) return r;
-  const Level& L = S.levels.back();
-  r.op_begin = L.passes.front().op_begin;
-  r.op_count = L.passes.back().op_begin + L.passes.back().op_count - r.op_begin;
+  const int J = (int)S.levels.size();
+  if (d < 1 || d > J || S.levels[J - d].passes.empty() || S.levels.back().passes.empty()) return r;
+  r.op_begin = S.levels[J - d].passes.front().op_begin;
+  r.op_count = S.levels.back().passes.back().op_begin + S.levels.back().passes.back().op_count - r.op_begin;
   for (int o = r.op_begin; o < r.op_begin + r.op_count; ++o)
     if (S.ops[o].type == OP_GATE) r.qmask |= 1u << S.ops[o].q;
   r.nq = __builtin_popcount(r.qmask);
   return r;
+}
+
+// Levels the sparse leaf evaluation covers (0: none): the most trailing levels,
+// below at least the root, whose ops act non-diagonally on at most kMaxSparseQ
+// qubits Q, and (mode 0) with nsel * 2^|Q| <= 2^n / 8; mode 1: the |Q| limit only;
+// mode -1: none.
+int sparse_depth(const HalfSchedule& S, int64_t nsel, int mode) {
+  const int J = (int)S.levels.size();
+  if (mode < 0 || S.n > 32) return 0;
+  for (int d = J - 1; d >= 1; --d) {
+    const LeafOps lo = leaf_ops(S, d);
+    if (lo.nq > kMaxSparseQ) continue;
+    if (mode == 1 || (((uint64_t)nsel << lo.nq) <= (((uint64_t)1 << S.n) >> 3))) return d;
+  }
+  return 0;
 }
 
 int enqueue_tree(const CutPlan& P, int h, const TreeProgram& prog, void* const* lvl, const NodeEntry* table,
@@ -552,7 +571,7 @@ int enqueue_tree(const CutPlan& P, int h, const TreeProgram& prog, void* const* 
     void* dstp = r.dst_buf < 0 ? leafsel : lvl[r.dst_buf];
     PhaseScope ps(r.pass < 0 ? SIM_PHASE_GATHER : SIM_PHASE_SWEEP, st);
     if (r.pass == -2) {
-      const LeafOps lo = leaf_ops(S);
+      const LeafOps lo = leaf_ops(S, (int)S.levels.size() - 1 - r.level);
       SparseLeafLaunch sl;
       memset(&sl, 0, sizeof sl);
       sl.n = n;
@@ -641,18 +660,14 @@ int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel,
   // Selected leaf entries straight from the parents (no leaf states) where the
   // selection is sparse: 2^nq parent reads per entry against a pass over the whole
   // leaf (sim_opts.sparse_leaves: 1 wherever it applies, -1 never)
-  const LeafOps lo = leaf_ops(S);
-  const int sparse_mode = opts ? opts->sparse_leaves : 0;
-  bool sparse = false;
-  if (!full && J > 1 && sparse_mode >= 0 && lo.nq <= kMaxSparseQ && S.n <= 32)
-    sparse = sparse_mode == 1 || (((uint64_t)nsel << lo.nq) <= (((uint64_t)1 << S.n) >> 3));
-  const TreeProgram prog = plan_tree(S, cs, full, budget, sparse);
+  const int sparse_d = full ? 0 : sparse_depth(S, nsel, opts ? opts->sparse_leaves : 0);
+  const TreeProgram prog = plan_tree(S, cs, full, budget, sparse_d);
   std::vector<DevBuf> lvl(J);
   std::vector<HostBuf> hlvl(J);
   std::vector<void*> lp(J, nullptr);
   for (int j = 0; j < J; ++j) {
     const bool leaf = (j == J - 1);
-    if (leaf && (full || sparse)) continue;
+    if ((leaf && full) || j > J - 1 - sparse_d) continue;
     const size_t bytes = state_bytes * (size_t)prog.level_cap[j];
     if (host) {
       if (hlvl[j].alloc(bytes) != cudaSuccess) {
@@ -864,7 +879,7 @@ void finish_stats(const double a[3], const std::vector<unsigned long long>& hh, 
 
 namespace sim {
 TreeProgram rt_plan_tree(const HalfSchedule& S, const CopySet& cs, bool full, size_t budget) {
-  return plan_tree(S, cs, full, budget, false);
+  return plan_tree(S, cs, full, budget, 0);
 }
 int rt_enqueue_tree(const CutPlan& P, int half, const TreeProgram& prog, void* const* lvl, const NodeEntry* table,
                     const uint64_t* d_sel, int64_t nsel, void* leafsel, cudaStream_t st, int kernel_choice,
@@ -1078,9 +1093,12 @@ int sim_plan_levels(sim_cut_plan plan, int half, int32_t* out, int cap, int* n_l
   return SIM_OK;
 }
 
-int sim_plan_leaf_qubits(sim_cut_plan plan, int half, int* nq_out) {
+int sim_plan_sparse_qubits(sim_cut_plan plan, int half, int levels, int* nq_out) {
   if (!plan || half < 0 || half > 1 || !nq_out) return fail(SIM_EINVAL, "bad arguments");
-  *nq_out = leaf_ops(plan->p.sched[half]).nq;
+  const HalfSchedule& S = plan->p.sched[half];
+  if (levels < 1 || levels >= (int)S.levels.size())
+    return fail(SIM_EINVAL, "levels must be at least 1 and below the number of copy-tree levels");
+  *nq_out = leaf_ops(S, levels).nq;
   return SIM_OK;
 }
 

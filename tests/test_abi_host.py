@@ -159,25 +159,33 @@ def test_plan_levels_cover_the_copy_bits(R, C, d, b):
 
 
 
-def test_leaf_qubits_of_the_last_level():
-    """The qubits the last copy-tree level acts on non-diagonally (the |Q| of the
-    sparse leaf entries): none when the circuit ends with the last cut layer's
-    slots (depth 16: layer 15 is the last), a few at depth 22 (the light cone of
-    the layer-16 slots over layers 17-21), never more than the half's qubits."""
+def test_sparse_qubits_of_the_last_levels():
+    """The qubits the last copy-tree levels act on non-diagonally (the |Q| of the
+    sparse leaf entries): none for the last level when the circuit ends with the
+    last cut layer's slots (depth 16: layer 15 is the last), a few at depth 22 (the
+    light cone of the layer-16 slots over layers 17-21); never fewer for more
+    levels, never more than the half's qubits."""
     for (R, C, d, b), zero in (((6, 5, 16, 3), True), ((8, 8, 22, 4), False), ((6, 7, 22, 3), False)):
         circ = sim.sim_build_circuit(R, C, d, 0, b)
         plan, c, copies, nu, nl = sim.sim_cut(circ, b)
         try:
-            nq = [sim.sim_plan_leaf_qubits(plan, h) for h in (0, 1)]
-            assert all(0 <= q <= n for q, n in zip(nq, (nu, nl)))
-            assert (nq == [0, 0]) == zero
-            if not zero:
-                assert max(nq) <= 10
+            for half, n in ((0, nu), (1, nl)):
+                J = sim.sim_plan_levels(plan, half).shape[0]
+                nq = [sim.sim_plan_sparse_qubits(plan, half, lv) for lv in range(1, J)]
+                assert all(0 <= q <= n for q in nq)
+                assert all(a <= b2 for a, b2 in zip(nq, nq[1:]))
+                assert (nq[0] == 0) == zero
+                if not zero:
+                    assert nq[0] <= 10
+                for bad in (0, J):
+                    with pytest.raises(sim.SimError) as e:
+                        sim.sim_plan_sparse_qubits(plan, half, bad)
+                    assert e.value.code == sim.SIM_EINVAL
         finally:
             sim.sim_destroy_cut(plan)
             sim.sim_destroy_circuit(circ)
         with pytest.raises(sim.SimError):
-            sim.sim_plan_leaf_qubits(None, 0)
+            sim.sim_plan_sparse_qubits(None, 0, 1)
 
 
 @pytest.mark.parametrize("R,C,d,b,leaf_passes", [(6, 7, 22, 3, 1), (8, 8, 22, 4, 1)])

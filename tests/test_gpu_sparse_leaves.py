@@ -1,10 +1,13 @@
-"""Selected leaf entries computed from the parent states (sim_opts.sparse_leaves):
+"""Selected leaf entries computed from an ancestor's state (sim_opts.sparse_leaves):
 the same leaves and amplitudes as whole leaf states swept and gathered, and the
 oracle's cut-and-sum, through the C-ABI.
 
-The last copy-tree level's ops act non-diagonally on a qubit set Q; an entry x of
-a leaf is then the level's ops applied to the 2^|Q| parent entries that agree with
-x outside Q (Section 2.3.1: only the selected entries are needed)."""
+The ops of the last d copy-tree levels act non-diagonally on a qubit set Q; an
+entry x of a leaf is then those ops applied to the 2^|Q| entries of its ancestor d
+levels up that agree with x outside Q (Section 2.3.1: only the selected entries are
+needed).  Forced mode takes the largest d with |Q| <= 10: on these 8- to 12-qubit
+halves that reaches up to the root level, so the slots of several levels are
+applied in one evaluation."""
 import numpy as np
 import pytest
 
@@ -66,7 +69,7 @@ def check(circ, gplan, b, copies, su, sl, copy_list=None):
         hs, n_sparse = sweep_launches(lambda: evolve(1))
         hw, n_whole = sweep_launches(lambda: evolve(-1))
         try:
-            # the sparse route runs no leaf-level passes
+            # the sparse route runs no passes of the levels it covers
             assert n_sparse < n_whole
             ks = list(copy_list) if copy_list is not None else [0, ncopies // 3, ncopies - 1]
             for a, w in zip(leaves(hs, ks, su.size, sl.size), leaves(hw, ks, su.size, sl.size)):
