@@ -493,14 +493,8 @@ def run_q64(sim, torch, stream, leaves, contraction_tflops):
     sparse = []
     for half, (n_h, n_sel) in enumerate(((nu, su.size), (nl, sl.size))):
         lv = sim.sim_plan_levels(plan, half)
-        # the library's automatic rule for sparse leaves (include/sim.h, sim_opts): the
-        # most trailing levels with |Q| <= 10 and n_sel 2^|Q| <= 2^n / 8 are not formed
-        depth = 0
-        for d in range(len(lv) - 1, 0, -1):
-            nq = sim.sim_plan_sparse_qubits(plan, half, d)
-            if nq <= 10 and (n_sel << nq) <= (1 << n_h) >> 3:
-                depth = d
-                break
+        # trailing levels the evolve leaves unformed for this selection (sparse leaves)
+        depth = sim.sim_plan_sparse_depth(plan, half, n_sel)
         sparse.append(depth)
         for j, (layer, b0, b1, npass) in enumerate(lv):
             nodes = len(np.unique(lst & np.uint64((1 << int(b1)) - 1)))

@@ -260,6 +260,13 @@ int sim_plan_levels(sim_cut_plan plan, int half, int32_t* out, int cap, int* n_l
  * (sim_plan_levels), else SIM_EINVAL.  Host only. */
 int sim_plan_sparse_qubits(sim_cut_plan plan, int half, int levels, int* nq_out);
 
+/* The number of trailing copy-tree levels of a half that sim_evolve_halves leaves
+ * unformed for a selection of n_sel entries of that half under sim_opts.sparse_leaves
+ * = mode (0, 1 or -1; see sim_opts): the largest d below the number of levels with
+ * |Q| <= 10 (sim_plan_sparse_qubits) and, for mode 0, n_sel * 2^|Q| <= 2^n / 8; 0
+ * when none qualifies, mode is -1 or n_sel covers the whole half.  Host only. */
+int sim_plan_sparse_depth(sim_cut_plan plan, int half, uint64_t n_sel, int mode, int* depth_out);
+
 int sim_plan_schedule(sim_cut_plan plan, int half, int* levels, int* fused_passes,
                       int* plain_passes);
 

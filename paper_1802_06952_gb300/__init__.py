@@ -34,7 +34,7 @@ EXPORTS = (
     "sim_profile_enable", "sim_profile_read", "sim_amplitudes_noalloc", "sim_amplitudes_stats",
     "sim_evolve_halves_list", "sim_plan_levels", "sim_batch_create", "sim_batch_run", "sim_batch_results",
     "sim_batch_info", "sim_destroy_batch", "sim_born_sample", "sim_cut_ex", "sim_cut_output_phases",
-    "sim_cut_multi", "sim_multi_amplitudes", "sim_destroy_multi", "sim_selftest_wait", "sim_plan_sparse_qubits",
+    "sim_cut_multi", "sim_multi_amplitudes", "sim_destroy_multi", "sim_selftest_wait", "sim_plan_sparse_qubits", "sim_plan_sparse_depth",
 )
 SIM_NOALLOC_SCRATCH_BYTES = 32 << 20
 
@@ -97,6 +97,7 @@ def lib():
         "sim_plan_schedule": (ctypes.c_int, [vp, ctypes.c_int, ip, ip, ip]),
         "sim_plan_levels": (ctypes.c_int, [vp, ctypes.c_int, i32p, ctypes.c_int, ip]),
         "sim_plan_sparse_qubits": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip]),
+        "sim_plan_sparse_depth": (ctypes.c_int, [vp, ctypes.c_int, u64, ctypes.c_int, ip]),
         "sim_evolve_halves": (ctypes.c_int, [vp, ctypes.c_int, u64, u64, u64p, u64, u64p, u64,
                                              ctypes.POINTER(SimOpts), vp, ctypes.POINTER(vp)]),
         "sim_evolve_halves_list": (ctypes.c_int, [vp, ctypes.c_int, u64p, u64, u64p, u64, u64p, u64,
@@ -281,6 +282,12 @@ def sim_plan_schedule(plan, half):
     a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _check(lib().sim_plan_schedule(plan, half, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
     return a.value, b.value, c.value
+
+
+def sim_plan_sparse_depth(plan, half, n_sel, mode=0):
+    d = ctypes.c_int()
+    _check(lib().sim_plan_sparse_depth(plan, half, int(n_sel), int(mode), ctypes.byref(d)))
+    return d.value
 
 
 def sim_plan_sparse_qubits(plan, half, levels):

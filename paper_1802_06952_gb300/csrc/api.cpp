@@ -660,7 +660,9 @@ int evolve_c64_half(CutPlan& P, int h, const CopySet& cs, const uint64_t* d_sel,
   // Selected leaf entries straight from the parents (no leaf states) where the
   // selection is sparse: 2^nq parent reads per entry against a pass over the whole
   // leaf (sim_opts.sparse_leaves: 1 wherever it applies, -1 never)
-  const int sparse_d = full ? 0 : sparse_depth(S, nsel, opts ? opts->sparse_leaves : 0);
+  const int sparse_d = (full || (uint64_t)nsel >= ((uint64_t)1 << S.n))
+                           ? 0
+                           : sparse_depth(S, nsel, opts ? opts->sparse_leaves : 0);
   const TreeProgram prog = plan_tree(S, cs, full, budget, sparse_d);
   std::vector<DevBuf> lvl(J);
   std::vector<HostBuf> hlvl(J);
@@ -1099,6 +1101,14 @@ int sim_plan_sparse_qubits(sim_cut_plan plan, int half, int levels, int* nq_out)
   if (levels < 1 || levels >= (int)S.levels.size())
     return fail(SIM_EINVAL, "levels must be at least 1 and below the number of copy-tree levels");
   *nq_out = leaf_ops(S, levels).nq;
+  return SIM_OK;
+}
+
+int sim_plan_sparse_depth(sim_cut_plan plan, int half, uint64_t n_sel, int mode, int* depth_out) {
+  if (!plan || half < 0 || half > 1 || !depth_out || mode < -1 || mode > 1) return fail(SIM_EINVAL, "bad arguments");
+  const HalfSchedule& S = plan->p.sched[half];
+  // a selection of every index takes the full route (no gather, no sparse leaves)
+  *depth_out = n_sel >= ((uint64_t)1 << S.n) ? 0 : sparse_depth(S, (int64_t)n_sel, mode);
   return SIM_OK;
 }
 

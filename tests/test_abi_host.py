@@ -188,6 +188,32 @@ def test_sparse_qubits_of_the_last_levels():
             sim.sim_plan_sparse_qubits(None, 0, 1)
 
 
+def test_sparse_depth_rule():
+    """The trailing levels the evolve leaves unformed for a selection: the 64-qubit
+    2^14-entry selection skips two levels (|Q| = 8 over levels 15 and 16, and
+    2^14 * 2^8 <= 2^32 / 8); the 42-qubit one none (2^14 * 2^7 > 2^21 / 8) unless
+    forced; never with mode -1 or a selection of every index."""
+    cases = (((8, 8, 22, 4), 1 << 14, [2, 2], [2, 2]), ((6, 7, 22, 3), 1 << 14, [0, 0], [2, 2]))
+    for (R, C, d, b), n_sel, auto, forced in cases:
+        circ = sim.sim_build_circuit(R, C, d, 0, b)
+        plan, c, copies, nu, nl = sim.sim_cut(circ, b)
+        try:
+            assert [sim.sim_plan_sparse_depth(plan, h, n_sel) for h in (0, 1)] == auto
+            assert [sim.sim_plan_sparse_depth(plan, h, n_sel, 1) for h in (0, 1)] == forced
+            assert [sim.sim_plan_sparse_depth(plan, h, n_sel, -1) for h in (0, 1)] == [0, 0]
+            assert sim.sim_plan_sparse_depth(plan, 0, 1 << nu, 1) == 0
+            for h, n in ((0, nu), (1, nl)):
+                dd = sim.sim_plan_sparse_depth(plan, h, n_sel, 1)
+                if dd:
+                    assert sim.sim_plan_sparse_qubits(plan, h, dd) <= 10
+            with pytest.raises(sim.SimError) as e:
+                sim.sim_plan_sparse_depth(plan, 0, n_sel, 2)
+            assert e.value.code == sim.SIM_EINVAL
+        finally:
+            sim.sim_destroy_cut(plan)
+            sim.sim_destroy_circuit(circ)
+
+
 @pytest.mark.parametrize("R,C,d,b,leaf_passes", [(6, 7, 22, 3, 1), (8, 8, 22, 4, 1)])
 def test_copy_independent_ops_climb_the_tree(R, C, d, b, leaf_passes):
     """The cut slots are a level's only copy-dependent items and they are diagonal,
