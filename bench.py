@@ -724,6 +724,27 @@ def run_ours(args):
     streams = [stream] + [torch.cuda.Stream() for _ in range(nstreams - 1)]
     outs = [out] + [torch.empty_like(out) for _ in range(nstreams - 1)]
 
+    def alternate(n, body):
+        """body(i, p) for i in range(n), step i on host thread / stream p = i mod
+        nstreams; the first exception of any thread is re-raised after all joined."""
+        errs = []
+
+        def worker(p):
+            try:
+                torch.cuda.set_device(local)
+                for i in range(p, n, nstreams):
+                    body(i, p)
+            except Exception as ex:  # re-raised below
+                errs.append(ex)
+
+        threads = [threading.Thread(target=worker, args=(p,)) for p in range(nstreams)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        if errs:
+            raise errs[0]
+
     def prepare(i):
         circ = sim.sim_build_circuit(R, C, DEPTH, step_seed(i), CUT_ROW)
         plan, c, copies, nu, nl = sim.sim_cut(circ, CUT_ROW)
@@ -811,25 +832,13 @@ def run_ours(args):
     else:
         for sx in streams[1:]:
             sx.wait_event(e0)
-        errs = []
 
-        def worker(p):
-            try:
-                torch.cuda.set_device(local)
-                for i in range(p, args.steps, nstreams):
-                    per[i][0].record(streams[p])
-                    stats[i] = step(args.warmup + i, outs[p], stream=streams[p], ahead=nstreams)
-                    per[i][1].record(streams[p])
-            except Exception as ex:  # re-raised below
-                errs.append(ex)
+        def timed(i, p):
+            per[i][0].record(streams[p])
+            stats[i] = step(args.warmup + i, outs[p], stream=streams[p], ahead=nstreams)
+            per[i][1].record(streams[p])
 
-        threads = [threading.Thread(target=worker, args=(p,)) for p in range(nstreams)]
-        for t in threads:
-            t.start()
-        for t in threads:
-            t.join()
-        if errs:
-            raise errs[0]
+        alternate(args.steps, timed)
         for sx in streams[1:]:
             ej = torch.cuda.Event()
             ej.record(sx)
@@ -929,23 +938,7 @@ def run_ours(args):
             for i in range(ke):
                 step(i, host)
         else:
-            errs = []
-
-            def e2e_worker(p):
-                try:
-                    torch.cuda.set_device(local)
-                    for i in range(p, ke, nstreams):
-                        step(i, hosts[p], stream=streams[p], ahead=nstreams)
-                except Exception as ex:  # re-raised below
-                    errs.append(ex)
-
-            threads = [threading.Thread(target=e2e_worker, args=(p,)) for p in range(nstreams)]
-            for t in threads:
-                t.start()
-            for t in threads:
-                t.join()
-            if errs:
-                raise errs[0]
+            alternate(ke, lambda i, p: step(i, hosts[p], stream=streams[p], ahead=nstreams))
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         sim.sim_profile_enable(False)
