@@ -13,12 +13,17 @@
 // and reports the largest difference from the leaf's own entries.
 //
 // usage: schedule_exec_check gate_list_file cut_row fuse pass_order out_file k1 [k2 ...]
+//        schedule_exec_check gate_list_file multi:r1,r2,... fuse pass_order out_file k1 [k2 ...]
 // Writes, per listed copy, the upper then the lower leaf (complex128, index order)
-// to out_file and prints "ok <sparse depths tried> <max sparse difference>".
+// to out_file and prints "ok <sparse depths tried> <max sparse difference>".  The
+// multi form evolves every part of a multi-part cut at rows r1 < r2 < ... (each
+// part's schedule with its own copy index k, skipped where k >= 2^{c_p}) and writes
+// the parts' states in order.
 #include "../paper_1802_06952_gb300/csrc/host.cpp"
 
 #include <complex>
 #include <cstdio>
+#include <cstring>
 #include <cstdlib>
 #include <fstream>
 #include <sstream>
@@ -116,14 +121,39 @@ int main(int argc, char** argv) {
     printf("parse: %s\n", err.c_str());
     return 1;
   }
+  FILE* out = fopen(argv[5], "wb");
+  if (!out) return 1;
+  if (strncmp(argv[2], "multi:", 6) == 0) {
+    std::vector<int> rows;
+    for (const char* p = argv[2] + 6; *p;) {
+      rows.push_back((int)strtol(p, (char**)&p, 10));
+      if (*p == ',') ++p;
+    }
+    MultiPlan mp;
+    err = build_multi_plan(c, rows, atoi(argv[3]), atoi(argv[4]), mp);
+    if (!err.empty()) {
+      printf("plan: %s\n", err.c_str());
+      return 1;
+    }
+    for (int a = 6; a < argc; ++a) {
+      const uint64_t k = strtoull(argv[a], nullptr, 10);
+      for (int p = 0; p < mp.t; ++p) {
+        const HalfSchedule& S = mp.part[p].sched[0];
+        if (k >> mp.slot_bits[p].size()) continue;
+        const std::vector<cd> st = evolve(S, k, (int)S.levels.size());
+        fwrite(st.data(), sizeof(cd), st.size(), out);
+      }
+    }
+    fclose(out);
+    printf("ok 0 0\n");
+    return 0;
+  }
   CutPlan P;
   err = build_cut_plan(c, atoi(argv[2]), atoi(argv[3]), P, atoi(argv[4]), false);
   if (!err.empty()) {
     printf("plan: %s\n", err.c_str());
     return 1;
   }
-  FILE* out = fopen(argv[5], "wb");
-  if (!out) return 1;
   int depths_tried = 0;
   double worst = 0;
   for (int a = 6; a < argc; ++a) {

@@ -6,9 +6,10 @@ levels with their hoisted ops, passes, diagonal ops with cut slots) in FP64 with
 full gate matrices; every leaf must equal the oracle's gate-by-gate half-state of
 that copy (Supplementary A, Eqs. 1, 4-5).  It also evaluates selected leaf entries
 from an ancestor d levels up (the sparse leaves' formula), which must equal the
-leaf's own entries.  This pins the schedule transformations (dependency-aware pass
-formation, ops moved up the copy tree, controlled-gate slots) independently of the
-GPU kernels."""
+leaf's own entries.  Multi-part plans (Section 3, Fig. 3) are executed part by part
+against the oracle's part states.  This pins the schedule transformations
+(dependency-aware pass formation, ops moved up the copy tree, controlled-gate
+slots, the P_l / Z^l slots of middle parts) independently of the GPU kernels."""
 import os
 import shutil
 import subprocess
@@ -95,3 +96,30 @@ def test_schedules_of_random_circuits(checker, tmp_path):
         plan = oc.CutPlan(R * C, b * C, gates)
         copies = sorted({0, int(rng.integers(0, plan.copies)), plan.copies - 1})
         check(checker, tmp_path, R, C, d, gates, b, int(rng.integers(4, 14)), int(rng.integers(0, 2)), copies)
+
+
+@pytest.mark.parametrize("R,C,d,seed,rows", [(6, 3, 16, 0, (2, 4)), (8, 2, 20, 3, (2, 5, 6)), (6, 4, 12, 1, (3,))])
+def test_schedules_of_multi_part_cuts(checker, tmp_path, R, C, d, seed, rows):
+    gates = oc.generate(R, C, d, seed, rows[0])
+    plan = oc.MultiCutPlan(R, C, rows, gates)
+    txt = tmp_path / "circuit.txt"
+    txt.write_text(oc.to_text(R, C, d, 0, gates))
+    cbits = [len(plan.local[p]) for p in range(plan.t)]
+    copies = sorted({0, 1, 5, (1 << max(cbits)) - 1})
+    for fuse, order in ((13, 0), (5, 1)):
+        out = tmp_path / "parts.bin"
+        r = subprocess.run([checker, str(txt), "multi:" + ",".join(str(x) for x in rows), str(fuse), str(order),
+                            str(out)] + [str(k) for k in copies], capture_output=True, text=True)
+        assert r.returncode == 0 and r.stdout.startswith("ok"), r.stdout + r.stderr
+        data = np.fromfile(str(out), dtype=np.complex128)
+        pos = 0
+        for k in copies:
+            for p in range(plan.t):
+                if k >> cbits[p]:
+                    continue
+                got = data[pos:pos + (1 << plan.nq[p])]
+                pos += 1 << plan.nq[p]
+                ref = oracle.part_state(plan, p, int(k))
+                scale = max(float(np.max(np.abs(ref))), 1e-300)
+                assert float(np.max(np.abs(got - ref))) <= 1e-12 * scale, (k, p)
+        assert pos == data.size
