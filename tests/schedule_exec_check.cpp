@@ -12,6 +12,16 @@
 // levels' ops to the 2^|Q| ancestor entries that agree with the entry outside Q,
 // and reports the largest difference from the leaf's own entries.
 //
+// It also recomputes, for every pass the register-blocked sweep runs, what that
+// kernel derives from the host's per-op tables, and compares it with the op in
+// qubit space for every index: each gate's rank under the pass's rank map (moved by
+// its warp/register exchanges) is the gate's qubit; the gate's unscaled update times
+// the common factor is its matrix; a diagonal op's exponent built as the kernel
+// builds it (thread part, register-part table, register partners B, cut slots,
+// the pass phase) equals the qubit-space exponent mod 8, with the same projector
+// test; sign-only ops have exponents 0 or 4; and the pass's scale and phase are the
+// product of the factors its unscaled gates leave out.
+//
 // usage: schedule_exec_check gate_list_file cut_row fuse pass_order out_file k1 [k2 ...]
 //        schedule_exec_check gate_list_file multi:r1,r2,... fuse pass_order out_file k1 [k2 ...]
 // Writes, per listed copy, the upper then the lower leaf (complex128, index order)
@@ -105,6 +115,112 @@ std::vector<cd> evolve(const HalfSchedule& S, uint64_t k, int upto) {
   return psi;
 }
 
+// the register-blocked sweep's view of one pass, checked against qubit space for
+// copy k; returns an empty string or the first difference
+std::string check_register_pass(const HalfSchedule& S, const PassDesc& p, uint64_t k) {
+  const int R = p.k - 8;
+  int ord[16];
+  for (int r = 0; r < 16; ++r) ord[r] = r < p.k ? p.order[r] : -1;
+  const double s2 = 0.70710678118654752440;
+  const cd fxy(0.5, 0.5);  // (1+i)/2: X^1/2, Y^1/2 without it are [[1,-i],[-i,1]], [[1,-1],[1,1]]
+  int n_xy = 0, n_h = 0;
+  char buf[256];
+  for (int oi = 0; oi < p.op_count; ++oi) {
+    const OpRec& op = S.ops[p.op_begin + oi];
+    if (op.type == OP_SWAP) {
+      for (int m = 0; m < 3; ++m) std::swap(ord[5 + m], ord[10 + m]);
+      for (int r = 0; r < 8; ++r)
+        if (op.tq[r] != ord[r]) return "swap: thread rank map";
+      continue;
+    }
+    if (op.type == OP_GATE) {
+      if (op.lq < 0 || op.lq >= p.k || ord[op.lq] != op.q) {
+        snprintf(buf, sizeof buf, "gate on qubit %d at rank %d holding %d", op.q, op.lq, op.lq >= 0 ? ord[op.lq] : -1);
+        return buf;
+      }
+      cd u[4];
+      if (op.kind == 1) {
+        u[0] = fxy; u[1] = fxy * cd(0, -1); u[2] = fxy * cd(0, -1); u[3] = fxy;
+        ++n_xy;
+      } else if (op.kind == 2) {
+        u[0] = fxy; u[1] = -fxy; u[2] = fxy; u[3] = fxy;
+        ++n_xy;
+      } else if (op.kind == 3) {
+        u[0] = s2; u[1] = s2; u[2] = s2; u[3] = -s2;
+        ++n_h;
+      } else {
+        return "a general gate in a register-blocked pass";
+      }
+      for (int e = 0; e < 4; ++e)
+        if (std::abs(u[e] - cd(op.md[2 * e], op.md[2 * e + 1])) > 1e-15) return "gate kind and matrix differ";
+      continue;
+    }
+    uint32_t regmask = 0;
+    for (int r = 0; r < R; ++r) {
+      regmask |= 1u << ord[8 + r];
+      if (op.rq[r] != ord[8 + r]) return "diag: register qubits";
+    }
+    if (op.regmask != regmask) return "diag: register mask";
+    const int phase = (oi == p.phase_op) ? p.phase_e : 0;
+    if (op.sign_only && phase) return "sign-only op takes the pass phase";
+    for (uint64_t x = 0; x < ((uint64_t)1 << S.n); ++x) {
+      const uint32_t xt = (uint32_t)x & ~regmask;
+      uint32_t j = 0;
+      for (int r = 0; r < R; ++r)
+        if ((x >> ord[8 + r]) & 1ull) j |= 1u << r;
+      // the kernel's terms
+      int s2c = 0;
+      for (int s = 0; s < op.nsh; ++s) s2c += __builtin_popcount(xt & (xt >> op.sh_d[s]) & op.sh_m[s]);
+      int et = __builtin_popcount(xt & op.tmask) + 4 * s2c + phase;
+      uint32_t B = 0;
+      for (int r = 0; r < R; ++r)
+        if (op.pq[r] != 0xFF && ((xt >> op.pq[r]) & 1u)) B |= 1u << r;
+      bool keep = true;
+      uint32_t wsum = 0;  // weights of phase slots on register qubits with j's bit set
+      for (int i = 0; i < op.ncut; ++i) {
+        const uint32_t q = op.cutq[i];
+        const uint64_t l = (k >> op.cutm[i]) & 1ull;
+        const bool reg = (regmask >> q) & 1u;
+        const uint32_t bit = (uint32_t)((x >> q) & 1ull);
+        if (!((op.cutz >> i) & 1u)) {
+          if (bit != l) keep = false;
+        } else if (l) {
+          const uint32_t w = op.cutw[i];
+          if (!reg) {
+            et += (int)((w & 4u) ? 4 * bit : 0) + (int)((w & 1u) ? bit : 0) + (int)((w & 2u) ? 2 * bit : 0);
+          } else {
+            int r = 0;
+            while (ord[8 + r] != (int)q) ++r;
+            if (w & 4u) B ^= 1u << r;
+            if (bit) wsum += (w & 3u);
+          }
+        }
+      }
+      const uint32_t field = (op.ereg[j / 8] >> (4 * (j % 8))) & 0xFu;
+      int ek = (int)((field + (uint32_t)(et & 7)) & 7u);
+      if (__builtin_popcount(B & j) & 1) ek = (ek + 4) & 7;
+      ek = (ek + (int)wsum) & 7;
+      bool kq;
+      const int eq = (diag_exponent(op, x, k, kq) + phase) & 7;
+      if (kq != keep || (keep && eq != ek)) {
+        snprintf(buf, sizeof buf, "diag op %d at x=%llu: kernel e=%d keep=%d, qubit space e=%d keep=%d", oi,
+                 (unsigned long long)x, ek, (int)keep, eq, (int)kq);
+        return buf;
+      }
+      if (op.sign_only && keep && (eq & 3)) return "sign-only op with an exponent other than 0 or 4";
+    }
+  }
+  // scale and phase: the factors the unscaled gates leave out
+  const cd want = std::pow(cd(s2, 0), n_xy + n_h) * std::pow(cd(s2, s2), n_xy);  // |(1+i)/2| = 1/sqrt2, arg pi/4
+  const cd have = (double)p.scale * omega(p.phase_e);
+  if (std::abs(want - have) > 1e-6 * std::abs(want)) {
+    snprintf(buf, sizeof buf, "pass factor: want %g%+gi, scale*w^e %g%+gi", want.real(), want.imag(), have.real(),
+             have.imag());
+    return buf;
+  }
+  return "";
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
@@ -161,6 +277,15 @@ int main(int argc, char** argv) {
     for (int h = 0; h < 2; ++h) {
       const HalfSchedule& S = P.sched[h];
       const int J = (int)S.levels.size();
+      for (const Level& L : S.levels)
+        for (const PassDesc& pd : L.passes)
+          if (pd.k >= 8 && pd.low == 5 && !pd.general_gates && pd.op_count > 0) {
+            const std::string e = check_register_pass(S, pd, k);
+            if (!e.empty()) {
+              printf("tables: half %d: %s\n", h, e.c_str());
+              return 1;
+            }
+          }
       const std::vector<cd> leaf = evolve(S, k, J);
       fwrite(leaf.data(), sizeof(cd), leaf.size(), out);
       // sparse entries from the ancestor d levels up, on a seeded selection
